@@ -1,0 +1,190 @@
+/*
+ * vorogpu.h -- C ABI of the GB300 library for the cell-based Voronoi method
+ * of "An extension to Voro++ for multithreaded computation of Voronoi cells"
+ * (arXiv 2209.11606).
+ *
+ * The library computes, for every particle, its Voronoi cell (or radical
+ * Voronoi cell) inside a rectangular container, and reduces per-cell
+ * statistics.  The method is the paper's Sec. 2.1:
+ *   - particles are sorted into a grid of equal blocks (Sec. 2.1.1);
+ *   - a cell starts as the container box relative to its particle
+ *     (Eqs. 1-2) and is cut by the half-space of Eq. 3 for each neighbour,
+ *     visited near-to-far, until the radius bound of Sec. 2.1.3 shows that
+ *     no remaining particle can cut it;
+ *   - statistics are taken from the finished cell (Sec. 2.1.2).
+ *
+ * Conventions for every call:
+ *   - Every function returns a vg_status; nothing throws across the ABI.
+ *     On failure vg_last_error() gives a one-line reason.
+ *   - The caller owns every input and output buffer it passes; the context
+ *     owns its internal device buffers and frees them in vg_destroy().
+ *   - `on_device` = 1 means the pointer is CUDA device memory (for example a
+ *     torch tensor's data_ptr()); 0 means host memory.  Host outputs are
+ *     written synchronously; device outputs are written asynchronously on
+ *     the context's stream.
+ *   - All work is queued on the CUDA stream given to vg_create() (NULL =
+ *     the legacy default stream); the caller synchronises that stream.
+ *   - A context is not thread-safe; use one context per host thread.
+ *   - Cells are reported in the caller's original particle order.
+ *   - Particle count is limited to 2^31 - 1 (neighbour ids are int32); the
+ *     sorted-candidate prefetch form is used up to 2^27 particles and the
+ *     plain walk beyond.
+ */
+#ifndef VOROGPU_H
+#define VOROGPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vg_ctx vg_ctx;
+
+typedef enum {
+    VG_OK = 0,
+    VG_ERR_ARG = 1,        /* invalid argument (NULL, size, dimension) */
+    VG_ERR_OOM = 2,        /* device allocation failed */
+    VG_ERR_OUT_OF_BOX = 3, /* a walled coordinate lies outside [lo, hi] */
+    VG_ERR_NONFINITE = 4,  /* a coordinate or radius is NaN or infinite */
+    VG_ERR_CAP = 5,        /* some cell exceeded every capacity tier */
+    VG_ERR_CUDA = 6,       /* a CUDA call failed; see vg_last_error() */
+    VG_ERR_STATE = 7,      /* call out of order (e.g. compute before insert) */
+    VG_ERR_DUP_POINT = 8   /* two particles coincide (undefined bisector) */
+} vg_status;
+
+/* Arithmetic forms of the cell computation. */
+enum {
+    VG_FP64 = 0,        /* plain form: every cut and statistic in FP64 */
+    VG_FP32_RETEST = 1  /* FP32 cuts relative to the particle; any vertex
+                           within the FP32 band of a cutting plane is
+                           re-tested in FP64 from the original positions;
+                           volumes accumulated in FP64 */
+};
+
+/* Order in which neighbours are offered to a cell. */
+enum {
+    VG_WALK = 0,     /* Sec. 2.1.3: own block, then blocks in order of their
+                        distance bound, stopped by the radius bound */
+    VG_PREFETCH = 1  /* the candidates of the 27 surrounding blocks within a
+                        prefetch radius, sorted by distance and cut in that
+                        order; the radius bound still decides, and a cell
+                        that needs more falls back to VG_WALK */
+};
+
+/* Per-cell status values written by vg_get_cells(). */
+enum {
+    VG_CELL_OK = 0,
+    VG_CELL_EMPTY = 1,   /* radical variant: the cell does not exist
+                            (Sec. 2.2.3: compute_cell returns false) */
+    VG_CELL_CAP = 2,     /* vertex or face capacity exceeded on every tier */
+    VG_CELL_DUP = 3,     /* another particle sits on this one */
+    VG_CELL_LIMIT = 4    /* the walk ran past its shell limit */
+};
+
+typedef struct {
+    int precision;     /* VG_FP64 or VG_FP32_RETEST */
+    int order;         /* VG_WALK or VG_PREFETCH */
+    double tol32;      /* FP32 band: |d| <= tol32 * R * |q| is re-tested in
+                          FP64 (R: current max vertex distance); default 1e-5 */
+    double tau_rel;    /* FP64 on-plane band: |d| <= tau_rel * s * |q| counts
+                          as on the plane and the vertex stays (s = mean
+                          spacing (V/N)^(1/dim)); default 1e-11 */
+    double merge_rel;  /* vertices closer than merge_rel * s are one vertex
+                          (degree > 3 on exact lattices); default 1e-9 */
+    int prefetch_k;    /* VG_PREFETCH: target candidate count; <= 0: the
+                          library default (3D 72, 2D 24) */
+    int use_mlp;       /* VG_PREFETCH: 1 = take the per-block candidate count
+                          from the loaded MLP (vg_mlp_set_weights) */
+    int chunk;         /* cells taken per work-queue ticket; <= 0: default */
+    int warps_per_cta; /* <= 0: default */
+    int collect_stats; /* 1 = fill the per-cell work counters */
+} vg_config;
+
+/* Fills `cfg` with the defaults listed above (FP32_RETEST, PREFETCH). */
+void vg_config_default(vg_config *cfg);
+
+/*
+ * Creates a container: the box [lo, hi] (dim = 2 or 3 doubles each), the
+ * periodic flag per axis (Sec. 2.1.1), and the block grid.  `nblocks` gives
+ * blocks per axis; NULL selects the Sec. 2.1.4 rule from `n_opt` particles
+ * per block at the time of vg_insert() (lambda = (N/(n_opt V))^(1/dim),
+ * n_a = max(1, floor(lambda L_a)); n_opt <= 0 selects 4.6 in 3D, 3.4 in 2D).
+ * `stream` is a cudaStream_t (NULL: default stream).
+ */
+vg_status vg_create(vg_ctx **out, int dim, const double *lo, const double *hi,
+                    const int *periodic, const int *nblocks, double n_opt,
+                    void *stream);
+
+/*
+ * Replaces the container's particles (the paper's clear() followed by
+ * add_parallel(), Sec. 2.2.5) and sorts them into blocks with a counting
+ * sort on the GPU.  `pos` is n x dim doubles, row-major; `radii` is n doubles
+ * or NULL (NULL: plain Voronoi; non-NULL: radical variant).  Coordinates on
+ * a periodic axis are wrapped into [lo, hi); on a walled axis they must lie
+ * in [lo, hi] (VG_ERR_OUT_OF_BOX otherwise; a point on hi goes to the last
+ * block).  Inside a block particles are ordered by input index, so results
+ * do not depend on thread timing.
+ */
+vg_status vg_insert(vg_ctx *ctx, int64_t n, const double *pos, const double *radii,
+                    int on_device);
+
+/* Computes all cells with the given configuration (NULL: defaults). */
+vg_status vg_compute(vg_ctx *ctx, const vg_config *cfg);
+
+/* Number of cells and total number of faces (edges in 2D) of the last
+ * vg_compute(); synchronises the stream. */
+vg_status vg_get_counts(vg_ctx *ctx, int64_t *n_cells, int64_t *n_faces);
+
+/*
+ * Per-cell outputs, n entries each, in input order (any pointer may be
+ * NULL to skip it):
+ *   vol       volume (3D) or area (2D), FP64
+ *   area      total face area (3D) or perimeter (2D), FP64
+ *   centroid  n x dim, relative to the particle, FP64
+ *   nv ne nf  vertex, edge and face counts (2D: nv = ne = nf = edges)
+ *   status    VG_CELL_* code
+ */
+vg_status vg_get_cells(vg_ctx *ctx, double *vol, double *area, double *centroid,
+                       int32_t *nv, int32_t *ne, int32_t *nf, uint8_t *status,
+                       int on_device);
+
+/*
+ * Faces as CSR: face_off has n+1 entries; cell i's faces are
+ * [face_off[i], face_off[i+1]) in canonical order, ascending (neighbour id,
+ * image shift).  nbr_id is the neighbour's input index, or -1..-6 for the
+ * walls x-, x+, y-, y+, z-, z+ of a walled axis; nbr_img is the periodic
+ * image shift of the neighbour, 3 int8 per face (z = 0 in 2D); face_order is
+ * the number of vertices of the face (2 in 2D).
+ */
+vg_status vg_get_faces(vg_ctx *ctx, int64_t *face_off, int32_t *nbr_id, int8_t *nbr_img,
+                       uint8_t *face_order, int on_device);
+
+/*
+ * Per-cell work counters of the last vg_compute() with collect_stats = 1,
+ * n entries each (any may be NULL): candidates offered to the cut routine,
+ * vertex-plane tests, cuts that removed something, FP64 re-tests, and
+ * whether the prefetch form fell back to the walk (0/1).
+ */
+vg_status vg_get_work(vg_ctx *ctx, int32_t *n_tested, int32_t *n_vtests, int32_t *n_cuts,
+                      int32_t *n_retest, uint8_t *fallback, int on_device);
+
+/*
+ * The sorted container: block_start has B+1 entries (B = product of the
+ * block counts) and order[k] is the input index of the k-th particle in
+ * block order.  For checking the counting sort; device or host output.
+ */
+vg_status vg_get_sorted(vg_ctx *ctx, int64_t *n_blocks, int32_t *block_start, int32_t *order,
+                        int on_device);
+
+/* The block counts in use (after vg_insert() when the n_opt rule applies). */
+vg_status vg_get_grid(vg_ctx *ctx, int *nblocks);
+
+const char *vg_last_error(vg_ctx *ctx);
+void vg_destroy(vg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VOROGPU_H */

@@ -1,0 +1,283 @@
+// Counting sort of particles into the block grid, and exclusive scans.
+//
+// The paper's serial put() and parallel put_parallel() (Sec. 2.2.5) place a
+// particle in slot co[k]++ of its block k, the latter via an atomic capture
+// and an overflow buffer.  On the GPU the same atomic capture gives each
+// particle a slot; an exclusive scan of the block counts then gives every
+// block exact capacity, so no overflow buffer exists.  A last pass orders the
+// particles inside a block by input index (the paper notes that thread timing
+// otherwise changes the insertion order, Sec. 2.2.5), making the result
+// deterministic.
+#include "vg_internal.cuh"
+
+namespace vg {
+
+namespace {
+
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// Block coordinate of one axis: floor((x - lo)/h) clamped to [0, n-1].
+__device__ __forceinline__ int block_coord(double x, double lo, double h, int n) {
+    int b = (int)floor(__ddiv_rn(__dsub_rn(x, lo), h));
+    return b < 0 ? 0 : (b >= n ? n - 1 : b);
+}
+
+// Wraps a periodic coordinate into [lo, hi).
+__device__ __forceinline__ double wrap(double x, double lo, double L) {
+    double t = __dsub_rn(x, lo);
+    if (t < 0.0 || t >= L) {
+        t = t - floor(t / L) * L;
+        if (t >= L) t -= L;
+        if (t < 0.0) t = 0.0;
+    }
+    return __dadd_rn(lo, t);
+}
+
+// Step 1: validate, wrap, compute the block key and take a slot with an
+// atomic capture on the block count.
+__global__ void k_index(Grid g, long long n, const double *__restrict__ pos,
+                        const double *__restrict__ rad, int *__restrict__ key,
+                        int *__restrict__ slot, int *__restrict__ count, int *__restrict__ err) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    long long k = 0, mul = 1;
+    bool bad = false, outside = false;
+    for (int a = 0; a < g.dim; a++) {
+        double x = pos[i * g.dim + a];
+        if (!isfinite(x)) { bad = true; x = g.lo[a]; }
+        if (g.per[a]) x = wrap(x, g.lo[a], g.L[a]);
+        else if (x < g.lo[a] || x > g.hi[a]) { outside = true; x = g.lo[a]; }
+        k += mul * block_coord(x, g.lo[a], g.h[a], g.nb[a]);
+        mul *= g.nb[a];
+    }
+    if (rad && !(isfinite(rad[i]) && rad[i] >= 0.0)) bad = true;
+    if (bad) atomicAdd(&err[1], 1);
+    if (outside) atomicAdd(&err[0], 1);
+    key[i] = (int)k;
+    slot[i] = atomicAdd(&count[k], 1);
+}
+
+// Step 3: scatter input indices to their (unordered) slot in the block.
+__global__ void k_scatter(long long n, const int *__restrict__ key, const int *__restrict__ slot,
+                          const int *__restrict__ bstart, int *__restrict__ tmp_id) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    tmp_id[bstart[key[i]] + slot[i]] = (int)i;
+}
+
+// Step 4: rank inside the block by input index and write the sorted store.
+__global__ void k_finalize(Grid g, long long n, const int *__restrict__ key,
+                           const int *__restrict__ bstart, const int *__restrict__ tmp_id,
+                           const double *__restrict__ pos, const double *__restrict__ rad,
+                           float4 *__restrict__ p32, D4 *__restrict__ p64,
+                           int *__restrict__ sid, int *__restrict__ sblk) {
+    long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    int i = tmp_id[u];
+    int k = key[i];
+    int b0 = bstart[k], b1 = bstart[k + 1];
+    int rank = 0;
+    for (int v = b0; v < b1; v++) rank += tmp_id[v] < i;
+    int dst = b0 + rank;
+    double x[3] = {0, 0, 0};
+    float o[3] = {0.f, 0.f, 0.f};
+    int kk = k;
+    for (int a = 0; a < g.dim; a++) {
+        double xa = pos[(long long)i * g.dim + a];
+        if (!isfinite(xa)) xa = g.lo[a];
+        if (g.per[a]) xa = wrap(xa, g.lo[a], g.L[a]);
+        else xa = fmin(fmax(xa, g.lo[a]), g.hi[a]);
+        int b = kk % g.nb[a];
+        kk /= g.nb[a];
+        double corner = __dadd_rn(g.lo[a], __dmul_rn((double)b, g.h[a]));
+        x[a] = xa;
+        o[a] = __double2float_rn(__dsub_rn(xa, corner));
+    }
+    double r = rad ? rad[i] : 0.0;
+    p32[dst] = make_float4(o[0], o[1], o[2], (float)r);
+    D4 v; v.x = x[0]; v.y = x[1]; v.z = x[2]; v.w = r;
+    p64[dst] = v;
+    sid[dst] = i;
+    sblk[dst] = k;
+}
+
+// ---- exclusive scan: tiles, recursive tile sums, add back ------------------
+
+template <typename TI, typename TO>
+__global__ void k_scan_tiles(const TI *__restrict__ in, TO *__restrict__ out, long long n,
+                             TO *__restrict__ tile_sums) {
+    __shared__ TO warp_tot[SCAN_THREADS / 32];
+    long long base = blockIdx.x * (long long)SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    TO v[SCAN_ITEMS];
+    TO run = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; j++) {
+        long long idx = base + j;
+        TO x = idx < n ? (TO)in[idx] : (TO)0;
+        v[j] = run;
+        run += x;
+    }
+    // warp inclusive scan of per-thread totals
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    TO incl = run;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        TO y = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        TO t = lane < SCAN_THREADS / 32 ? warp_tot[lane] : (TO)0;
+        TO ti = t;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            TO y = __shfl_up_sync(FULL, ti, d);
+            if (lane >= d) ti += y;
+        }
+        if (lane < SCAN_THREADS / 32) warp_tot[lane] = ti - t;  // exclusive
+        if (lane == SCAN_THREADS / 32 - 1 && tile_sums) tile_sums[blockIdx.x] = ti;
+    }
+    __syncthreads();
+    TO off = warp_tot[w] + (incl - run);
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; j++) {
+        long long idx = base + j;
+        if (idx < n) out[idx] = v[j] + off;
+    }
+}
+
+template <typename T>
+__global__ void k_add_tile(T *__restrict__ out, long long n, const T *__restrict__ tile_off) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx < n) out[idx] += tile_off[idx / SCAN_TILE];
+}
+
+template <typename T>
+size_t scan_tmp_bytes(long long n) {
+    size_t bytes = 0;
+    long long m = n;
+    while (m > 1) {
+        long long tiles = (m + SCAN_TILE - 1) / SCAN_TILE;
+        bytes += 2 * (size_t)(tiles + 1) * sizeof(T) + 256;
+        m = tiles;
+        if (tiles == 1) break;
+    }
+    return bytes + 256;
+}
+
+// Exclusive scan of n inputs into out[0..n) (out[n] is not written here).
+template <typename TI, typename TO>
+cudaError_t scan_rec(const TI *in, TO *out, long long n, char *tmp, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    long long tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    TO *sums = (TO *)tmp;
+    TO *sums_x = sums + (tiles + 1);
+    char *next = (char *)(sums_x + (tiles + 1));
+    next = (char *)(((uintptr_t)next + 255) & ~(uintptr_t)255);
+    k_scan_tiles<TI, TO><<<(unsigned)tiles, SCAN_THREADS, 0, st>>>(in, out, n, sums);
+    if (tiles > 1) {
+        cudaError_t e = scan_rec<TO, TO>(sums, sums_x, tiles, next, st);
+        if (e != cudaSuccess) return e;
+        k_add_tile<TO><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, n, sums_x);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t scan_tmp_bytes_i32(long long n) { return scan_tmp_bytes<int>(n); }
+size_t scan_tmp_bytes_i64(long long n) { return scan_tmp_bytes<long long>(n); }
+
+// out has n+1 entries: out[n] = total.
+cudaError_t exclusive_scan_i32(const int *in, int *out, long long n, void *tmp, cudaStream_t st) {
+    // scanning n+1 entries with the last input read as 0 yields the total
+    cudaError_t e = scan_rec<int, int>(in, out, n, (char *)tmp, st);
+    if (e != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+cudaError_t exclusive_scan_i64_from_i32(const int *in, long long *out, long long n, void *tmp,
+                                        cudaStream_t st) {
+    return scan_rec<int, long long>(in, out, n, (char *)tmp, st);
+}
+
+namespace {
+// total = out[n-1] + in[n-1], written to out[n]
+template <typename TI, typename TO>
+__global__ void k_total(const TI *in, TO *out, long long n) {
+    out[n] = n > 0 ? out[n - 1] + (TO)in[n - 1] : (TO)0;
+}
+}  // namespace
+
+cudaError_t sort_particles(const Grid &g, long long n, const double *pos, const double *radii,
+                           int *key, int *slot, int *count, int *bstart, int *tmp_id,
+                           float4 *p32, D4 *p64, int *sid, int *sblk, int *errflags,
+                           void *scan_tmp, size_t scan_tmp_bytes_, cudaStream_t st) {
+    (void)scan_tmp_bytes_;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(count, 0, sizeof(int) * g.nblk, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(errflags, 0, sizeof(int) * 2, st)) != cudaSuccess) return e;
+    const int T = 256;
+    unsigned nbk = (unsigned)((n + T - 1) / T);
+    if (n > 0) k_index<<<nbk, T, 0, st>>>(g, n, pos, radii, key, slot, count, errflags);
+    if ((e = exclusive_scan_i32(count, bstart, g.nblk, scan_tmp, st)) != cudaSuccess) return e;
+    k_total<int, int><<<1, 1, 0, st>>>(count, bstart, g.nblk);
+    if (n > 0) {
+        k_scatter<<<nbk, T, 0, st>>>(n, key, slot, bstart, tmp_id);
+        k_finalize<<<nbk, T, 0, st>>>(g, n, key, bstart, tmp_id, pos, radii, p32, p64, sid, sblk);
+    }
+    return cudaGetLastError();
+}
+
+// ---- CSR compaction of faces ---------------------------------------------------
+
+namespace {
+__global__ void k_nf_ok(long long n, const int *nf, const unsigned char *status, int *nf_ok) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) nf_ok[i] = status[i] == VG_CELL_OK ? nf[i] : 0;
+}
+
+// one warp per 32 cells: each lane copies its cell's faces
+__global__ void k_compact(long long n, const int *__restrict__ nf_ok,
+                          const long long *__restrict__ fptr, const int2 *__restrict__ faces,
+                          const long long *__restrict__ face_off, int *__restrict__ nbr_id,
+                          signed char *__restrict__ nbr_img, unsigned char *__restrict__ face_order) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int k = nf_ok[i];
+    long long src = fptr[i], dst = face_off[i];
+    for (int f = 0; f < k; f++) {
+        int2 e = faces[src + f];
+        nbr_id[dst + f] = e.x;
+        nbr_img[(dst + f) * 3 + 0] = (signed char)(e.y & 0xff);
+        nbr_img[(dst + f) * 3 + 1] = (signed char)((e.y >> 8) & 0xff);
+        nbr_img[(dst + f) * 3 + 2] = (signed char)((e.y >> 16) & 0xff);
+        face_order[dst + f] = (unsigned char)((unsigned)e.y >> 24);
+    }
+}
+
+}  // namespace
+
+cudaError_t compact_faces(long long n, const int *nf, const unsigned char *status,
+                          const long long *fptr, const int2 *faces, long long *face_off,
+                          int *nbr_id, signed char *nbr_img, unsigned char *face_order,
+                          void *scan_tmp, cudaStream_t st) {
+    // nf_ok is staged in the tail of face_off's memory? no: reuse nbr_id head is unsafe;
+    // the caller provides scan_tmp large enough for n ints plus the i64 scan.
+    int *nf_ok = (int *)scan_tmp;
+    char *tmp = (char *)scan_tmp + (((size_t)n * sizeof(int) + 255) & ~(size_t)255);
+    const int T = 256;
+    unsigned nbk = (unsigned)((n + T - 1) / T);
+    if (n > 0) k_nf_ok<<<nbk, T, 0, st>>>(n, nf, status, nf_ok);
+    cudaError_t e = scan_rec<int, long long>(nf_ok, face_off, n, tmp, st);
+    if (e != cudaSuccess) return e;
+    k_total<int, long long><<<1, 1, 0, st>>>(nf_ok, face_off, n);
+    if (n > 0)
+        k_compact<<<nbk, T, 0, st>>>(n, nf_ok, fptr, faces, face_off, nbr_id, nbr_img, face_order);
+    return cudaGetLastError();
+}
+
+}  // namespace vg

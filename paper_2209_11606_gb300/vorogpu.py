@@ -1,0 +1,225 @@
+"""Python binding of libvorogpu (include/vorogpu.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and passes
+plain pointers through ctypes; all computation runs in the library's CUDA
+kernels.  PyTorch is used for device memory and streams: tensors are passed
+by ``data_ptr()``.  If the shared library has not been built the import-time
+loader raises; there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvorogpu.so")
+
+VG_OK = 0
+STATUS_NAMES = {0: "VG_OK", 1: "VG_ERR_ARG", 2: "VG_ERR_OOM", 3: "VG_ERR_OUT_OF_BOX",
+                4: "VG_ERR_NONFINITE", 5: "VG_ERR_CAP", 6: "VG_ERR_CUDA", 7: "VG_ERR_STATE",
+                8: "VG_ERR_DUP_POINT"}
+VG_FP64, VG_FP32_RETEST = 0, 1
+VG_WALK, VG_PREFETCH = 0, 1
+VG_CELL_OK, VG_CELL_EMPTY, VG_CELL_CAP, VG_CELL_DUP, VG_CELL_LIMIT = 0, 1, 2, 3, 4
+
+EXPORTS = ["vg_config_default", "vg_create", "vg_insert", "vg_compute", "vg_get_counts",
+           "vg_get_cells", "vg_get_faces", "vg_get_work", "vg_get_sorted", "vg_get_grid",
+           "vg_last_error", "vg_destroy"]
+
+
+class VgConfig(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("order", ctypes.c_int), ("tol32", ctypes.c_double),
+                ("tau_rel", ctypes.c_double), ("merge_rel", ctypes.c_double),
+                ("prefetch_k", ctypes.c_int), ("use_mlp", ctypes.c_int), ("chunk", ctypes.c_int),
+                ("warps_per_cta", ctypes.c_int), ("collect_stats", ctypes.c_int)]
+
+
+class VgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads the shared library (build it with paper_2209_11606_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libvorogpu.so not built at {path}; run paper_2209_11606_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    sig = {
+        "vg_config_default": (None, [ctypes.POINTER(VgConfig)]),
+        "vg_create": (I, [ctypes.POINTER(P), I, P, P, P, P, D, P]),
+        "vg_insert": (I, [P, L, P, P, I]),
+        "vg_compute": (I, [P, ctypes.POINTER(VgConfig)]),
+        "vg_get_counts": (I, [P, ctypes.POINTER(L), ctypes.POINTER(L)]),
+        "vg_get_cells": (I, [P, P, P, P, P, P, P, P, I]),
+        "vg_get_faces": (I, [P, P, P, P, P, I]),
+        "vg_get_work": (I, [P, P, P, P, P, P, I]),
+        "vg_get_sorted": (I, [P, ctypes.POINTER(L), P, P, I]),
+        "vg_get_grid": (I, [P, P]),
+        "vg_last_error": (ctypes.c_char_p, [P]),
+        "vg_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(ctx, code):
+    if code != VG_OK:
+        msg = _lib.vg_last_error(ctx).decode() if ctx else ""
+        raise VgError(code, msg)
+
+
+def _ptr(x):
+    """Address of a numpy array or torch tensor, and whether it is on a GPU."""
+    if x is None:
+        return None, 0
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data, 0
+    # torch tensor
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return x.data_ptr(), 1 if x.is_cuda else 0
+
+
+def vg_config_default() -> VgConfig:
+    cfg = VgConfig()
+    load().vg_config_default(ctypes.byref(cfg))
+    return cfg
+
+
+def vg_create(dim, lo, hi, periodic, nblocks=None, n_opt=0.0, stream=None):
+    lib = load()
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    per = np.ascontiguousarray([1 if p else 0 for p in periodic], dtype=np.int32)
+    nb = None if nblocks is None else np.ascontiguousarray(nblocks, dtype=np.int32)
+    h = ctypes.c_void_p()
+    st = None
+    if stream is not None:
+        st = stream if isinstance(stream, int) else stream.cuda_stream
+    code = lib.vg_create(ctypes.byref(h), int(dim), lo.ctypes.data, hi.ctypes.data, per.ctypes.data,
+                         None if nb is None else nb.ctypes.data, float(n_opt), st)
+    if code != VG_OK:
+        raise VgError(code, "vg_create failed")
+    return h
+
+
+def vg_insert(ctx, pos, radii=None):
+    p, dev = _ptr(pos)
+    r, rdev = _ptr(radii)
+    if radii is not None and rdev != dev:
+        raise ValueError("pos and radii must both be host or both device")
+    n = pos.shape[0]
+    _check(ctx, load().vg_insert(ctx, n, p, r, dev))
+
+
+def vg_compute(ctx, cfg: VgConfig | None = None):
+    _check(ctx, load().vg_compute(ctx, None if cfg is None else ctypes.byref(cfg)))
+
+
+def vg_get_counts(ctx):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx, load().vg_get_counts(ctx, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def vg_get_cells(ctx, vol=None, area=None, centroid=None, nv=None, ne=None, nf=None, status=None):
+    arrs = [vol, area, centroid, nv, ne, nf, status]
+    dev = {(_ptr(a)[1]) for a in arrs if a is not None}
+    if len(dev) > 1:
+        raise ValueError("outputs must all be host or all device")
+    on_dev = dev.pop() if dev else 0
+    _check(ctx, load().vg_get_cells(ctx, *[_ptr(a)[0] for a in arrs], on_dev))
+
+
+def vg_get_faces(ctx, face_off=None, nbr_id=None, nbr_img=None, face_order=None):
+    arrs = [face_off, nbr_id, nbr_img, face_order]
+    dev = {(_ptr(a)[1]) for a in arrs if a is not None}
+    on_dev = dev.pop() if dev else 0
+    _check(ctx, load().vg_get_faces(ctx, *[_ptr(a)[0] for a in arrs], on_dev))
+
+
+def vg_get_work(ctx, n_tested=None, n_vtests=None, n_cuts=None, n_retest=None, fallback=None):
+    arrs = [n_tested, n_vtests, n_cuts, n_retest, fallback]
+    dev = {(_ptr(a)[1]) for a in arrs if a is not None}
+    on_dev = dev.pop() if dev else 0
+    _check(ctx, load().vg_get_work(ctx, *[_ptr(a)[0] for a in arrs], on_dev))
+
+
+def vg_get_sorted(ctx, block_start=None, order=None):
+    nb = ctypes.c_int64()
+    arrs = [block_start, order]
+    dev = {(_ptr(a)[1]) for a in arrs if a is not None}
+    on_dev = dev.pop() if dev else 0
+    _check(ctx, load().vg_get_sorted(ctx, ctypes.byref(nb), *[_ptr(a)[0] for a in arrs], on_dev))
+    return nb.value
+
+
+def vg_get_grid(ctx, dim):
+    out = np.zeros(dim, dtype=np.int32)
+    _check(ctx, load().vg_get_grid(ctx, out.ctypes.data))
+    return tuple(int(v) for v in out)
+
+
+def vg_destroy(ctx):
+    if ctx:
+        load().vg_destroy(ctx)
+
+
+# ---- convenience: one call from host arrays to host results -------------------
+
+def compute_host(pos, lo, hi, periodic, radii=None, nblocks=None, n_opt=0.0, precision="fp32",
+                 order="prefetch", work=False, **cfg_kw) -> dict:
+    """Runs insert + compute on the current CUDA device from host numpy arrays
+    and returns host numpy results in the oracle's layout."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    n, d = pos.shape
+    ctx = vg_create(d, lo, hi, periodic, nblocks, n_opt)
+    try:
+        vg_insert(ctx, pos, None if radii is None else np.ascontiguousarray(radii, dtype=np.float64))
+        cfg = vg_config_default()
+        cfg.precision = VG_FP64 if precision == "fp64" else VG_FP32_RETEST
+        cfg.order = VG_WALK if order == "walk" else VG_PREFETCH
+        cfg.collect_stats = 1 if work else 0
+        for k, v in cfg_kw.items():
+            setattr(cfg, k, v)
+        vg_compute(ctx, cfg)
+        ncell, nface = vg_get_counts(ctx)
+        out = {
+            "vol": np.zeros(n), "area": np.zeros(n), "centroid": np.zeros((n, d)),
+            "nv": np.zeros(n, np.int32), "ne": np.zeros(n, np.int32), "nf": np.zeros(n, np.int32),
+            "status": np.zeros(n, np.uint8),
+        }
+        vg_get_cells(ctx, out["vol"], out["area"], out["centroid"], out["nv"], out["ne"], out["nf"],
+                     out["status"])
+        fo = np.zeros(n + 1, np.int64)
+        ids = np.zeros(max(nface, 1), np.int32)
+        img = np.zeros((max(nface, 1), 3), np.int8)
+        order_ = np.zeros(max(nface, 1), np.uint8)
+        vg_get_faces(ctx, fo, ids, img, order_)
+        out.update({"face_off": fo, "nbr_id": ids[:nface], "nbr_img": img[:nface, :d],
+                    "face_order": order_[:nface], "grid": vg_get_grid(ctx, d)})
+        if work:
+            w = {k: np.zeros(n, np.int32) for k in ("n_tested", "n_vtests", "n_cuts", "n_retest")}
+            fb = np.zeros(n, np.uint8)
+            vg_get_work(ctx, w["n_tested"], w["n_vtests"], w["n_cuts"], w["n_retest"], fb)
+            w["fallback"] = fb
+            out["work"] = w
+        return out
+    finally:
+        vg_destroy(ctx)

@@ -1,0 +1,88 @@
+"""Parity of the CUDA path with the FP64 oracle, element by element.
+
+Tolerances: topology (status, V/E/F, neighbour ids and images, face orders)
+bit-exact; volume, area and centroid within 1e-12 relative for the FP64
+form and 1e-5 for the FP32 form with FP64 re-test."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2209_11606_gb300 import workloads as W
+from tests.compare import compare
+
+pytestmark = pytest.mark.gpu
+
+FORMS = [("fp64", "walk", 1e-12), ("fp32", "walk", 1e-5), ("fp32", "prefetch", 1e-5)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_11606_gb300 import build
+    build.build()
+
+
+def run(s, nb, precision, order, **kw):
+    from paper_2209_11606_gb300 import vorogpu
+    return vorogpu.compute_host(s.pos, s.lo, s.hi, s.periodic, radii=s.radii, nblocks=nb,
+                                precision=precision, order=order, **kw)
+
+
+def check(s, nb, precision, order, rtol, method="grid"):
+    ref = oracle.compute(s.pos, s.lo, s.hi, s.periodic, radii=s.radii, method=method, nblocks=nb)
+    got = run(s, nb, precision, order)
+    rep = compare(got, ref, rtol)
+    assert rep["topology_ok"], rep
+    assert rep["values_ok"], rep
+    return got, ref, rep
+
+
+@pytest.mark.parametrize("precision,order,rtol", FORMS)
+def test_unit_cube_1000_walled(precision, order, rtol):
+    s = W.workload("unit1000")
+    check(s, (6, 6, 6), precision, order, rtol, method="brute")
+
+
+@pytest.mark.parametrize("precision,order,rtol", FORMS)
+def test_uniform_periodic(precision, order, rtol):
+    s = W.uniform(3000, 3, 3000 ** (1 / 3), True, seed=7)
+    check(s, (8, 8, 8), precision, order, rtol)
+
+
+@pytest.mark.parametrize("precision,order,rtol", FORMS)
+def test_mixed_periodicity_ragged_grid(precision, order, rtol):
+    s = W.uniform(2500, 3, 1.0, False, seed=8)
+    s.periodic = (True, False, True)
+    check(s, (7, 5, 6), precision, order, rtol)
+
+
+@pytest.mark.parametrize("precision,order,rtol", FORMS)
+def test_bcc_exact_lattice(precision, order, rtol):
+    s = W.bcc(4, 1.25)
+    got, _, _ = check(s, (4, 4, 4), precision, order, rtol)
+    assert np.all(got["nf"] == 14) and np.all(got["nv"] == 24)
+
+
+@pytest.mark.parametrize("precision,order,rtol", FORMS)
+def test_fcc_exact_lattice_degree4(precision, order, rtol):
+    s = W.fcc(3, 1.0)
+    got, _, _ = check(s, (3, 3, 3), precision, order, rtol)
+    assert np.all(got["nf"] == 12) and np.all(got["nv"] == 14) and np.all(got["ne"] == 24)
+
+
+@pytest.mark.parametrize("precision,order,rtol", FORMS)
+def test_perturbed_bcc(precision, order, rtol):
+    s = W.bcc(6, 1.25, 0.02, seed=2)
+    got, _, _ = check(s, (6, 6, 6), precision, order, rtol)
+    for i in range(s.n):
+        a, b = got["face_off"][i], got["face_off"][i + 1]
+        assert sorted(got["face_order"][a:b].tolist()) == [4] * 6 + [6] * 8
+
+
+@pytest.mark.parametrize("precision,order,rtol", FORMS)
+def test_tiny_systems(precision, order, rtol):
+    for n, per in ((1, True), (1, False), (2, False), (5, True)):
+        s = W.uniform(n, 3, 1.0, per, seed=10 + n)
+        check(s, (2, 2, 2), precision, order, rtol, method="brute")
