@@ -99,6 +99,8 @@ typedef struct {
     int chunk;         /* cells taken per work-queue ticket; <= 0: default */
     int warps_per_cta; /* <= 0: default */
     int collect_stats; /* 1 = fill the per-cell work counters */
+    int time_kernels;  /* 1 = record CUDA events around the cell kernels on the
+                          context's stream (read with vg_get_kernel_ms) */
 } vg_config;
 
 /* Fills `cfg` with the defaults listed above (FP32_RETEST, PREFETCH). */
@@ -163,11 +165,19 @@ vg_status vg_get_faces(vg_ctx *ctx, int64_t *face_off, int32_t *nbr_id, int8_t *
 /*
  * Per-cell work counters of the last vg_compute() with collect_stats = 1,
  * n entries each (any may be NULL): candidates offered to the cut routine,
- * vertex-plane tests, cuts that removed something, FP64 re-tests, and
- * whether the prefetch form fell back to the walk (0/1).
+ * vertex-plane tests, cuts that removed something, vertices those cuts
+ * created, FP64 re-tests, and whether the prefetch form fell back to the
+ * walk (0/1).
  */
 vg_status vg_get_work(vg_ctx *ctx, int32_t *n_tested, int32_t *n_vtests, int32_t *n_cuts,
-                      int32_t *n_retest, uint8_t *fallback, int on_device);
+                      int32_t *n_newv, int32_t *n_retest, uint8_t *fallback, int on_device);
+
+/*
+ * Device time of the cell-kernel phase of every vg_compute() made with
+ * time_kernels = 1 since the previous call of this function: the sum in
+ * milliseconds and the number of computes.  Synchronises the stream.
+ */
+vg_status vg_get_kernel_ms(vg_ctx *ctx, double *total_ms, int64_t *count);
 
 /*
  * The sorted container: block_start has B+1 entries (B = product of the
@@ -176,6 +186,10 @@ vg_status vg_get_work(vg_ctx *ctx, int32_t *n_tested, int32_t *n_vtests, int32_t
  */
 vg_status vg_get_sorted(vg_ctx *ctx, int64_t *n_blocks, int32_t *block_start, int32_t *order,
                         int on_device);
+
+/* Number of CUDA kernels this context has launched since vg_create()
+ * (diagnostics: lets a caller count the GPU work behind a call). */
+vg_status vg_get_launches(vg_ctx *ctx, int64_t *count);
 
 /* The block counts in use (after vg_insert() when the n_opt rule applies). */
 vg_status vg_get_grid(vg_ctx *ctx, int *nblocks);

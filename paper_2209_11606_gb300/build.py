@@ -25,8 +25,9 @@ def _nvcc() -> str:
 
 
 def _flags(extra=()):
+    env = os.environ.get("VG_NVCC_EXTRA", "").split()
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
-                   "-I", CSRC, "--expt-relaxed-constexpr"] + list(extra)
+                   "-I", CSRC, "--expt-relaxed-constexpr"] + env + list(extra)
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:

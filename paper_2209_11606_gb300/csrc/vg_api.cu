@@ -12,6 +12,10 @@
 
 using namespace vg;
 
+namespace vg {
+thread_local long long g_launch_count = 0;
+}
+
 namespace {
 
 vg_status fail(vg_ctx *c, vg_status s, const std::string &msg) {
@@ -158,6 +162,7 @@ void vg_config_default(vg_config *cfg) {
     cfg->chunk = 0;
     cfg->warps_per_cta = 0;
     cfg->collect_stats = 0;
+    cfg->time_kernels = 0;
 }
 
 vg_status vg_create(vg_ctx **out, int dim, const double *lo, const double *hi, const int *periodic,
@@ -246,6 +251,7 @@ vg_status vg_insert(vg_ctx *c, int64_t n, const double *pos, const double *radii
     VG_CUDA(ensure(c, c->d_w_vtests, n));
     VG_CUDA(ensure(c, c->d_w_cuts, n));
     VG_CUDA(ensure(c, c->d_w_retest, n));
+    VG_CUDA(ensure(c, c->d_w_newv, n));
     VG_CUDA(ensure(c, c->d_w_fallback, n));
     if (!on_device) {
         VG_CUDA(ensure(c, c->d_pos, n * d));
@@ -286,9 +292,11 @@ vg_status vg_insert(vg_ctx *c, int64_t n, const double *pos, const double *radii
         }
         for (int64_t i = 0; i < n; i++) if (src[i] > c->rmax) c->rmax = src[i];
     }
+    const long long l0 = g_launch_count;
     cudaError_t e = sort_particles(c->g, n, dpos, drad, c->d_key, c->d_slot, c->d_count, c->d_bstart,
                                    c->d_tmp, c->d_p32, c->d_p64, c->d_sid, c->d_sblk, c->d_err,
                                    c->d_scan, c->scan_bytes, c->stream);
+    c->launches += g_launch_count - l0;
     if (e != cudaSuccess) return cuda_fail(c, e, "sort_particles");
     int herr[2] = {0, 0};
     VG_CUDA(cudaMemcpyAsync(herr, c->d_err, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->stream));
@@ -309,6 +317,7 @@ vg_status vg_compute(vg_ctx *c, const vg_config *cfg_in) {
     if (!(cfg.tol32 > 0) || !(cfg.tau_rel > 0) || !(cfg.merge_rel > 0)) return fail(c, VG_ERR_ARG, "tolerances");
     if (cfg.use_mlp && !c->d_kblock) return fail(c, VG_ERR_STATE, "use_mlp without MLP predictions");
     const long long n = c->n;
+    const long long l0 = g_launch_count;
     // face buffer: start at 24 faces per cell, grow on overflow
     long long want = std::max<long long>(1024, n * 24);
     if (c->fcap < want) {
@@ -332,11 +341,17 @@ vg_status vg_compute(vg_ctx *c, const vg_config *cfg_in) {
         o.nv = c->d_nv; o.ne = c->d_ne; o.nf = c->d_nf; o.status = c->d_status;
         o.fptr = c->d_fptr; o.faces = c->d_faces; o.fcount = c->d_fcount; o.fcap = c->fcap;
         o.w_tested = c->d_w_tested; o.w_vtests = c->d_w_vtests; o.w_cuts = c->d_w_cuts;
-        o.w_retest = c->d_w_retest; o.w_fallback = c->d_w_fallback;
+        o.w_retest = c->d_w_retest; o.w_fallback = c->d_w_fallback; o.w_newv = c->d_w_newv;
         o.retry = c->d_caplist; o.retry_count = c->d_capcount;
         VG_CUDA(cudaMemsetAsync(c->d_fcount, 0, sizeof(unsigned long long), c->stream));
         VG_CUDA(cudaMemsetAsync(c->d_capcount, 0, sizeof(int), c->stream));
         cudaError_t e;
+        const bool timed = cfg.time_kernels && c->nev < vg_ctx::NEV;
+        if (timed) {
+            for (int k = 0; k < 2; k++)
+                if (!c->ev[2 * c->nev + k]) VG_CUDA(cudaEventCreate(&c->ev[2 * c->nev + k]));
+            VG_CUDA(cudaEventRecord(c->ev[2 * c->nev], c->stream));
+        }
         if (c->dim == 3) {
             e = launch_cells3(c->g, st, o, pp, off, cfg.precision, c->d_ticket, c->sm_count, cfg.warps_per_cta,
                               nullptr, (int)n, 0, c->stream);
@@ -351,6 +366,10 @@ vg_status vg_compute(vg_ctx *c, const vg_config *cfg_in) {
             e = launch_cells2(c->g, st, o, pp, off, cfg.precision, c->d_ticket + 1, c->sm_count, 0,
                               c->d_caplist, 0, 1, c->stream);
             if (e != cudaSuccess) return cuda_fail(c, e, "launch_cells2 (big cells)");
+        }
+        if (timed) {
+            VG_CUDA(cudaEventRecord(c->ev[2 * c->nev + 1], c->stream));
+            c->nev++;
         }
         unsigned long long used = 0;
         VG_CUDA(cudaMemcpyAsync(&used, c->d_fcount, sizeof used, cudaMemcpyDeviceToHost, c->stream));
@@ -372,6 +391,7 @@ vg_status vg_compute(vg_ctx *c, const vg_config *cfg_in) {
     VG_CUDA(ensure(c, c->d_ford, need_csr));
     cudaError_t e = compact_faces(n, c->d_nf, c->d_status, c->d_fptr, c->d_faces, c->d_face_off, c->d_nbr,
                                   c->d_img, c->d_ford, c->d_scan, c->stream);
+    c->launches += g_launch_count - l0;
     if (e != cudaSuccess) return cuda_fail(c, e, "compact_faces");
     c->computed = 1;
     c->total_faces = -1;
@@ -433,8 +453,23 @@ vg_status vg_get_faces(vg_ctx *c, int64_t *face_off, int32_t *nbr_id, int8_t *nb
     return VG_OK;
 }
 
-vg_status vg_get_work(vg_ctx *c, int32_t *n_tested, int32_t *n_vtests, int32_t *n_cuts, int32_t *n_retest,
-                      uint8_t *fallback, int on_device) {
+vg_status vg_get_kernel_ms(vg_ctx *c, double *total_ms, int64_t *count) {
+    if (!c || !total_ms || !count) return VG_ERR_ARG;
+    VG_CUDA(cudaStreamSynchronize(c->stream));
+    double t = 0;
+    for (int k = 0; k < c->nev; k++) {
+        float ms = 0;
+        VG_CUDA(cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]));
+        t += ms;
+    }
+    *total_ms = t;
+    *count = c->nev;
+    c->nev = 0;
+    return VG_OK;
+}
+
+vg_status vg_get_work(vg_ctx *c, int32_t *n_tested, int32_t *n_vtests, int32_t *n_cuts, int32_t *n_newv,
+                      int32_t *n_retest, uint8_t *fallback, int on_device) {
     if (!c) return VG_ERR_ARG;
     if (!c->computed) return fail(c, VG_ERR_STATE, "no computed cells");
     const long long n = c->n;
@@ -442,6 +477,7 @@ vg_status vg_get_work(vg_ctx *c, int32_t *n_tested, int32_t *n_vtests, int32_t *
     if ((s = copy_out(c, n_tested, c->d_w_tested, sizeof(int) * n, on_device))) return s;
     if ((s = copy_out(c, n_vtests, c->d_w_vtests, sizeof(int) * n, on_device))) return s;
     if ((s = copy_out(c, n_cuts, c->d_w_cuts, sizeof(int) * n, on_device))) return s;
+    if ((s = copy_out(c, n_newv, c->d_w_newv, sizeof(int) * n, on_device))) return s;
     if ((s = copy_out(c, n_retest, c->d_w_retest, sizeof(int) * n, on_device))) return s;
     if ((s = copy_out(c, fallback, c->d_w_fallback, n, on_device))) return s;
     return VG_OK;
@@ -454,6 +490,12 @@ vg_status vg_get_sorted(vg_ctx *c, int64_t *n_blocks, int32_t *block_start, int3
     vg_status s;
     if ((s = copy_out(c, block_start, c->d_bstart, sizeof(int) * (c->g.nblk + 1), on_device))) return s;
     if ((s = copy_out(c, order, c->d_sid, sizeof(int) * c->n, on_device))) return s;
+    return VG_OK;
+}
+
+vg_status vg_get_launches(vg_ctx *c, int64_t *count) {
+    if (!c || !count) return VG_ERR_ARG;
+    *count = c->launches;
     return VG_OK;
 }
 
@@ -476,7 +518,9 @@ void vg_destroy(vg_ctx *c) {
     release(c->d_ticket); release(c->d_face_off); release(c->d_nbr); release(c->d_img); release(c->d_ford);
     release(c->d_w_tested); release(c->d_w_vtests); release(c->d_w_cuts); release(c->d_w_retest);
     release(c->d_w_fallback); release(c->d_caplist); release(c->d_capcount);
-    release(c->d_off_code); release(c->d_off_lb); release(c->d_kblock);
+    release(c->d_off_code); release(c->d_off_lb); release(c->d_kblock); release(c->d_w_newv);
+    for (int k = 0; k < 2 * vg_ctx::NEV; k++)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     delete c;
 }
 

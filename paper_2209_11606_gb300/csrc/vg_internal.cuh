@@ -13,6 +13,9 @@ namespace vg {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Kernels launched by this host thread (every launch site increments it).
+extern thread_local long long g_launch_count;
+
 // FP64 position + radius, 32-byte aligned (one sector per particle).
 struct __align__(32) D4 {
     double x, y, z, w;
@@ -52,7 +55,7 @@ struct Out {
     unsigned long long *fcount;   // bump counter
     long long fcap;               // capacity of `faces`
     // optional work counters
-    int *w_tested, *w_vtests, *w_cuts, *w_retest;
+    int *w_tested, *w_vtests, *w_cuts, *w_newv, *w_retest;
     unsigned char *w_fallback;
     int *retry;                   // sorted indices of cells for the next tier
     int *retry_count;
@@ -153,6 +156,11 @@ struct vg_ctx {
     unsigned char *d_ford = nullptr;
     long long cap_faces_csr = 0;
     int *d_w_tested = nullptr, *d_w_vtests = nullptr, *d_w_cuts = nullptr, *d_w_retest = nullptr;
+    int *d_w_newv = nullptr;
+    // event pairs around the cell kernels (time_kernels)
+    static constexpr int NEV = 256;
+    cudaEvent_t ev[2 * NEV] = {};
+    int nev = 0;
     unsigned char *d_w_fallback = nullptr;
     int *d_caplist = nullptr, *d_capcount = nullptr;
     long long total_faces = -1;
@@ -161,6 +169,8 @@ struct vg_ctx {
     int *d_off_code = nullptr;
     float *d_off_lb = nullptr;
     int off_count = 0, off_shell = 0;
+
+    long long launches = 0;   // kernels launched by this context
 
     // MLP per-block predictions
     float *d_kblock = nullptr;

@@ -177,10 +177,12 @@ cudaError_t scan_rec(const TI *in, TO *out, long long n, char *tmp, cudaStream_t
     TO *sums_x = sums + (tiles + 1);
     char *next = (char *)(sums_x + (tiles + 1));
     next = (char *)(((uintptr_t)next + 255) & ~(uintptr_t)255);
+    ++g_launch_count;
     k_scan_tiles<TI, TO><<<(unsigned)tiles, SCAN_THREADS, 0, st>>>(in, out, n, sums);
     if (tiles > 1) {
         cudaError_t e = scan_rec<TO, TO>(sums, sums_x, tiles, next, st);
         if (e != cudaSuccess) return e;
+        ++g_launch_count;
         k_add_tile<TO><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, n, sums_x);
     }
     return cudaGetLastError();
@@ -222,11 +224,14 @@ cudaError_t sort_particles(const Grid &g, long long n, const double *pos, const 
     if ((e = cudaMemsetAsync(errflags, 0, sizeof(int) * 2, st)) != cudaSuccess) return e;
     const int T = 256;
     unsigned nbk = (unsigned)((n + T - 1) / T);
-    if (n > 0) k_index<<<nbk, T, 0, st>>>(g, n, pos, radii, key, slot, count, errflags);
+    if (n > 0) { ++g_launch_count; k_index<<<nbk, T, 0, st>>>(g, n, pos, radii, key, slot, count, errflags); }
     if ((e = exclusive_scan_i32(count, bstart, g.nblk, scan_tmp, st)) != cudaSuccess) return e;
+    ++g_launch_count;
     k_total<int, int><<<1, 1, 0, st>>>(count, bstart, g.nblk);
     if (n > 0) {
+        ++g_launch_count;
         k_scatter<<<nbk, T, 0, st>>>(n, key, slot, bstart, tmp_id);
+        ++g_launch_count;
         k_finalize<<<nbk, T, 0, st>>>(g, n, key, bstart, tmp_id, pos, radii, p32, p64, sid, sblk);
     }
     return cudaGetLastError();
@@ -271,11 +276,13 @@ cudaError_t compact_faces(long long n, const int *nf, const unsigned char *statu
     char *tmp = (char *)scan_tmp + (((size_t)n * sizeof(int) + 255) & ~(size_t)255);
     const int T = 256;
     unsigned nbk = (unsigned)((n + T - 1) / T);
-    if (n > 0) k_nf_ok<<<nbk, T, 0, st>>>(n, nf, status, nf_ok);
+    if (n > 0) { ++g_launch_count; k_nf_ok<<<nbk, T, 0, st>>>(n, nf, status, nf_ok); }
     cudaError_t e = scan_rec<int, long long>(nf_ok, face_off, n, tmp, st);
     if (e != cudaSuccess) return e;
+    ++g_launch_count;
     k_total<int, long long><<<1, 1, 0, st>>>(nf_ok, face_off, n);
     if (n > 0)
+        ++g_launch_count;
         k_compact<<<nbk, T, 0, st>>>(n, nf_ok, fptr, faces, face_off, nbr_id, nbr_img, face_order);
     return cudaGetLastError();
 }

@@ -26,6 +26,7 @@ VG_CELL_OK, VG_CELL_EMPTY, VG_CELL_CAP, VG_CELL_DUP, VG_CELL_LIMIT = 0, 1, 2, 3,
 
 EXPORTS = ["vg_config_default", "vg_create", "vg_insert", "vg_compute", "vg_get_counts",
            "vg_get_cells", "vg_get_faces", "vg_get_work", "vg_get_sorted", "vg_get_grid",
+           "vg_get_launches", "vg_get_kernel_ms",
            "vg_last_error", "vg_destroy"]
 
 
@@ -33,7 +34,8 @@ class VgConfig(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("order", ctypes.c_int), ("tol32", ctypes.c_double),
                 ("tau_rel", ctypes.c_double), ("merge_rel", ctypes.c_double),
                 ("prefetch_k", ctypes.c_int), ("use_mlp", ctypes.c_int), ("chunk", ctypes.c_int),
-                ("warps_per_cta", ctypes.c_int), ("collect_stats", ctypes.c_int)]
+                ("warps_per_cta", ctypes.c_int), ("collect_stats", ctypes.c_int),
+                ("time_kernels", ctypes.c_int)]
 
 
 class VgError(RuntimeError):
@@ -62,9 +64,11 @@ def load(path: str = LIB_PATH):
         "vg_get_counts": (I, [P, ctypes.POINTER(L), ctypes.POINTER(L)]),
         "vg_get_cells": (I, [P, P, P, P, P, P, P, P, I]),
         "vg_get_faces": (I, [P, P, P, P, P, I]),
-        "vg_get_work": (I, [P, P, P, P, P, P, I]),
+        "vg_get_work": (I, [P, P, P, P, P, P, P, I]),
+        "vg_get_kernel_ms": (I, [P, ctypes.POINTER(D), ctypes.POINTER(L)]),
         "vg_get_sorted": (I, [P, ctypes.POINTER(L), P, P, I]),
         "vg_get_grid": (I, [P, P]),
+        "vg_get_launches": (I, [P, ctypes.POINTER(L)]),
         "vg_last_error": (ctypes.c_char_p, [P]),
         "vg_destroy": (None, [P]),
     }
@@ -154,8 +158,9 @@ def vg_get_faces(ctx, face_off=None, nbr_id=None, nbr_img=None, face_order=None)
     _check(ctx, load().vg_get_faces(ctx, *[_ptr(a)[0] for a in arrs], on_dev))
 
 
-def vg_get_work(ctx, n_tested=None, n_vtests=None, n_cuts=None, n_retest=None, fallback=None):
-    arrs = [n_tested, n_vtests, n_cuts, n_retest, fallback]
+def vg_get_work(ctx, n_tested=None, n_vtests=None, n_cuts=None, n_newv=None, n_retest=None,
+                fallback=None):
+    arrs = [n_tested, n_vtests, n_cuts, n_newv, n_retest, fallback]
     dev = {(_ptr(a)[1]) for a in arrs if a is not None}
     on_dev = dev.pop() if dev else 0
     _check(ctx, load().vg_get_work(ctx, *[_ptr(a)[0] for a in arrs], on_dev))
@@ -174,6 +179,18 @@ def vg_get_grid(ctx, dim):
     out = np.zeros(dim, dtype=np.int32)
     _check(ctx, load().vg_get_grid(ctx, out.ctypes.data))
     return tuple(int(v) for v in out)
+
+
+def vg_get_kernel_ms(ctx):
+    t, c = ctypes.c_double(), ctypes.c_int64()
+    _check(ctx, load().vg_get_kernel_ms(ctx, ctypes.byref(t), ctypes.byref(c)))
+    return t.value, c.value
+
+
+def vg_get_launches(ctx):
+    v = ctypes.c_int64()
+    _check(ctx, load().vg_get_launches(ctx, ctypes.byref(v)))
+    return v.value
 
 
 def vg_destroy(ctx):
@@ -215,9 +232,9 @@ def compute_host(pos, lo, hi, periodic, radii=None, nblocks=None, n_opt=0.0, pre
         out.update({"face_off": fo, "nbr_id": ids[:nface], "nbr_img": img[:nface, :d],
                     "face_order": order_[:nface], "grid": vg_get_grid(ctx, d)})
         if work:
-            w = {k: np.zeros(n, np.int32) for k in ("n_tested", "n_vtests", "n_cuts", "n_retest")}
+            w = {k: np.zeros(n, np.int32) for k in ("n_tested", "n_vtests", "n_cuts", "n_newv", "n_retest")}
             fb = np.zeros(n, np.uint8)
-            vg_get_work(ctx, w["n_tested"], w["n_vtests"], w["n_cuts"], w["n_retest"], fb)
+            vg_get_work(ctx, w["n_tested"], w["n_vtests"], w["n_cuts"], w["n_newv"], w["n_retest"], fb)
             w["fallback"] = fb
             out["work"] = w
         return out
