@@ -194,6 +194,41 @@ vg_status vg_get_launches(vg_ctx *ctx, int64_t *count);
 /* The block counts in use (after vg_insert() when the n_opt rule applies). */
 vg_status vg_get_grid(vg_ctx *ctx, int *nblocks);
 
+/*
+ * Counting sort into blocks that allocates no device memory.  The paper has
+ * no counterpart: it is a variant of the sort inside vg_insert() for callers
+ * that must not allocate at call time -- for example a plugin whose host
+ * framework owns all device memory and forbids allocation on its execution
+ * path, a latency-critical loop that cannot absorb the device
+ * synchronisation cudaMalloc/cudaFree imply, or a process near its memory
+ * limit.  The sort's scratch (keys, slots, block counts) lives in one fixed
+ * __device__ array inside the library, about 13 MB, which every device that
+ * loads the library holds until the process exits.
+ *
+ *   dim, lo, hi, periodic, nblocks   the container, as in vg_create()
+ *   n, pos      n x dim doubles in DEVICE memory; n <= 1,048,576
+ *   block_start DEVICE output, B + 1 int32 (B = product of nblocks <= 262,144)
+ *   order       DEVICE output, n int32: input index of each particle in block
+ *               order, ascending input index inside a block -- the same
+ *               arrays vg_get_sorted() returns after vg_insert()
+ *   stream      cudaStream_t (NULL: default stream); the call synchronises it
+ *   errbuf      optional caller buffer of errlen bytes for a one-line reason
+ *
+ * Returns VG_ERR_ARG (with the reason in errbuf) when n or B exceeds the
+ * limits above, VG_ERR_OUT_OF_BOX / VG_ERR_NONFINITE as vg_insert() does,
+ * VG_ERR_CUDA on a CUDA failure.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.  The first call on each device looks up the device
+ * address of the scratch array (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls on a
+ * device share the one scratch array, so calls that overlap on the GPU (from
+ * two streams or two host threads) race and must be serialised by the
+ * caller.
+ */
+vg_status vg_sort_blocks_noalloc(int dim, const double *lo, const double *hi, const int *periodic,
+                                 const int *nblocks, int64_t n, const double *pos,
+                                 int32_t *block_start, int32_t *order, void *stream,
+                                 char *errbuf, int errlen);
+
 const char *vg_last_error(vg_ctx *ctx);
 void vg_destroy(vg_ctx *ctx);
 

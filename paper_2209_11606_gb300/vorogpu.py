@@ -26,7 +26,7 @@ VG_CELL_OK, VG_CELL_EMPTY, VG_CELL_CAP, VG_CELL_DUP, VG_CELL_LIMIT = 0, 1, 2, 3,
 
 EXPORTS = ["vg_config_default", "vg_create", "vg_insert", "vg_compute", "vg_get_counts",
            "vg_get_cells", "vg_get_faces", "vg_get_work", "vg_get_sorted", "vg_get_grid",
-           "vg_get_launches", "vg_get_kernel_ms",
+           "vg_get_launches", "vg_get_kernel_ms", "vg_sort_blocks_noalloc",
            "vg_last_error", "vg_destroy"]
 
 
@@ -69,6 +69,7 @@ def load(path: str = LIB_PATH):
         "vg_get_sorted": (I, [P, ctypes.POINTER(L), P, P, I]),
         "vg_get_grid": (I, [P, P]),
         "vg_get_launches": (I, [P, ctypes.POINTER(L)]),
+        "vg_sort_blocks_noalloc": (I, [I, P, P, P, P, L, P, P, P, P, ctypes.c_char_p, I]),
         "vg_last_error": (ctypes.c_char_p, [P]),
         "vg_destroy": (None, [P]),
     }
@@ -191,6 +192,28 @@ def vg_get_launches(ctx):
     v = ctypes.c_int64()
     _check(ctx, load().vg_get_launches(ctx, ctypes.byref(v)))
     return v.value
+
+
+def vg_sort_blocks_noalloc(dim, lo, hi, periodic, nblocks, pos, block_start, order, stream=None):
+    """Counting sort into blocks with no device allocation (see vorogpu.h):
+    `pos`, `block_start` and `order` are CUDA tensors; raises VgError with
+    the library's reason on failure."""
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    per = np.ascontiguousarray([1 if p else 0 for p in periodic], dtype=np.int32)
+    nb = np.ascontiguousarray(nblocks, dtype=np.int32)
+    for t in (pos, block_start, order):
+        if _ptr(t)[1] != 1:
+            raise ValueError("pos, block_start and order must be CUDA tensors")
+    st = None
+    if stream is not None:
+        st = stream if isinstance(stream, int) else stream.cuda_stream
+    buf = ctypes.create_string_buffer(256)
+    code = load().vg_sort_blocks_noalloc(int(dim), lo.ctypes.data, hi.ctypes.data, per.ctypes.data,
+                                         nb.ctypes.data, int(pos.shape[0]), pos.data_ptr(),
+                                         block_start.data_ptr(), order.data_ptr(), st, buf, 256)
+    if code != VG_OK:
+        raise VgError(code, buf.value.decode())
 
 
 def vg_destroy(ctx):
