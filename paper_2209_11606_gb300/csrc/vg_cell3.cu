@@ -19,7 +19,8 @@
 //   2. marks the directed edges of the removed triangles in a bit matrix; an
 //      edge (x, y) of a removed triangle whose twin (y, x) is unmarked borders
 //      the kept part and yields the new vertex (x, y, new plane);
-//   3. compacts kept and new vertices through shared memory with a warp scan.
+//   3. compacts kept and new vertices through shared memory with a warp scan
+//      and solves the new vertices one per lane.
 //
 // FP32 form: positions relative to the particle in FP32.  Each vertex carries
 // the condition number of its three planes; a vertex whose signed distance to
@@ -29,10 +30,15 @@
 // FP64 one, and FP64 runs only when a decision needs it.
 //
 // Candidate order: either the walk of Sec. 2.1.3 (blocks by ascending distance
-// bound) or a prefetch: the candidates inside a radius rho around the particle
-// are gathered from the block grid, sorted by distance and cut in that order;
-// the radius bound decides, and a cell whose bound still exceeds rho
-// continues with the walk, skipping what the prefetch already offered.
+// bound, 32 blocks set up in parallel per window) or a prefetch: the
+// candidates inside a radius rho around the particle are gathered from the
+// block grid, sorted by distance and cut in that order; the radius bound
+// decides, and a cell whose bound still exceeds rho continues with the walk,
+// skipping what the prefetch already offered.
+//
+// Warp-uniform bookkeeping (the candidate source, per-cell constants that
+// only cold paths read) lives in per-warp shared memory rather than in
+// registers, to keep the register file for the cell itself.
 #include "vg_internal.cuh"
 
 namespace vg {
@@ -42,11 +48,12 @@ constexpr unsigned TRI_EMPTY = 0xffffffffu;
 constexpr int KMAX = 128;         // prefetch list capacity
 constexpr int NRUN = 128;         // prefetch gather: runs of contiguous blocks
 constexpr int RGMAX = 3;          // prefetch gather: largest block reach per axis
+constexpr int NBIN = 8;           // prefetch: radial buckets
 constexpr float KAP0 = 4.0f;      // condition number covered by the base FP32 band
 constexpr float KAP_MAX2 = 1e8f;  // condition number^2 beyond which a new vertex is solved in FP64
 constexpr int MAX_SHELL_EXTRA = 4;
 #ifndef VG_MINB
-#define VG_MINB 1
+#define VG_MINB 4
 #endif
 
 template <typename T> struct V4T;
@@ -63,6 +70,30 @@ template <> __device__ __forceinline__ D4 mk4<double>(double x, double y, double
     return r;
 }
 
+// Per-cell constants read by the cold FP64 paths.
+struct CellC {
+    int i;        // sorted index
+    int self_id;  // input index
+    int b[3];     // home block
+    int pad;
+    double p[3];  // FP64 position
+    double rp;    // radius (radical) or 0
+};
+
+// Candidate source, warp-uniform.
+struct Src {
+    int mode;          // 0 prefetch list, 1 walk list, 2 walk shells, 3 done
+    int u, count;      // prefetch list cursor and length
+    int e;             // walk: next offset list entry
+    int shell, sidx;   // walk: Chebyshev shell and position in it
+    int vp, vtot;      // walk: particle cursor over the current window
+    int nwin;          // walk: blocks in the current window
+    int limit, fell_back;
+    int last;          // walk: the current window is the last one
+    float rho2;        // prefetch radius^2 (0: none)
+    int rg[3];         // prefetch reach in blocks per axis
+};
+
 template <typename T, int VPL, int MAXP>
 struct Smem {
     typename V4T<T>::t pl[MAXP];  // plane normal (x,y,z) and constant (w), cell frame
@@ -71,21 +102,29 @@ struct Smem {
     unsigned stri[32 * VPL];      // staging for compaction and statistics
     T sx[32 * VPL], sy[32 * VPL], sz[32 * VPL];
     float skap[32 * VPL];
-    union {
-        unsigned long long E[MAXP][MAXP / 64];  // removed directed edges of one cut
-        double dpos[32 * VPL][3];               // FP64 vertices (degenerate cells)
-    } u;
+    unsigned long long E[MAXP][MAXP / 64];  // removed directed edges of one cut
     union {
         unsigned char ftab[32][MAXP];  // face walk tables, one row per face of a round
         struct {
             int start[NRUN], j0[NRUN], oxb[NRUN], oyz[NRUN];
         } run;                         // prefetch gather: runs of contiguous blocks
+        struct {
+            int vstart[32], j0[32], o[32], m[32];
+        } win;                         // walk: a window of up to 32 blocks
     } w;
-    unsigned char sfirst[32];       // a triangle of each face of a round
-    int elist[32 * VPL];            // boundary edges (x | y << 8) of one cut
-    unsigned long long ckey[KMAX];  // prefetch keys
-    int cslot[KMAX];                // prefetch: sorted order of the key slots
-    int coid[KMAX];                 // prefetch: block offset of each key slot
+    union {
+        struct {
+            float4 q[KMAX];  // candidate position relative to the particle, |q|^2
+            int2 r[KMAX];    // sorted index and packed image
+            int slot[KMAX];  // sorted order of the slots
+        } pf;
+        double dpos[32 * VPL][3];  // FP64 vertices (degenerate cells)
+    } x;
+    unsigned char sfirst[32];  // a triangle of each face of a round
+    int elist[32 * VPL];       // boundary edges (x | y << 8) of one cut
+    CellC cc;
+    Src src;
+    int cnt[6];  // work counters
 };
 
 __device__ __forceinline__ int imgc(int img, int a) { return (int)(signed char)((img >> (8 * a)) & 0xff); }
@@ -175,22 +214,11 @@ __device__ __forceinline__ void bitonic(unsigned long long (&k)[E], int lane) {
     }
 }
 
-// Per-cell constants.
-struct CellIn {
-    int i;        // sorted index
-    int self_id;  // input index
-    int b[3];     // home block
-    float o[3];   // FP32 offset inside the home block
-    double p[3];  // FP64 position
-    double rp;    // radius (radical) or 0
-    float rp32;
-};
-
 // FP64 plane of a neighbour (sorted index `ref`, image `img`) or of a wall
 // (ref = -(1 + 2 axis + side)): the cell lies on n.r <= c, relative to p.
 // Same operation order as the oracle's: q = (x_j + m L) - x_p.
-__device__ __forceinline__ void plane64(const Grid &g, const Store &s, const CellIn &ci, int ref,
-                                        int img, double n[3], double &c) {
+__device__ __forceinline__ void plane64(const Grid &g, const Store &s, const CellC &ci, int ref, int img,
+                                        double n[3], double &c) {
     if (ref < 0) {
         int w = -ref - 1, a = w >> 1, side = w & 1;
         n[0] = n[1] = n[2] = 0.0;
@@ -224,13 +252,13 @@ __device__ __forceinline__ void solve3_d(const double n1[3], double c1, const do
 // ---- cold FP64 paths (out of line) ----------------------------------------------
 
 // FP64 position of the vertex with plane triple t.
-__device__ __noinline__ void vertex64(const Grid *g, const Store *st, CellIn ci, const int *pref,
+__device__ __noinline__ void vertex64(const Grid *g, const Store *st, const CellC *ci, const int *pref,
                                       const int *pimg, unsigned t, double *v) {
     double n1[3], n2[3], n3[3], c1, c2, c3;
     int a = tri_a(t), b = tri_b(t), c = tri_c(t);
-    plane64(*g, *st, ci, pref[a], pimg[a], n1, c1);
-    plane64(*g, *st, ci, pref[b], pimg[b], n2, c2);
-    plane64(*g, *st, ci, pref[c], pimg[c], n3, c3);
+    plane64(*g, *st, *ci, pref[a], pimg[a], n1, c1);
+    plane64(*g, *st, *ci, pref[b], pimg[b], n2, c2);
+    plane64(*g, *st, *ci, pref[c], pimg[c], n3, c3);
     double r[3];
     solve3_d(n1, c1, n2, c2, n3, c3, r);
     v[0] = r[0]; v[1] = r[1]; v[2] = r[2];
@@ -238,12 +266,12 @@ __device__ __noinline__ void vertex64(const Grid *g, const Store *st, CellIn ci,
 
 // FP64 classification of vertex t against the plane of neighbour (ref, img):
 // 1 outside, 0 on the plane (|d| <= tau_rel*s*|q|), -1 inside.
-__device__ __noinline__ int classify64(const Grid *g, const Store *st, CellIn ci, const int *pref,
+__device__ __noinline__ int classify64(const Grid *g, const Store *st, const CellC *ci, const int *pref,
                                        const int *pimg, unsigned t, int ref, int img, double tau_rel_s) {
     double v[3];
     vertex64(g, st, ci, pref, pimg, t, v);
     double q[3], cq;
-    plane64(*g, *st, ci, ref, img, q, cq);
+    plane64(*g, *st, *ci, ref, img, q, cq);
     double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
     double tau = tau_rel_s * qn;
     double d = __dsub_rn(__dadd_rn(__dadd_rn(__dmul_rn(q[0], v[0]), __dmul_rn(q[1], v[1])), __dmul_rn(q[2], v[2])), cq);
@@ -251,31 +279,31 @@ __device__ __noinline__ int classify64(const Grid *g, const Store *st, CellIn ci
 }
 
 // FP64 solve of the new vertex on planes x, y and the cutting plane.
-__device__ __noinline__ float3 solve_new64(const Grid *g, const Store *st, CellIn ci, const int *pref,
+__device__ __noinline__ float3 solve_new64(const Grid *g, const Store *st, const CellC *ci, const int *pref,
                                            const int *pimg, int x, int y, int ref, int img) {
     double n1[3], n2[3], n3[3], c1, c2, c3, v[3];
-    plane64(*g, *st, ci, pref[x], pimg[x], n1, c1);
-    plane64(*g, *st, ci, pref[y], pimg[y], n2, c2);
-    plane64(*g, *st, ci, ref, img, n3, c3);
+    plane64(*g, *st, *ci, pref[x], pimg[x], n1, c1);
+    plane64(*g, *st, *ci, pref[y], pimg[y], n2, c2);
+    plane64(*g, *st, *ci, ref, img, n3, c3);
     solve3_d(n1, c1, n2, c2, n3, c3, v);
     return make_float3((float)v[0], (float)v[1], (float)v[2]);
 }
 
 // ---- geometry of candidates ------------------------------------------------------
 
-// FP32 position of particle pj seen from the cell's particle through block
-// offset (ox, oy, oz); shared by the prefetch gather and the walk so that both
-// see bit-identical distances.
-__device__ __forceinline__ void cand32(const Grid &g, const CellIn &ci, float4 pj, int ox, int oy, int oz,
-                                       float &qx, float &qy, float &qz, float &qq) {
-    qx = __fadd_rn(__fmul_rn((float)ox, g.hf[0]), __fsub_rn(pj.x, ci.o[0]));
-    qy = __fadd_rn(__fmul_rn((float)oy, g.hf[1]), __fsub_rn(pj.y, ci.o[1]));
-    qz = __fadd_rn(__fmul_rn((float)oz, g.hf[2]), __fsub_rn(pj.z, ci.o[2]));
+// FP32 position of particle pj seen from the cell's particle (offset o0..o2
+// in its home block) through block offset (ox, oy, oz); shared by the
+// prefetch gather and the walk so that both see bit-identical distances.
+__device__ __forceinline__ void cand32(const Grid &g, float o0, float o1, float o2, float4 pj, int ox, int oy,
+                                       int oz, float &qx, float &qy, float &qz, float &qq) {
+    qx = __fadd_rn(__fmul_rn((float)ox, g.hf[0]), __fsub_rn(pj.x, o0));
+    qy = __fadd_rn(__fmul_rn((float)oy, g.hf[1]), __fsub_rn(pj.y, o1));
+    qz = __fadd_rn(__fmul_rn((float)oz, g.hf[2]), __fsub_rn(pj.z, o2));
     qq = __fadd_rn(__fadd_rn(__fmul_rn(qx, qx), __fmul_rn(qy, qy)), __fmul_rn(qz, qz));
 }
 
-__device__ __forceinline__ void cand64(const Grid &g, const CellIn &ci, D4 pj, int mx, int my, int mz,
-                                       double &qx, double &qy, double &qz, double &qq) {
+__device__ __forceinline__ void cand64(const Grid &g, const CellC &ci, D4 pj, int mx, int my, int mz, double &qx,
+                                       double &qy, double &qz, double &qq) {
     qx = __dsub_rn(__dadd_rn(pj.x, __dmul_rn((double)mx, g.L[0])), ci.p[0]);
     qy = __dsub_rn(__dadd_rn(pj.y, __dmul_rn((double)my, g.L[1])), ci.p[1]);
     qz = __dsub_rn(__dadd_rn(pj.z, __dmul_rn((double)mz, g.L[2])), ci.p[2]);
@@ -283,27 +311,27 @@ __device__ __forceinline__ void cand64(const Grid &g, const CellIn &ci, D4 pj, i
 }
 
 // Distance from the particle to the slab of block offset o along axis a, FP32.
-__device__ __forceinline__ float axis_gap(const Grid &g, const CellIn &ci, int a, int o) {
-    float lo = __fsub_rn(__fmul_rn((float)o, g.hf[a]), ci.o[a]);
+__device__ __forceinline__ float axis_gap(const Grid &g, float oa, int a, int o) {
+    float lo = __fsub_rn(__fmul_rn((float)o, g.hf[a]), oa);
     float hi = __fadd_rn(lo, g.hf[a]);
     return lo > 0.f ? lo : (hi < 0.f ? -hi : 0.f);
 }
-__device__ __forceinline__ float row_gap2(const Grid &g, const CellIn &ci, int oy, int oz) {
-    float gy = axis_gap(g, ci, 1, oy), gz = axis_gap(g, ci, 2, oz);
+__device__ __forceinline__ float row_gap2(const Grid &g, float o1, float o2, int oy, int oz) {
+    float gy = axis_gap(g, o1, 1, oy), gz = axis_gap(g, o2, 2, oz);
     return __fadd_rn(__fmul_rn(gy, gy), __fmul_rn(gz, gz));
 }
-__device__ __forceinline__ float block_gap2(const Grid &g, const CellIn &ci, int ox, int oy, int oz) {
-    float gx = axis_gap(g, ci, 0, ox);
-    return __fadd_rn(__fmul_rn(gx, gx), row_gap2(g, ci, oy, oz));
+__device__ __forceinline__ float block_gap2(const Grid &g, float o0, float o1, float o2, int ox, int oy, int oz) {
+    float gx = axis_gap(g, o0, 0, ox);
+    return __fadd_rn(__fmul_rn(gx, gx), row_gap2(g, o1, o2, oy, oz));
 }
 
 // Block offset o -> linear block index and image shift; false outside a wall.
-__device__ __forceinline__ bool resolve(const Grid &g, const CellIn &ci, int ox, int oy, int oz, int &k,
-                                        int &mx, int &my, int &mz) {
+__device__ __forceinline__ bool resolve(const Grid &g, const int *b, int ox, int oy, int oz, int &k, int &mx,
+                                        int &my, int &mz) {
     int o[3] = {ox, oy, oz}, t[3], m[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        int ta = ci.b[a] + o[a];
+        int ta = b[a] + o[a];
         m[a] = 0;
         if (g.per[a]) {
             m[a] = floordiv(ta, g.nb[a]);
@@ -321,10 +349,10 @@ __device__ __forceinline__ bool resolve(const Grid &g, const CellIn &ci, int ox,
 // ---- the kernel ------------------------------------------------------------------
 
 template <typename T, int VPL, int MAXP>
-__global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__ Grid g, const __grid_constant__ Store st,
-                                                const __grid_constant__ Out o, const __grid_constant__ Params pp,
-                                                const __grid_constant__ Offsets off, unsigned *ticket,
-                                                const int *cells, int ncells, int tier) {
+__global__ void __launch_bounds__(128, VG_MINB)
+    k_cells3(const __grid_constant__ Grid g, const __grid_constant__ Store st, const __grid_constant__ Out o,
+             const __grid_constant__ Params pp, const __grid_constant__ Offsets off, unsigned *ticket,
+             const int *cells, int ncells, int tier) {
     constexpr bool F32 = sizeof(T) == 4;
     constexpr int CAP = 32 * VPL;
     constexpr int NW = MAXP / 64;
@@ -333,17 +361,12 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
     extern __shared__ __align__(32) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     S_t &S = reinterpret_cast<S_t *>(smem_raw)[warp];
+    Src &src = S.src;
     // the edge matrix starts clear; every cut leaves it clear
-    for (int u = lane; u < MAXP * NW; u += 32) (&S.u.E[0][0])[u] = 0ull;
+    for (int u = lane; u < MAXP * NW; u += 32) (&S.E[0][0])[u] = 0ull;
     __syncwarp();
     const int total = cells ? (tier > 0 ? *o.retry_count : ncells) : st.n;
     const int chunk = pp.chunk > 0 ? pp.chunk : 1;
-    const double tau_rel_s = pp.tau_rel * g.s;
-    const float tol32 = (float)pp.tol32;
-    const float hmin = fminf(g.hf[0], fminf(g.hf[1], g.hf[2]));
-    const float lbmax = (float)off.shell * hmin;
-    const int maxs = off.shell + MAX_SHELL_EXTRA + 2 * max(g.nb[0], max(g.nb[1], g.nb[2]));
-    const T rmax2 = (T)(st.rmax * st.rmax);
 
     for (int iter = 0; iter < (1 << 30); iter++) {
         int base = 0;
@@ -354,48 +377,57 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
         for (int w = base; w < wend; w++) {
             const int i = cells ? cells[w] : w;
             // ---------------------------------------------------------- setup
-            CellIn ci;
-            ci.i = i;
-            ci.self_id = __ldg(&st.sid[i]);
             const int kh = __ldg(&st.sblk[i]);
-            ci.b[0] = kh % g.nb[0];
-            ci.b[1] = (kh / g.nb[0]) % g.nb[1];
-            ci.b[2] = kh / (g.nb[0] * g.nb[1]);
+            float o0, o1, o2, rp32;
             {
-                float4 p32 = __ldg(&st.p32[i]);
-                D4 p64 = st.p64[i];
-                ci.o[0] = p32.x; ci.o[1] = p32.y; ci.o[2] = p32.z;
-                ci.p[0] = p64.x; ci.p[1] = p64.y; ci.p[2] = p64.z;
-                ci.rp = p64.w;
-                ci.rp32 = p32.w;
+                const float4 p32 = __ldg(&st.p32[i]);
+                o0 = p32.x; o1 = p32.y; o2 = p32.z; rp32 = p32.w;
+                if (lane == 0) {
+                    const D4 p64 = st.p64[i];
+                    S.cc.i = i;
+                    S.cc.self_id = __ldg(&st.sid[i]);
+                    S.cc.b[0] = kh % g.nb[0];
+                    S.cc.b[1] = (kh / g.nb[0]) % g.nb[1];
+                    S.cc.b[2] = kh / (g.nb[0] * g.nb[1]);
+                    S.cc.p[0] = p64.x; S.cc.p[1] = p64.y; S.cc.p[2] = p64.z;
+                    S.cc.rp = p64.w;
+                }
+                if (pp.collect && lane < 6) S.cnt[lane] = 0;
             }
             // ------------------------------------- initial cell, Eqs. (1)-(2)
             unsigned tri[VPL];
             T vx[VPL], vy[VPL], vz[VPL];
             float kap[VPL];
             {
+                __syncwarp();
                 T lo[3], hi[3];
+                const float oo[3] = {o0, o1, o2};
 #pragma unroll
                 for (int a = 0; a < 3; a++) {
                     if (g.per[a]) {
-                        lo[a] = (T)(-0.5 * g.L[a]);
-                        hi[a] = (T)(0.5 * g.L[a]);
+                        if constexpr (F32) { lo[a] = -0.5f * g.Lf[a]; hi[a] = 0.5f * g.Lf[a]; }
+                        else { lo[a] = -0.5 * g.L[a]; hi[a] = 0.5 * g.L[a]; }
                     } else if constexpr (F32) {
-                        lo[a] = -((float)ci.b[a] * g.hf[a] + ci.o[a]);
-                        hi[a] = (float)(g.nb[a] - ci.b[a]) * g.hf[a] - ci.o[a];
+                        lo[a] = -((float)S.cc.b[a] * g.hf[a] + oo[a]);
+                        hi[a] = (float)(g.nb[a] - S.cc.b[a]) * g.hf[a] - oo[a];
                     } else {
-                        lo[a] = g.lo[a] - ci.p[a];
-                        hi[a] = g.hi[a] - ci.p[a];
+                        lo[a] = g.lo[a] - S.cc.p[a];
+                        hi[a] = g.hi[a] - S.cc.p[a];
                     }
                 }
                 if (lane < 6) {
-                    int a = lane >> 1, side = lane & 1;
+                    const int a = lane >> 1, side = lane & 1;
                     T n[3] = {0, 0, 0};
                     T c;
                     int ref, img;
                     if (g.per[a]) {
-                        n[a] = side ? (T)g.L[a] : -(T)g.L[a];
-                        c = (T)(0.5 * g.L[a] * g.L[a]);
+                        if constexpr (F32) {
+                            n[a] = side ? g.Lf[a] : -g.Lf[a];
+                            c = 0.5f * g.Lf[a] * g.Lf[a];
+                        } else {
+                            n[a] = side ? g.L[a] : -g.L[a];
+                            c = 0.5 * g.L[a] * g.L[a];
+                        }
                         ref = i;
                         img = pack_img(a == 0 ? (side ? 1 : -1) : 0, a == 1 ? (side ? 1 : -1) : 0,
                                        a == 2 ? (side ? 1 : -1) : 0);
@@ -416,43 +448,50 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
                     kap[s] = 1.f;
                 }
                 if (lane < 8) {
-                    int sx = lane & 1, sy = (lane >> 1) & 1, sz = (lane >> 2) & 1;
-                    int minus = (1 - sx) + (1 - sy) + (1 - sz);
-                    int A = sx, B = 2 + sy, C = 4 + sz;
+                    const int sx = lane & 1, sy = (lane >> 1) & 1, sz = (lane >> 2) & 1;
+                    const int minus = (1 - sx) + (1 - sy) + (1 - sz);
+                    const int A = sx, B = 2 + sy, C = 4 + sz;
                     tri[0] = (minus & 1) ? mk_tri(A, C, B) : mk_tri(A, B, C);
                     vx[0] = sx ? hi[0] : lo[0];
                     vy[0] = sy ? hi[1] : lo[1];
                     vz[0] = sz ? hi[2] : lo[2];
                 }
             }
-            int ntri = 8;
+            int ntri = 8;        // vertices
+            unsigned rows = 1;   // register slots (rows of 32) that hold any vertex
             unsigned long long live[NW];
 #pragma unroll
             for (int w2 = 0; w2 < NW; w2++) live[w2] = w2 == 0 ? 0x3full : 0ull;
             T r2 = warp_max_t(lane < 8 ? vx[0] * vx[0] + vy[0] * vy[0] + vz[0] * vz[0] : (T)0);
-            bool degen = false, fail = false, empty = false, dup = false;
-            int n_tested = 0, n_vtests = 0, n_cuts = 0, n_newv = 0, n_retest = 0;
-            __syncwarp();
+            // bit 0 degenerate, 1 capacity/consistency failure, 2 empty, 3 duplicate point
+            int flags = 0;
 
             // radius bound (Sec. 2.1.3), squared, with a small relative margin
             // that covers the rounding of R and of candidate distances
             auto stop2 = [&]() -> T {
                 const T margin = F32 ? (T)1.0001 : (T)(1.0 + 1e-12);
                 if (!st.radical) return (T)4 * r2 * margin;
-                T disc = r2 + rmax2 - (T)(ci.rp * ci.rp);
+                T disc = r2 + (T)(st.rmax * st.rmax) - (T)(S.cc.rp * S.cc.rp);
                 if (disc <= (T)0) return (T)0;
                 T rs = sqrt(r2) + sqrt(disc);
                 return rs * rs * margin;
             };
 
             // ----------------------------------------------- candidate source
-            // mode 0: sorted prefetch list; 1: walk over the offset list;
-            // 2: walk over Chebyshev shells beyond it; 3: done
-            int mode = 1;
-            float rho2 = 0.f;
-            int rg0 = 0, rg1 = 0, rg2 = 0;
-            int count = 0, u = 0;
-            int fell_back = 0;
+            src.mode = 1;
+            src.rho2 = 0.f;
+            src.rg[0] = src.rg[1] = src.rg[2] = 0;
+            src.count = 0;
+            src.u = 0;
+            src.e = 0;
+            src.shell = 1;
+            src.sidx = 0;
+            src.vp = 0;
+            src.vtot = 0;
+            src.nwin = 0;
+            src.limit = 0;
+            src.fell_back = 0;
+            src.last = 0;
             if constexpr (F32) {
                 if (pp.order == VG_PREFETCH && st.n < (1 << 27)) {
                     float kt = (float)(pp.prefetch_k > 0 ? pp.prefetch_k : 72);
@@ -461,16 +500,19 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
                     int n27 = 0, v27 = 0;
                     if (lane < 27) {
                         int kk, mx, my, mz;
-                        if (resolve(g, ci, lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1, kk, mx, my, mz)) {
+                        if (resolve(g, S.cc.b, lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1, kk, mx, my, mz)) {
                             n27 = __ldg(&st.bstart[kk + 1]) - __ldg(&st.bstart[kk]);
                             v27 = 1;
                         }
                     }
                     n27 = __reduce_add_sync(FULL, n27);
                     v27 = __reduce_add_sync(FULL, v27);
-                    float dens = (float)max(n27, 1) / ((float)max(v27, 1) * g.hf[0] * g.hf[1] * g.hf[2]);
+                    const float dens = (float)max(n27, 1) / ((float)max(v27, 1) * g.hf[0] * g.hf[1] * g.hf[2]);
                     float rho = cbrtf(3.f * kt / (4.f * 3.14159265f * dens));
+                    int count = 0;
                     bool give_up = false;
+                    float rho2 = 0.f;
+                    int rg0 = 0, rg1 = 0, rg2 = 0;
                     for (int attempt = 0; attempt < 6; attempt++) {
                         rho2 = rho * rho;
                         rg0 = (int)ceilf(rho / g.hf[0]);
@@ -481,45 +523,56 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
                         // 1. runs of contiguous blocks: rows along x (fixed oy, oz)
                         //    split where the x image shift changes; one row per lane
                         const int wy = 2 * rg1 + 1, nrows = wy * (2 * rg2 + 1);
+                        const int bx = S.cc.b[0];
                         int nrun = 0, npart = 0;
                         for (int r0 = 0; r0 < nrows; r0 += 32) {
                             const int r = r0 + lane;
-                            int oy = 0, oz = 0, krow = 0, ox = -rg0;
+                            int oy = 0, oz = 0, krow = 0, ox = 0, oxhi = -1;
                             bool rowok = false;
                             if (r < nrows) {
                                 oy = r % wy - rg1;
                                 oz = r / wy - rg2;
                                 int kk, mx, my, mz;
-                                rowok = row_gap2(g, ci, oy, oz) < rho2 && resolve(g, ci, 0, oy, oz, kk, mx, my, mz);
-                                krow = kk - ci.b[0];
-                                if (rowok && !g.per[0]) ox = max(-rg0, -ci.b[0]);
+                                rowok = row_gap2(g, o1, o2, oy, oz) < rho2 &&
+                                        resolve(g, S.cc.b, 0, oy, oz, kk, mx, my, mz);
+                                krow = kk - bx;
+                                if (rowok) {
+                                    // the blocks of the row within rho: an interval around 0
+                                    int lo = 0, hi = 0;
+                                    while (lo > -rg0 && block_gap2(g, o0, o1, o2, lo - 1, oy, oz) < rho2) lo--;
+                                    while (hi < rg0 && block_gap2(g, o0, o1, o2, hi + 1, oy, oz) < rho2) hi++;
+                                    if (!g.per[0]) { lo = max(lo, -bx); hi = min(hi, g.nb[0] - 1 - bx); }
+                                    ox = lo;
+                                    oxhi = hi;
+                                }
                             }
                             for (int k = 0; k <= 2 * RGMAX; k++) {
-                                bool have = rowok && ox <= rg0;
+                                bool have = rowok && ox <= oxhi;
                                 int xa = 0, xb = 0, m0 = 0;
                                 if (have) {
-                                    const int tx = ci.b[0] + ox;
+                                    const int tx = bx + ox;
                                     if (g.per[0]) {
                                         m0 = floordiv(tx, g.nb[0]);
                                         xa = tx - m0 * g.nb[0];
-                                        xb = min(g.nb[0] - 1, xa + (rg0 - ox));
-                                    } else if (tx >= g.nb[0]) {
-                                        have = false;
+                                        xb = min(g.nb[0] - 1, xa + (oxhi - ox));
                                     } else {
                                         xa = tx;
-                                        xb = min(g.nb[0] - 1, ci.b[0] + rg0);
+                                        xb = bx + oxhi;
                                     }
                                 }
-                                unsigned hb = __ballot_sync(FULL, have);
+                                const unsigned hb = __ballot_sync(FULL, have);
                                 if (!hb) break;
-                                int len = 0;
-                                if (have) len = __ldg(&st.bstart[krow + xb + 1]) - __ldg(&st.bstart[krow + xa]);
+                                int len = 0, j0r = 0;
+                                if (have) {
+                                    j0r = __ldg(&st.bstart[krow + xa]);
+                                    len = __ldg(&st.bstart[krow + xb + 1]) - j0r;
+                                }
                                 int ltot;
                                 const int lex = warp_excl_scan(len, lane, ltot);
                                 const int slot = nrun + __popc(hb & ((1u << lane) - 1));
                                 if (have && slot < NRUN) {
                                     S.w.run.start[slot] = npart + lex;
-                                    S.w.run.j0[slot] = __ldg(&st.bstart[krow + xa]);
+                                    S.w.run.j0[slot] = j0r;
                                     // x offset of a particle = oxb + its block index
                                     S.w.run.oxb[slot] = (ox - xa) - krow;
                                     S.w.run.oyz[slot] = (oy + 64) | ((oz + 64) << 8);
@@ -535,29 +588,32 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
                         for (int v0 = 0; v0 < npart; v0 += 32) {
                             const int v = v0 + lane;
                             bool keep = false;
-                            float qq = 0.f;
-                            int j = 0, oid = 0;
+                            float qx = 0.f, qy = 0.f, qz = 0.f, qq = 0.f;
+                            int j = 0, img = 0;
                             if (v < npart) {
                                 int lo = 0, hi = nrun - 1;  // last run with start <= v
                                 while (lo < hi) {
-                                    int mid = (lo + hi + 1) >> 1;
+                                    const int mid = (lo + hi + 1) >> 1;
                                     if (S.w.run.start[mid] <= v) lo = mid; else hi = mid - 1;
                                 }
                                 j = S.w.run.j0[lo] + (v - S.w.run.start[lo]);
                                 const int oyz = S.w.run.oyz[lo];
                                 const int oy = (oyz & 0xff) - 64, oz = ((oyz >> 8) & 0xff) - 64;
                                 const int oxj = S.w.run.oxb[lo] + __ldg(&st.sblk[j]);
-                                float4 pj = __ldg(&st.p32[j]);
-                                float qx, qy, qz;
-                                cand32(g, ci, pj, oxj, oy, oz, qx, qy, qz, qq);
+                                const float4 pj = __ldg(&st.p32[j]);
+                                cand32(g, o0, o1, o2, pj, oxj, oy, oz, qx, qy, qz, qq);
                                 keep = qq < rho2 && !(j == i && oxj == 0 && oy == 0 && oz == 0);
-                                oid = (oxj + 63) | ((oy + 63) << 7) | ((oz + 63) << 14);
+                                if (keep) {
+                                    int kk, mx, my, mz;
+                                    resolve(g, S.cc.b, oxj, oy, oz, kk, mx, my, mz);
+                                    img = pack_img(mx, my, mz);
+                                }
                             }
                             const unsigned bal = __ballot_sync(FULL, keep);
                             const int pos = count + __popc(bal & ((1u << lane) - 1));
                             if (keep && pos < KMAX) {
-                                S.ckey[pos] = ((unsigned long long)__float_as_uint(qq) << 32) | (unsigned)j;
-                                S.coid[pos] = oid;
+                                S.x.pf.q[pos] = make_float4(qx, qy, qz, qq);
+                                S.x.pf.r[pos] = make_int2(j, img);
                             }
                             count += __popc(bal);
                         }
@@ -565,178 +621,223 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
                         if (count <= KMAX) break;
                         rho *= 0.8f * cbrtf((float)KMAX / (float)count);
                     }
-                    if (give_up) count = KMAX + 1;
-                    __syncwarp();
-                    if (count <= KMAX) {
-                        // sort the slots by (distance^2, slot); the gather order
-                        // is deterministic, so ties keep a fixed order
-                        if (count <= 64) {
-                            unsigned long long kk2[2];
+                    if (!give_up && count <= KMAX) {
+                        // order by radial bucket: NBIN shells of equal volume inside
+                        // rho (about equal counts); inside a bucket the gather order,
+                        // which is deterministic, is kept
+                        const float irho2 = 1.f / rho2;
+                        int bin[KMAX / 32];
 #pragma unroll
-                            for (int e2 = 0; e2 < 2; e2++) {
-                                int slot = lane * 2 + e2;
-                                kk2[e2] = slot < count ? ((S.ckey[slot] & 0xffffffff00000000ull) | (unsigned)slot) : ~0ull;
-                            }
-                            bitonic<2>(kk2, lane);
-#pragma unroll
-                            for (int e2 = 0; e2 < 2; e2++) {
-                                int pos = lane * 2 + e2;
-                                if (pos < count) S.cslot[pos] = (int)(kk2[e2] & 0xffffffffu);
-                            }
-                        } else {
-                            unsigned long long kk4[4];
-#pragma unroll
-                            for (int e2 = 0; e2 < 4; e2++) {
-                                int slot = lane * 4 + e2;
-                                kk4[e2] = slot < count ? ((S.ckey[slot] & 0xffffffff00000000ull) | (unsigned)slot) : ~0ull;
-                            }
-                            bitonic<4>(kk4, lane);
-#pragma unroll
-                            for (int e2 = 0; e2 < 4; e2++) {
-                                int pos = lane * 4 + e2;
-                                if (pos < count) S.cslot[pos] = (int)(kk4[e2] & 0xffffffffu);
+                        for (int e2 = 0; e2 < KMAX / 32; e2++) {
+                            const int slot = e2 * 32 + lane;
+                            bin[e2] = NBIN;
+                            if (slot < count) {
+                                const float t = fminf(S.x.pf.q[slot].w * irho2, 1.f);
+                                bin[e2] = min(NBIN - 1, (int)((float)NBIN * t * sqrtf(t)));
                             }
                         }
-                        __syncwarp();
-                        mode = 0;
-                    } else {
-                        rho2 = 0.f;  // prefetch abandoned: plain walk
-                        count = 0;
+                        int pos0 = 0;
+                        for (int b = 0; b < NBIN; b++) {
+#pragma unroll
+                            for (int e2 = 0; e2 < KMAX / 32; e2++) {
+                                const unsigned m = __ballot_sync(FULL, bin[e2] == b);
+                                if (bin[e2] == b) S.x.pf.slot[pos0 + __popc(m & ((1u << lane) - 1))] = e2 * 32 + lane;
+                                pos0 += __popc(m);
+                            }
+                        }
+                        src.mode = 0;
+                        src.count = count;
+                        src.rho2 = rho2;
+                        src.rg[0] = rg0; src.rg[1] = rg1; src.rg[2] = rg2;
                     }
+                    __syncwarp();
                 }
             }
-            int e = 0;                // offset list position
-            int shell = 1, sidx = 0;  // shell enumeration
-            int jb = 0, j1 = 0;       // particles of the current block
-            int bo0 = 0, bo1 = 0, bo2 = 0, bm0 = 0, bm1 = 0, bm2 = 0;
-            bool binpref = false, bself = false;
             unsigned want = 0;
             T cqx = 0, cqy = 0, cqz = 0, cqq = 0, crj = 0;
             int cref = 0, cimg = 0;
-            int limit = 0;
             T stop = stop2();
 
             for (int guard = 0; guard < (1 << 30); guard++) {
                 // ---------------------------------- refill the candidate batch
-                while (want == 0 && mode != 3) {
+                while (want == 0) {
+                    const int mode = src.mode;
+                    if (mode == 3) break;
                     if (mode == 0) {
+                        const int u = src.u, count = src.count;
                         if (u >= count) {
-                            if ((T)stop <= (T)rho2 * (T)0.9999) mode = 3;
-                            else { mode = 1; fell_back = 1; }
+                            if ((T)stop <= (T)src.rho2 * (T)0.9999) src.mode = 3;
+                            else { src.mode = 1; src.fell_back = 1; }
                             continue;
                         }
-                        int idx = u + lane;
-                        bool in = idx < count, ok = false;
+                        const int idx = u + lane;
+                        const bool in = idx < count;
+                        bool ok = false;
                         if (in) {
-                            int slot = S.cslot[idx];
-                            unsigned long long key = S.ckey[slot];
-                            int j = (int)(key & 0xffffffffu);
-                            int oid = S.coid[slot];
-                            int ox = (oid & 127) - 63, oy = ((oid >> 7) & 127) - 63, oz = ((oid >> 14) & 127) - 63;
-                            float4 pj = __ldg(&st.p32[j]);
-                            float qx, qy, qz, qq;
-                            cand32(g, ci, pj, ox, oy, oz, qx, qy, qz, qq);
-                            int kk, mx, my, mz;
-                            resolve(g, ci, ox, oy, oz, kk, mx, my, mz);
-                            cqx = (T)qx; cqy = (T)qy; cqz = (T)qz; cqq = (T)qq; crj = (T)pj.w;
-                            cref = j;
-                            cimg = pack_img(mx, my, mz);
-                            ok = (T)qq < stop;
+                            const int slot = S.x.pf.slot[idx];
+                            const float4 q4 = S.x.pf.q[slot];
+                            const int2 r = S.x.pf.r[slot];
+                            cqx = (T)q4.x; cqy = (T)q4.y; cqz = (T)q4.z; cqq = (T)q4.w;
+                            cref = r.x;
+                            cimg = r.y;
+                            crj = st.radical ? (T)__ldg(&st.p32[r.x]).w : (T)0;
+                            ok = (T)q4.w < stop;
                         }
                         want = __ballot_sync(FULL, ok);
-                        // sorted: the first candidate at the bound ends the list
-                        if (want != __ballot_sync(FULL, in)) u = count;
-                        else u += 32;
+                        // bucketed: once the last entry's bucket starts beyond the
+                        // bound, every later entry lies beyond it too
+                        const int last = min(count - u, 32) - 1;
+                        const float qlast = __shfl_sync(FULL, (float)cqq, last);
+                        const float t = fminf(qlast / src.rho2, 1.f);
+                        const int bl = min(NBIN - 1, (int)((float)NBIN * t * sqrtf(t)));
+                        const float f = (float)bl / (float)NBIN;
+                        const float lb2 = src.rho2 * cbrtf(f * f) * 0.9999f;  // margin for rounding
+                        src.u = ((T)lb2 >= stop) ? count : u + 32;
                         continue;
                     }
-                    if (jb < j1) {
-                        int j = jb + lane;
+                    const int vp = src.vp, vtot = src.vtot;
+                    if (vp < vtot) {
+                        // a batch of the current window's particles
+                        const int v = vp + lane;
                         bool ok = false;
-                        if (j < j1) {
+                        if (v < vtot) {
+                            int lo = 0, hi = src.nwin - 1;  // last block with vstart <= v
+                            while (lo < hi) {
+                                const int mid = (lo + hi + 1) >> 1;
+                                if (S.w.win.vstart[mid] <= v) lo = mid; else hi = mid - 1;
+                            }
+                            const int j = S.w.win.j0[lo] + (v - S.w.win.vstart[lo]);
+                            const int oc = S.w.win.o[lo], mc = S.w.win.m[lo];
+                            const int ox = imgc(oc, 0), oy = imgc(oc, 1), oz = imgc(oc, 2);
                             if constexpr (F32) {
-                                float4 pj = __ldg(&st.p32[j]);
+                                const float4 pj = __ldg(&st.p32[j]);
                                 float qx, qy, qz, qq;
-                                cand32(g, ci, pj, bo0, bo1, bo2, qx, qy, qz, qq);
+                                cand32(g, o0, o1, o2, pj, ox, oy, oz, qx, qy, qz, qq);
                                 cqx = qx; cqy = qy; cqz = qz; cqq = qq; crj = pj.w;
-                                ok = !(binpref && qq < rho2);
+                                // bit 24 of the packed offset: inside the prefetch box
+                                ok = !(((oc >> 24) & 1) && qq < src.rho2);
                             } else {
-                                D4 pj = st.p64[j];
-                                cand64(g, ci, pj, bm0, bm1, bm2, cqx, cqy, cqz, cqq);
+                                const D4 pj = st.p64[j];
+                                cand64(g, S.cc, pj, imgc(mc, 0), imgc(mc, 1), imgc(mc, 2), cqx, cqy, cqz, cqq);
                                 crj = pj.w;
                                 ok = true;
                             }
-                            if (bself && j == i) ok = false;
+                            if (ox == 0 && oy == 0 && oz == 0 && j == i) ok = false;
                             ok = ok && cqq < stop;
                             cref = j;
-                            cimg = pack_img(bm0, bm1, bm2);
+                            cimg = mc & 0xffffff;
                         }
                         want = __ballot_sync(FULL, ok);
-                        jb += 32;
+                        src.vp = vp + 32;
                         continue;
                     }
-                    // next block
-                    int ox, oy, oz;
+                    // a new window: up to 32 blocks set up in parallel
+                    if (src.last) { src.mode = 3; continue; }
+                    int ox = 0, oy = 0, oz = 0;
+                    bool cand = false;
                     if (mode == 1) {
-                        if (e >= off.count) { mode = 2; continue; }
-                        float lb = __ldg(&off.lb[e]);
-                        if ((T)(lb * lb) * (T)0.99998 >= stop) { mode = 3; continue; }
-                        int code = __ldg(&off.code[e]);
-                        e++;
-                        ox = imgc(code, 0); oy = imgc(code, 1); oz = imgc(code, 2);
+                        const int e = src.e;
+                        if (e >= off.count) { src.mode = 2; continue; }
+                        const int ei = e + lane;
+                        bool beyond = true;
+                        if (ei < off.count) {
+                            const float lb = __ldg(&off.lb[ei]);
+                            beyond = (T)(lb * lb) * (T)0.99998 >= stop;
+                            const int code = __ldg(&off.code[ei]);
+                            ox = imgc(code, 0); oy = imgc(code, 1); oz = imgc(code, 2);
+                        }
+                        // the list is sorted by its bound: entries past the first
+                        // one beyond the stop radius are all beyond it
+                        const unsigned bb = __ballot_sync(FULL, beyond);
+                        const int first = bb ? __ffs(bb) - 1 : 32;
+                        cand = lane < first;
+                        if (first < 32 && e + first < off.count) src.last = 1;
+                        src.e = e + 32;
                     } else {
-                        float sb = (float)(shell - 1) * hmin;
-                        if ((T)(sb * sb) * (T)0.99998 >= stop) { mode = 3; continue; }
-                        if (shell > maxs) { limit = 1; mode = 3; continue; }
-                        int wd = 2 * shell + 1;
-                        if (sidx >= wd * wd * wd) { shell++; sidx = 0; continue; }
-                        ox = sidx % wd - shell;
-                        oy = (sidx / wd) % wd - shell;
-                        oz = sidx / (wd * wd) - shell;
-                        sidx++;
-                        if (max(abs(ox), max(abs(oy), abs(oz))) != shell) continue;
-                        float lbx = fmaxf(0.f, (float)(abs(ox) - 1)) * g.hf[0];
-                        float lby = fmaxf(0.f, (float)(abs(oy) - 1)) * g.hf[1];
-                        float lbz = fmaxf(0.f, (float)(abs(oz) - 1)) * g.hf[2];
-                        if (lbx * lbx + lby * lby + lbz * lbz < lbmax * lbmax) continue;  // held by the list
+                        const int shell = src.shell;
+                        const float hmin = fminf(g.hf[0], fminf(g.hf[1], g.hf[2]));
+                        const float sb = (float)(shell - 1) * hmin;
+                        if ((T)(sb * sb) * (T)0.99998 >= stop) { src.mode = 3; continue; }
+                        const int maxs = off.shell + MAX_SHELL_EXTRA + 2 * max(g.nb[0], max(g.nb[1], g.nb[2]));
+                        if (shell > maxs) { src.limit = 1; src.mode = 3; continue; }
+                        const int wd = 2 * shell + 1, sidx = src.sidx;
+                        if (sidx >= wd * wd * wd) { src.shell = shell + 1; src.sidx = 0; continue; }
+                        const int si = sidx + lane;
+                        if (si < wd * wd * wd) {
+                            ox = si % wd - shell;
+                            oy = (si / wd) % wd - shell;
+                            oz = si / (wd * wd) - shell;
+                            const float lbmax = (float)off.shell * hmin;
+                            const float lbx = fmaxf(0.f, (float)(abs(ox) - 1)) * g.hf[0];
+                            const float lby = fmaxf(0.f, (float)(abs(oy) - 1)) * g.hf[1];
+                            const float lbz = fmaxf(0.f, (float)(abs(oz) - 1)) * g.hf[2];
+                            // shell members that the offset list did not hold
+                            cand = max(abs(ox), max(abs(oy), abs(oz))) == shell &&
+                                   !(lbx * lbx + lby * lby + lbz * lbz < lbmax * lbmax);
+                        }
+                        src.sidx = sidx + 32;
                     }
-                    int kk, mx, my, mz;
-                    if (!resolve(g, ci, ox, oy, oz, kk, mx, my, mz)) continue;
-                    float gap2 = block_gap2(g, ci, ox, oy, oz);
-                    if ((T)gap2 * (T)0.99998 >= stop) continue;
-                    // particles the prefetch already offered: inside its block
-                    // box, in a row it gathered, and closer than its radius
-                    binpref = rho2 > 0.f && abs(ox) <= rg0 && abs(oy) <= rg1 && abs(oz) <= rg2 &&
-                              row_gap2(g, ci, oy, oz) < rho2;
-                    bself = ox == 0 && oy == 0 && oz == 0;
-                    bo0 = ox; bo1 = oy; bo2 = oz;
-                    bm0 = mx; bm1 = my; bm2 = mz;
-                    jb = __ldg(&st.bstart[kk]);
-                    j1 = __ldg(&st.bstart[kk + 1]);
+                    int kk = 0, mx = 0, my = 0, mz = 0, len = 0, j0b = 0, inpref = 0;
+                    if (cand) {
+                        cand = resolve(g, S.cc.b, ox, oy, oz, kk, mx, my, mz);
+                        if (cand) {
+                            const float gap2 = block_gap2(g, o0, o1, o2, ox, oy, oz);
+                            cand = !((T)gap2 * (T)0.99998 >= stop);
+                        }
+                        if (cand) {
+                            j0b = __ldg(&st.bstart[kk]);
+                            len = __ldg(&st.bstart[kk + 1]) - j0b;
+                            cand = len > 0;
+                            // particles the prefetch already offered: inside its
+                            // block box, in a row it gathered, closer than its radius
+                            const float rho2 = src.rho2;
+                            inpref = rho2 > 0.f && abs(ox) <= src.rg[0] && abs(oy) <= src.rg[1] &&
+                                     abs(oz) <= src.rg[2] && row_gap2(g, o1, o2, oy, oz) < rho2 &&
+                                     block_gap2(g, o0, o1, o2, ox, oy, oz) < rho2;
+                        }
+                    }
+                    const unsigned cb = __ballot_sync(FULL, cand);
+                    int ltot;
+                    const int lex = warp_excl_scan(cand ? len : 0, lane, ltot);
+                    if (cand) {
+                        const int slot = __popc(cb & ((1u << lane) - 1));
+                        S.w.win.vstart[slot] = lex;
+                        S.w.win.j0[slot] = j0b;
+                        S.w.win.o[slot] = pack_img(ox, oy, oz) | (inpref << 24);
+                        S.w.win.m[slot] = pack_img(mx, my, mz);
+                    }
+                    src.nwin = __popc(cb);
+                    src.vp = 0;
+                    src.vtot = ltot;
+                    __syncwarp();
                 }
                 if (want == 0) break;
-                const int src = __ffs(want) - 1;
+                const int srcl = __ffs(want) - 1;
                 want &= want - 1;
-                const T qx = __shfl_sync(FULL, cqx, src), qy = __shfl_sync(FULL, cqy, src);
-                const T qz = __shfl_sync(FULL, cqz, src), qq = __shfl_sync(FULL, cqq, src);
-                const T rj = __shfl_sync(FULL, crj, src);
-                const int ref = __shfl_sync(FULL, cref, src), img = __shfl_sync(FULL, cimg, src);
+                const T qx = __shfl_sync(FULL, cqx, srcl), qy = __shfl_sync(FULL, cqy, srcl);
+                const T qz = __shfl_sync(FULL, cqz, srcl), qq = __shfl_sync(FULL, cqq, srcl);
+                const int ref = __shfl_sync(FULL, cref, srcl), img = __shfl_sync(FULL, cimg, srcl);
                 if (qq >= stop) continue;
-                if (qq < (T)1e-30) { dup = true; continue; }
+                if (qq < (T)1e-30) { flags |= 8; continue; }
                 T c;
-                if constexpr (F32) c = 0.5f * (qq + ci.rp32 * ci.rp32 - rj * rj);
-                else c = 0.5 * (qq + ci.rp * ci.rp - rj * rj);
+                if (st.radical) {
+                    const T rj = __shfl_sync(FULL, crj, srcl);
+                    if constexpr (F32) c = 0.5f * (qq + rp32 * rp32 - rj * rj);
+                    else c = 0.5 * (qq + S.cc.rp * S.cc.rp - rj * rj);
+                } else {
+                    c = (T)0.5 * qq;
+                }
 
                 // ================================= cut by the plane q.r = c
-                n_tested++;
-                n_vtests += ntri;
+                if (pp.collect && lane == 0) { S.cnt[0]++; S.cnt[1] += ntri; }
                 T tau;
-                if constexpr (F32) tau = tol32 * sqrtf(r2 * qq);
-                else tau = (T)(tau_rel_s * sqrt((double)qq));
+                if constexpr (F32) tau = (float)pp.tol32 * sqrtf(r2 * qq);
+                else tau = (T)(pp.tau_rel * g.s * sqrt((double)qq));
                 unsigned outm = 0, nearm = 0, onm = 0;
 #pragma unroll
                 for (int s = 0; s < VPL; s++) {
-                    if (s * 32 < ntri) {
-                        T d = vx[s] * qx + vy[s] * qy + vz[s] * qz - c;
+                    if ((rows >> s) & 1) {
+                        const T d = vx[s] * qx + vy[s] * qy + vz[s] * qz - c;
                         T band = tau;
                         if constexpr (F32) band = tau * kap[s];
                         if (tri[s] != TRI_EMPTY) {
@@ -750,11 +851,12 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
                 }
                 if constexpr (F32) {
                     if (__any_sync(FULL, nearm)) {
-                        n_retest++;
+                        if (pp.collect && lane == 0) S.cnt[4]++;
 #pragma unroll
                         for (int s = 0; s < VPL; s++) {
                             if (nearm & (1u << s)) {
-                                int r = classify64(&g, &st, ci, S.pref, S.pimg, tri[s], ref, img, tau_rel_s);
+                                const int r = classify64(&g, &st, &S.cc, S.pref, S.pimg, tri[s], ref, img,
+                                                         pp.tau_rel * g.s);
                                 if (r > 0) outm |= 1u << s;
                                 else if (r == 0) onm |= 1u << s;
                             }
@@ -762,21 +864,21 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
                     }
                 }
                 if (!__any_sync(FULL, outm)) continue;
-                if (__any_sync(FULL, onm)) degen = true;
-                n_cuts++;
+                if (__any_sync(FULL, onm)) flags |= 1;
+                if (pp.collect && lane == 0) S.cnt[2]++;
                 int np = -1;
 #pragma unroll
                 for (int w2 = NW - 1; w2 >= 0; w2--)
                     if (~live[w2]) np = w2 * 64 + __ffsll((long long)~live[w2]) - 1;
-                if (np < 0) { fail = true; break; }
+                if (np < 0) { flags |= 2; break; }
                 // mark the directed edges of removed triangles
 #pragma unroll
                 for (int s = 0; s < VPL; s++) {
                     if (outm & (1u << s)) {
-                        int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
-                        atomicOr(&S.u.E[a][b >> 6], 1ull << (b & 63));
-                        atomicOr(&S.u.E[b][cc >> 6], 1ull << (cc & 63));
-                        atomicOr(&S.u.E[cc][a >> 6], 1ull << (a & 63));
+                        const int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
+                        atomicOr(&S.E[a][b >> 6], 1ull << (b & 63));
+                        atomicOr(&S.E[b][cc >> 6], 1ull << (cc & 63));
+                        atomicOr(&S.E[cc][a >> 6], 1ull << (a & 63));
                     }
                 }
                 __syncwarp();
@@ -786,11 +888,11 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
                 for (int s = 0; s < VPL; s++) {
                     bnd[s] = 0;
                     if (outm & (1u << s)) {
-                        int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
+                        const int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
                         // edge (x,y) borders the kept part iff its twin (y,x) was not removed
-                        if (!((S.u.E[b][a >> 6] >> (a & 63)) & 1)) bnd[s] |= 1;
-                        if (!((S.u.E[cc][b >> 6] >> (b & 63)) & 1)) bnd[s] |= 2;
-                        if (!((S.u.E[a][cc >> 6] >> (cc & 63)) & 1)) bnd[s] |= 4;
+                        if (!((S.E[b][a >> 6] >> (a & 63)) & 1)) bnd[s] |= 1;
+                        if (!((S.E[cc][b >> 6] >> (b & 63)) & 1)) bnd[s] |= 2;
+                        if (!((S.E[a][cc >> 6] >> (cc & 63)) & 1)) bnd[s] |= 4;
                         nc += __popc(bnd[s]);
                     } else if (tri[s] != TRI_EMPTY) {
                         kc++;
@@ -801,58 +903,55 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
 #pragma unroll
                 for (int s = 0; s < VPL; s++) {
                     if (outm & (1u << s)) {
-                        int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
+                        const int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
 #pragma unroll
-                        for (int w2 = 0; w2 < NW; w2++) { S.u.E[a][w2] = 0; S.u.E[b][w2] = 0; S.u.E[cc][w2] = 0; }
+                        for (int w2 = 0; w2 < NW; w2++) { S.E[a][w2] = 0; S.E[b][w2] = 0; S.E[cc][w2] = 0; }
                     }
                 }
                 int tot2;
                 const int pk = warp_excl_scan(kc | (nc << 16), lane, tot2);
                 const int K = tot2 & 0xffff, N = tot2 >> 16;
                 const int tot = K + N;
-                n_newv += N;
+                if (pp.collect && lane == 0) S.cnt[3] += N;
                 const int rc = tot > CAP ? 3 : (tot == 0 ? 2 : 1);
-                if (rc == 1) {
-                    int kpos = pk & 0xffff, npos = pk >> 16;
+                if (rc != 1) {
+                    flags |= rc == 2 ? 4 : 2;
+                    break;
+                }
+                {
+                    int npos = pk >> 16;
 #pragma unroll
                     for (int s = 0; s < VPL; s++) {
                         if (outm & (1u << s)) {
-                            int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
+                            const int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
                             if (bnd[s] & 1) S.elist[npos++] = a | (b << 8);
                             if (bnd[s] & 2) S.elist[npos++] = b | (cc << 8);
                             if (bnd[s] & 4) S.elist[npos++] = cc | (a << 8);
-                        } else if (tri[s] != TRI_EMPTY) {
-                            S.stri[kpos] = tri[s];
-                            S.sx[kpos] = vx[s]; S.sy[kpos] = vy[s]; S.sz[kpos] = vz[s];
-                            S.skap[kpos] = kap[s];
-                            kpos++;
+                            tri[s] = TRI_EMPTY;  // removed: its slot is free
                         }
                     }
                 }
                 __syncwarp();
-                if (rc != 1) {
-                    if (rc == 2) empty = true; else fail = true;
-                    break;
-                }
                 // new vertices, one per lane: planes x, y and the cutting plane
                 for (int q = lane; q < N; q += 32) {
                     const int xy = S.elist[q];
                     const int x = xy & 0xff, y = xy >> 8;
-                    auto P1 = S.pl[x];
-                    auto P2 = S.pl[y];
-                    T x23x = P2.y * qz - P2.z * qy, x23y = P2.z * qx - P2.x * qz, x23z = P2.x * qy - P2.y * qx;
-                    T x31x = qy * P1.z - qz * P1.y, x31y = qz * P1.x - qx * P1.z, x31z = qx * P1.y - qy * P1.x;
-                    T x12x = P1.y * P2.z - P1.z * P2.y, x12y = P1.z * P2.x - P1.x * P2.z, x12z = P1.x * P2.y - P1.y * P2.x;
-                    T det = P1.x * x23x + P1.y * x23y + P1.z * x23z;
+                    const auto P1 = S.pl[x];
+                    const auto P2 = S.pl[y];
+                    const T x23x = P2.y * qz - P2.z * qy, x23y = P2.z * qx - P2.x * qz, x23z = P2.x * qy - P2.y * qx;
+                    const T x31x = qy * P1.z - qz * P1.y, x31y = qz * P1.x - qx * P1.z, x31z = qx * P1.y - qy * P1.x;
+                    const T x12x = P1.y * P2.z - P1.z * P2.y, x12y = P1.z * P2.x - P1.x * P2.z,
+                            x12z = P1.x * P2.y - P1.y * P2.x;
+                    const T det = P1.x * x23x + P1.y * x23y + P1.z * x23z;
                     T nx, ny, nz;
                     float kp = 1.f;
                     bool solved = false;
                     if constexpr (F32) {
-                        float m123 = (P1.x * P1.x + P1.y * P1.y + P1.z * P1.z) *
-                                     (P2.x * P2.x + P2.y * P2.y + P2.z * P2.z) * qq;
-                        float d2 = det * det;
+                        const float m123 = (P1.x * P1.x + P1.y * P1.y + P1.z * P1.z) *
+                                           (P2.x * P2.x + P2.y * P2.y + P2.z * P2.z) * qq;
+                        const float d2 = det * det;
                         if (!(d2 * KAP_MAX2 >= m123)) {
-                            float3 v = solve_new64(&g, &st, ci, S.pref, S.pimg, x, y, ref, img);
+                            const float3 v = solve_new64(&g, &st, &S.cc, S.pref, S.pimg, x, y, ref, img);
                             nx = v.x; ny = v.y; nz = v.z;
                             solved = true;
                         } else {
@@ -860,14 +959,14 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
                         }
                     }
                     if (!solved) {
-                        T id = (T)1 / det;
+                        const T id = (T)1 / det;
                         nx = (P1.w * x23x + P2.w * x31x + c * x12x) * id;
                         ny = (P1.w * x23y + P2.w * x31y + c * x12y) * id;
                         nz = (P1.w * x23z + P2.w * x31z + c * x12z) * id;
                     }
-                    S.stri[K + q] = mk_tri(x, y, np);
-                    S.sx[K + q] = nx; S.sy[K + q] = ny; S.sz[K + q] = nz;
-                    S.skap[K + q] = kp;
+                    S.stri[q] = mk_tri(x, y, np);
+                    S.sx[q] = nx; S.sy[q] = ny; S.sz[q] = nz;
+                    S.skap[q] = kp;
                 }
                 if (lane == 0) {
                     S.pl[np] = mk4<T>(qx, qy, qz, c);
@@ -875,28 +974,35 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
                     S.pimg[np] = img;
                 }
                 __syncwarp();
+                // kept vertices stay in place; free slots take the new ones in order
                 ntri = tot;
                 unsigned long long lv[NW];
 #pragma unroll
                 for (int w2 = 0; w2 < NW; w2++) lv[w2] = 0;
                 T rr = 0;
+                int rank0 = 0;
+                rows = 0;
 #pragma unroll
                 for (int s = 0; s < VPL; s++) {
-                    int t = s * 32 + lane;
-                    if (t < tot) {
-                        tri[s] = S.stri[t];
-                        vx[s] = S.sx[t]; vy[s] = S.sy[t]; vz[s] = S.sz[t];
-                        kap[s] = S.skap[t];
-                        int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
+                    const bool fr = tri[s] == TRI_EMPTY;
+                    const unsigned fm = __ballot_sync(FULL, fr);
+                    const int rank = rank0 + __popc(fm & ((1u << lane) - 1));
+                    rank0 += __popc(fm);
+                    if (fr && rank < N) {
+                        tri[s] = S.stri[rank];
+                        vx[s] = S.sx[rank]; vy[s] = S.sy[rank]; vz[s] = S.sz[rank];
+                        kap[s] = S.skap[rank];
+                    }
+                    if (tri[s] != TRI_EMPTY) {
+                        const int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
                         lv[a >> 6] |= 1ull << (a & 63);
                         lv[b >> 6] |= 1ull << (b & 63);
                         lv[cc >> 6] |= 1ull << (cc & 63);
                         T q2 = vx[s] * vx[s] + vy[s] * vy[s] + vz[s] * vz[s];
                         if constexpr (F32) q2 *= 1.f + 4e-6f * kap[s];  // allowance for FP32 error
                         rr = rr > q2 ? rr : q2;
-                    } else {
-                        tri[s] = TRI_EMPTY;
                     }
+                    if (__any_sync(FULL, tri[s] != TRI_EMPTY)) rows |= 1u << s;
                 }
 #pragma unroll
                 for (int w2 = 0; w2 < NW; w2++) live[w2] = warp_or64(lv[w2]);
@@ -906,29 +1012,29 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
             }
 
             // ================================================= statistics
+            const bool degen = flags & 1;
+            bool fail = flags & 2;
             int status = VG_CELL_OK;
-            if (empty) status = VG_CELL_EMPTY;
-            else if (dup) status = VG_CELL_DUP;
-            else if (limit) status = VG_CELL_LIMIT;
-            const int out_i = ci.self_id;
+            if (flags & 4) status = VG_CELL_EMPTY;
+            else if (flags & 8) status = VG_CELL_DUP;
+            else if (src.limit) status = VG_CELL_LIMIT;
+            const int out_i = S.cc.self_id;
             if (!fail && status == VG_CELL_OK) {
                 const int T_ = ntri;
 #pragma unroll
                 for (int s = 0; s < VPL; s++) {
-                    int t = s * 32 + lane;
-                    if (t < T_) { S.stri[t] = tri[s]; S.sx[t] = vx[s]; S.sy[t] = vy[s]; S.sz[t] = vz[s]; }
+                    const int t = s * 32 + lane;
+                    S.stri[t] = tri[s]; S.sx[t] = vx[s]; S.sy[t] = vy[s]; S.sz[t] = vz[s];
                 }
-                const double eps = pp.merge_rel * g.s;
-                const double eps2 = eps * eps;
                 if (degen) {
 #pragma unroll
                     for (int s = 0; s < VPL; s++) {
-                        int t = s * 32 + lane;
-                        if (t < T_) {
+                        const int t = s * 32 + lane;
+                        if (tri[s] != TRI_EMPTY) {
                             if constexpr (F32) {
-                                vertex64(&g, &st, ci, S.pref, S.pimg, tri[s], S.u.dpos[t]);
+                                vertex64(&g, &st, &S.cc, S.pref, S.pimg, tri[s], S.x.dpos[t]);
                             } else {
-                                S.u.dpos[t][0] = vx[s]; S.u.dpos[t][1] = vy[s]; S.u.dpos[t][2] = vz[s];
+                                S.x.dpos[t][0] = vx[s]; S.x.dpos[t][1] = vy[s]; S.x.dpos[t][2] = vz[s];
                             }
                         }
                     }
@@ -956,7 +1062,8 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
                             if (a < 0 && f < cntw + pc) {
                                 const unsigned lo32 = (unsigned)live[w2], hi32 = (unsigned)(live[w2] >> 32);
                                 const int nth = f - cntw, plo = __popc(lo32);
-                                a = w2 * 64 + (nth < plo ? (int)__fns(lo32, 0, nth + 1) : 32 + (int)__fns(hi32, 0, nth - plo + 1));
+                                a = w2 * 64 + (nth < plo ? (int)__fns(lo32, 0, nth + 1)
+                                                         : 32 + (int)__fns(hi32, 0, nth - plo + 1));
                             }
                             cntw += pc;
                         }
@@ -965,7 +1072,7 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
 #pragma unroll
                     for (int s = 0; s < VPL; s++) {
                         const int t = s * 32 + lane;
-                        if (t < T_) {
+                        if (tri[s] != TRI_EMPTY) {
                             const unsigned tr = tri[s];
                             const int pp3[3] = {tri_a(tr), tri_b(tr), tri_c(tr)};
 #pragma unroll
@@ -996,24 +1103,25 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
                         if (!degen) {
                             const T u0x = S.sx[t0], u0y = S.sy[t0], u0z = S.sz[t0];
                             T fv = 0, fcx = 0, fcy = 0, fcz = 0, fax = 0, fay = 0, faz = 0;
-                            for (steps = 0; steps < T_; steps++) {
-                                unsigned tr = S.stri[cur];
-                                int p0 = tri_a(tr), p1 = tri_b(tr), p2 = tri_c(tr);
-                                int yy = p0 == a ? p2 : (p1 == a ? p0 : (p2 == a ? p1 : -1));
+                            for (steps = 0; steps < CAP; steps++) {
+                                const unsigned tr = S.stri[cur];
+                                const int p0 = tri_a(tr), p1 = tri_b(tr), p2 = tri_c(tr);
+                                const int yy = p0 == a ? p2 : (p1 == a ? p0 : (p2 == a ? p1 : -1));
                                 if (yy < 0) { bad = true; break; }
-                                int nx = S.w.ftab[lane][yy];
-                                if (nx >= T_) { bad = true; break; }
+                                const int nx = S.w.ftab[lane][yy];
+                                if (nx >= CAP || S.stri[nx] == TRI_EMPTY) { bad = true; break; }
                                 if (nx == t0) { steps++; closed = true; break; }
                                 if (cur != t0) {
-                                    T ax = S.sx[cur], ay = S.sy[cur], az = S.sz[cur];
-                                    T bx = S.sx[nx], by = S.sy[nx], bz = S.sz[nx];
-                                    T det = u0x * (ay * bz - az * by) - u0y * (ax * bz - az * bx) + u0z * (ax * by - ay * bx);
+                                    const T ax = S.sx[cur], ay = S.sy[cur], az = S.sz[cur];
+                                    const T bx = S.sx[nx], by = S.sy[nx], bz = S.sz[nx];
+                                    const T det = u0x * (ay * bz - az * by) - u0y * (ax * bz - az * bx) +
+                                                  u0z * (ax * by - ay * bx);
                                     fv += det;
                                     fcx += det * (u0x + ax + bx);
                                     fcy += det * (u0y + ay + by);
                                     fcz += det * (u0z + az + bz);
-                                    T e1x = ax - u0x, e1y = ay - u0y, e1z = az - u0z;
-                                    T e2x = bx - u0x, e2y = by - u0y, e2z = bz - u0z;
+                                    const T e1x = ax - u0x, e1y = ay - u0y, e1z = az - u0z;
+                                    const T e2x = bx - u0x, e2y = by - u0y, e2z = bz - u0z;
                                     fax += e1y * e2z - e1z * e2y;
                                     fay += e1z * e2x - e1x * e2z;
                                     faz += e1x * e2y - e1y * e2x;
@@ -1026,33 +1134,34 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
                             order = steps;
                         } else {
                             // degenerate cell: FP64 vertices, coincident ones merged
-                            const double fx = S.u.dpos[t0][0], fy = S.u.dpos[t0][1], fz = S.u.dpos[t0][2];
+                            const double eps = pp.merge_rel * g.s, eps2 = eps * eps;
+                            const double fx = S.x.dpos[t0][0], fy = S.x.dpos[t0][1], fz = S.x.dpos[t0][2];
                             double px = fx, py = fy, pz = fz, per = 0, fv = 0, fcx = 0, fcy = 0, fcz = 0;
                             double fax = 0, fay = 0, faz = 0;
                             int distinct = 1;
-                            for (steps = 0; steps < T_; steps++) {
-                                unsigned tr = S.stri[cur];
-                                int p0 = tri_a(tr), p1 = tri_b(tr), p2 = tri_c(tr);
-                                int yy = p0 == a ? p2 : (p1 == a ? p0 : (p2 == a ? p1 : -1));
+                            for (steps = 0; steps < CAP; steps++) {
+                                const unsigned tr = S.stri[cur];
+                                const int p0 = tri_a(tr), p1 = tri_b(tr), p2 = tri_c(tr);
+                                const int yy = p0 == a ? p2 : (p1 == a ? p0 : (p2 == a ? p1 : -1));
                                 if (yy < 0) { bad = true; break; }
-                                int nx = S.w.ftab[lane][yy];
-                                if (nx >= T_) { bad = true; break; }
+                                const int nx = S.w.ftab[lane][yy];
+                                if (nx >= CAP || S.stri[nx] == TRI_EMPTY) { bad = true; break; }
                                 if (nx == t0) { steps++; closed = true; break; }
-                                const double *A = S.u.dpos[cur], *B = S.u.dpos[nx];
+                                const double *A = S.x.dpos[cur], *B = S.x.dpos[nx];
                                 if (cur != t0) {
-                                    double det = fx * (A[1] * B[2] - A[2] * B[1]) - fy * (A[0] * B[2] - A[2] * B[0]) +
-                                                 fz * (A[0] * B[1] - A[1] * B[0]);
+                                    const double det = fx * (A[1] * B[2] - A[2] * B[1]) - fy * (A[0] * B[2] - A[2] * B[0]) +
+                                                       fz * (A[0] * B[1] - A[1] * B[0]);
                                     fv += det;
                                     fcx += det * (fx + A[0] + B[0]);
                                     fcy += det * (fy + A[1] + B[1]);
                                     fcz += det * (fz + A[2] + B[2]);
-                                    double e1x = A[0] - fx, e1y = A[1] - fy, e1z = A[2] - fz;
-                                    double e2x = B[0] - fx, e2y = B[1] - fy, e2z = B[2] - fz;
+                                    const double e1x = A[0] - fx, e1y = A[1] - fy, e1z = A[2] - fz;
+                                    const double e2x = B[0] - fx, e2y = B[1] - fy, e2z = B[2] - fz;
                                     fax += e1y * e2z - e1z * e2y;
                                     fay += e1z * e2x - e1x * e2z;
                                     faz += e1x * e2y - e1y * e2x;
                                 }
-                                double dx = B[0] - px, dy = B[1] - py, dz = B[2] - pz;
+                                const double dx = B[0] - px, dy = B[1] - py, dz = B[2] - pz;
                                 if (dx * dx + dy * dy + dz * dz > eps2) {
                                     per += sqrt(dx * dx + dy * dy + dz * dz);
                                     distinct++;
@@ -1060,10 +1169,10 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
                                 }
                                 cur = nx;
                             }
-                            double dx = fx - px, dy = fy - py, dz = fz - pz;
+                            const double dx = fx - px, dy = fy - py, dz = fz - pz;
                             if (distinct > 1 && dx * dx + dy * dy + dz * dz <= eps2) distinct--;
                             else per += sqrt(dx * dx + dy * dy + dz * dz);
-                            double fa = 0.5 * sqrt(fax * fax + fay * fay + faz * faz);
+                            const double fa = 0.5 * sqrt(fax * fax + fay * fay + faz * faz);
                             order = distinct;
                             keep = distinct >= 3 && fa > eps * per;
                             vol += fv;
@@ -1082,9 +1191,8 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
                                                 ((unsigned)(imgc(img, 1) + 128) << 8) | (unsigned)(imgc(img, 2) + 128);
                             // canonical order: ascending neighbour id (walls first), then
                             // image; the face order rides in the low byte
-                            const unsigned long long k =
-                                ((unsigned long long)((long long)nid + 8) << 32) | ((unsigned long long)ib << 8) |
-                                (unsigned)(order & 0xff);
+                            const unsigned long long k = ((unsigned long long)((long long)nid + 8) << 32) |
+                                                         ((unsigned long long)ib << 8) | (unsigned)(order & 0xff);
 #pragma unroll
                             for (int r = 0; r < R; r++)
                                 if (r == rnd) key[r] = k;
@@ -1101,15 +1209,17 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
                 int nv;
                 if (degen) {
                     // distinct vertices: a vertex counts if no earlier one coincides
+                    const double eps = pp.merge_rel * g.s, eps2 = eps * eps;
                     int cntv = 0;
 #pragma unroll
                     for (int s = 0; s < VPL; s++) {
-                        int t = s * 32 + lane;
-                        if (t < T_) {
+                        const int t = s * 32 + lane;
+                        if (tri[s] != TRI_EMPTY) {
                             bool first = true;
                             for (int q = 0; q < t && first; q++) {
-                                double dx = S.u.dpos[q][0] - S.u.dpos[t][0], dy = S.u.dpos[q][1] - S.u.dpos[t][1],
-                                       dz = S.u.dpos[q][2] - S.u.dpos[t][2];
+                                if (S.stri[q] == TRI_EMPTY) continue;
+                                const double dx = S.x.dpos[q][0] - S.x.dpos[t][0], dy = S.x.dpos[q][1] - S.x.dpos[t][1],
+                                             dz = S.x.dpos[q][2] - S.x.dpos[t][2];
                                 if (dx * dx + dy * dy + dz * dz <= eps2) first = false;
                             }
                             cntv += first;
@@ -1145,23 +1255,20 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
                         }
                     }
                     if (lane == 0) {
-                        o.vol[out_i] = vol / 6.0;
-                        o.area[out_i] = (double)area;
                         const double v6 = vol;
-                        o.cen[(long long)out_i * 3 + 0] = v6 != 0 ? (double)cx / (4.0 * v6) : 0.0;
-                        o.cen[(long long)out_i * 3 + 1] = v6 != 0 ? (double)cy / (4.0 * v6) : 0.0;
-                        o.cen[(long long)out_i * 3 + 2] = v6 != 0 ? (double)cz / (4.0 * v6) : 0.0;
+                        o.vol[out_i] = v6 * (1.0 / 6.0);
+                        o.area[out_i] = (double)area;
+                        // centroid = sum det (u0 + a + b) / (4 sum det)
+                        const T inv = v6 != 0.0 ? (T)1 / ((T)4 * (T)v6) : (T)0;
+                        o.cen[(long long)out_i * 3 + 0] = (double)(cx * inv);
+                        o.cen[(long long)out_i * 3 + 1] = (double)(cy * inv);
+                        o.cen[(long long)out_i * 3 + 2] = (double)(cz * inv);
                         o.nv[out_i] = nv;
                         o.ne[out_i] = osum / 2;
                         o.nf[out_i] = nfk;
                         o.status[out_i] = overflow ? (unsigned char)VG_CELL_CAP : (unsigned char)VG_CELL_OK;
                         o.fptr[out_i] = fbase;
                     }
-                }
-                if (degen) {
-                    // the FP64 vertices shared storage with the edge matrix
-                    __syncwarp();
-                    for (int q = lane; q < MAXP * NW; q += 32) (&S.u.E[0][0])[q] = 0ull;
                 }
                 __syncwarp();
             } else if (!fail && lane == 0) {
@@ -1174,7 +1281,7 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
             }
             if (fail && lane == 0) {
                 if (tier == 0) {
-                    int slot = atomicAdd(o.retry_count, 1);
+                    const int slot = atomicAdd(o.retry_count, 1);
                     o.retry[slot] = i;
                 }
                 o.status[out_i] = VG_CELL_CAP;
@@ -1183,12 +1290,12 @@ __global__ void __launch_bounds__(128, VG_MINB) k_cells3(const __grid_constant__
                 o.fptr[out_i] = 0;
             }
             if (pp.collect && lane == 0) {
-                o.w_tested[out_i] = n_tested;
-                o.w_vtests[out_i] = n_vtests;
-                o.w_cuts[out_i] = n_cuts;
-                o.w_newv[out_i] = n_newv;
-                o.w_retest[out_i] = n_retest;
-                o.w_fallback[out_i] = (unsigned char)fell_back;
+                o.w_tested[out_i] = S.cnt[0];
+                o.w_vtests[out_i] = S.cnt[1];
+                o.w_cuts[out_i] = S.cnt[2];
+                o.w_newv[out_i] = S.cnt[3];
+                o.w_retest[out_i] = S.cnt[4];
+                o.w_fallback[out_i] = (unsigned char)src.fell_back;
             }
             __syncwarp();
         }
@@ -1199,7 +1306,7 @@ template <typename T, int VPL, int MAXP>
 cudaError_t launch_t(const Grid &g, const Store &s, const Out &o, const Params &p, const Offsets &off,
                      unsigned *ticket, int sm_count, int warps, const int *cells, int ncells, int tier,
                      cudaStream_t st) {
-    size_t smem = sizeof(Smem<T, VPL, MAXP>) * warps;
+    const size_t smem = sizeof(Smem<T, VPL, MAXP>) * warps;
     auto kfn = k_cells3<T, VPL, MAXP>;
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1220,7 +1327,7 @@ cudaError_t launch_t(const Grid &g, const Store &s, const Out &o, const Params &
 cudaError_t launch_cells3(const Grid &g, const Store &s, const Out &o, const Params &p, const Offsets &off,
                           int precision, unsigned *ticket, int sm_count, int warps_per_cta, const int *cells,
                           int ncells, int tier, cudaStream_t st) {
-    int w = warps_per_cta > 0 ? warps_per_cta : 4;
+    const int w = warps_per_cta > 0 ? warps_per_cta : 4;
     if (tier > 0) return launch_t<double, 4, 128>(g, s, o, p, off, ticket, sm_count, 2, cells, ncells, tier, st);
     if (precision == VG_FP64) return launch_t<double, 2, 64>(g, s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
     return launch_t<float, 2, 64>(g, s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);

@@ -86,3 +86,17 @@ def test_tiny_systems(precision, order, rtol):
     for n, per in ((1, True), (1, False), (2, False), (5, True)):
         s = W.uniform(n, 3, 1.0, per, seed=10 + n)
         check(s, (2, 2, 2), precision, order, rtol, method="brute")
+
+
+@pytest.mark.parametrize("precision,order,rtol", FORMS)
+def test_uniform_periodic_20k_all_cells(precision, order, rtol):
+    # large enough that walks span several windows of blocks
+    s = W.uniform(20000, 3, 20000 ** (1 / 3), True, seed=17)
+    check(s, (16, 16, 16), precision, order, rtol)
+
+
+@pytest.mark.parametrize("precision,order,rtol", FORMS)
+def test_uniform_walled_fine_grid(precision, order, rtol):
+    # small blocks (about one particle each): long walks over many blocks
+    s = W.uniform(8000, 3, 1.0, False, seed=18)
+    check(s, (20, 20, 20), precision, order, rtol)
