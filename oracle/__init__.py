@@ -135,7 +135,7 @@ def quantize_local_f32(pos, lo, hi, nblocks) -> np.ndarray:
 
 
 def compute(pos, lo, hi, periodic, radii=None, method: str = "grid", nblocks=None,
-            cells=None, maxf: int = 128, threads: int = 0,
+            cells=None, maxf: int | None = None, threads: int = 0,
             tau_rel: float = TAU_REL, merge_rel: float = MERGE_REL) -> dict:
     """Cells of the particles `cells` (default: all).  Returns a dict of
     per-cell arrays (vol, area, centroid relative to the particle, nv, ne,
@@ -146,6 +146,9 @@ def compute(pos, lo, hi, periodic, radii=None, method: str = "grid", nblocks=Non
     lib = _load()
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     n, d = pos.shape
+    if maxf is None:
+        # face slots per cell: radical cells of large particles can have many
+        maxf = (320 if radii is not None else 96) if d == 3 else (256 if radii is not None else 64)
     lo = np.ascontiguousarray(lo, dtype=np.float64)
     hi = np.ascontiguousarray(hi, dtype=np.float64)
     per = np.ascontiguousarray([1 if p else 0 for p in periodic], dtype=np.int32)

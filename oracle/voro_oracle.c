@@ -53,10 +53,10 @@
 #include <omp.h>
 #endif
 
-#define OR_MAXF 160  /* faces per cell */
-#define OR_MAXFV 96  /* vertices per face */
-#define OR_MAXNP 512 /* points on one cutting plane (with duplicates) */
-#define OR_MAXV2 512 /* polygon vertices in 2D */
+#define OR_MAXF 384  /* faces per cell */
+#define OR_MAXFV 192 /* vertices per face */
+#define OR_MAXNP 1024 /* points on one cutting plane (with duplicates) */
+#define OR_MAXV2 1024 /* polygon vertices in 2D */
 
 enum { ST_OK = 0, ST_EMPTY = 1, ST_CAP = 2 };
 
@@ -524,16 +524,21 @@ typedef struct {
     int nv, ne, nf;
 } stats_t;
 
-/* 3D: volume and centroid by fans from each face's first vertex to the
- * origin (= the particle); area = sum of face areas; V, E by merging
- * coincident points (eps) over all faces. */
+/* 3D: volume and centroid by fans from each face's first vertex to a fixed
+ * apex o (the tetrahedral decomposition of a closed surface does not depend
+ * on the apex; a vertex of the cell is used so that a radical cell lying far
+ * from its particle does not cancel); area = sum of face areas; V, E by
+ * merging coincident points (eps) over all faces. */
 static void stats3(const cell3 *cl, double eps, stats_t *st, int *forder) {
     double vol = 0, cx = 0, cy = 0, cz = 0, area = 0;
+    const double *o = cl->nf > 0 ? cl->f[0].v[0] : NULL;
     for (int i = 0; i < cl->nf; i++) {
         const ofc *f = &cl->f[i];
         double A[3] = {0, 0, 0};
         for (int j = 1; j + 1 < f->nv; j++) {
-            const double *a = f->v[0], *b = f->v[j], *c = f->v[j + 1];
+            const double a[3] = {f->v[0][0] - o[0], f->v[0][1] - o[1], f->v[0][2] - o[2]};
+            const double b[3] = {f->v[j][0] - o[0], f->v[j][1] - o[1], f->v[j][2] - o[2]};
+            const double c[3] = {f->v[j + 1][0] - o[0], f->v[j + 1][1] - o[1], f->v[j + 1][2] - o[2]};
             double det = a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) +
                          a[2] * (b[0] * c[1] - b[1] * c[0]);
             double v6 = det / 6.0;
@@ -551,9 +556,9 @@ static void stats3(const cell3 *cl, double eps, stats_t *st, int *forder) {
     }
     st->vol = vol;
     st->area = area;
-    st->cen[0] = vol != 0 ? cx / vol : 0;
-    st->cen[1] = vol != 0 ? cy / vol : 0;
-    st->cen[2] = vol != 0 ? cz / vol : 0;
+    st->cen[0] = vol != 0 ? o[0] + cx / vol : 0;
+    st->cen[1] = vol != 0 ? o[1] + cy / vol : 0;
+    st->cen[2] = vol != 0 ? o[2] + cz / vol : 0;
     st->nf = cl->nf;
     /* distinct vertices */
     int tot = 0;
@@ -592,21 +597,26 @@ static void stats3(const cell3 *cl, double eps, stats_t *st, int *forder) {
     free(pts); free(cid); free(ea); free(eb);
 }
 
+/* 2D: shoelace sums taken about the first vertex o (translation does not
+ * change them; it avoids cancellation for cells far from their particle). */
 static void stats2(const cell2 *cl, stats_t *st) {
     double A = 0, cx = 0, cy = 0, per = 0;
     int n = cl->nv;
+    const double o[2] = {n ? cl->v[0][0] : 0.0, n ? cl->v[0][1] : 0.0};
     for (int i = 0; i < n; i++) {
         int j = (i + 1) % n;
-        double cr = cl->v[i][0] * cl->v[j][1] - cl->v[j][0] * cl->v[i][1];
+        const double ax = cl->v[i][0] - o[0], ay = cl->v[i][1] - o[1];
+        const double bx = cl->v[j][0] - o[0], by = cl->v[j][1] - o[1];
+        double cr = ax * by - bx * ay;
         A += cr / 2.0;
-        cx += cr * (cl->v[i][0] + cl->v[j][0]) / 6.0;
-        cy += cr * (cl->v[i][1] + cl->v[j][1]) / 6.0;
+        cx += cr * (ax + bx) / 6.0;
+        cy += cr * (ay + by) / 6.0;
         per += sqrt(dist2(cl->v[i], cl->v[j], 2));
     }
     st->vol = A;
     st->area = per;
-    st->cen[0] = A != 0 ? cx / A : 0;
-    st->cen[1] = A != 0 ? cy / A : 0;
+    st->cen[0] = A != 0 ? o[0] + cx / A : 0;
+    st->cen[1] = A != 0 ? o[1] + cy / A : 0;
     st->cen[2] = 0;
     st->nv = st->ne = st->nf = n;
     st->R = maxr2(cl);
