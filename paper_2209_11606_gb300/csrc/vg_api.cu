@@ -210,6 +210,7 @@ vg_status vg_create(vg_ctx **out, int dim, const double *lo, const double *hi, c
     VG_CUDA(cudaMalloc((void **)&c->d_fcount, sizeof(unsigned long long)));
     VG_CUDA(cudaMalloc((void **)&c->d_ticket, sizeof(unsigned) * 4));
     VG_CUDA(cudaMalloc((void **)&c->d_capcount, sizeof(int)));
+    VG_CUDA(cudaMalloc((void **)&c->d_capcount2, sizeof(int)));
     *out = c;
     return VG_OK;
 }
@@ -247,6 +248,7 @@ vg_status vg_insert(vg_ctx *c, int64_t n, const double *pos, const double *radii
     VG_CUDA(ensure(c, c->d_fptr, n));
     VG_CUDA(ensure(c, c->d_face_off, n + 1));
     VG_CUDA(ensure(c, c->d_caplist, n));
+    VG_CUDA(ensure(c, c->d_caplist2, n));
     VG_CUDA(ensure(c, c->d_w_tested, n));
     VG_CUDA(ensure(c, c->d_w_vtests, n));
     VG_CUDA(ensure(c, c->d_w_cuts, n));
@@ -343,8 +345,10 @@ vg_status vg_compute(vg_ctx *c, const vg_config *cfg_in) {
         o.w_tested = c->d_w_tested; o.w_vtests = c->d_w_vtests; o.w_cuts = c->d_w_cuts;
         o.w_retest = c->d_w_retest; o.w_fallback = c->d_w_fallback; o.w_newv = c->d_w_newv;
         o.retry = c->d_caplist; o.retry_count = c->d_capcount;
+        o.retry2 = c->d_caplist2; o.retry2_count = c->d_capcount2;
         VG_CUDA(cudaMemsetAsync(c->d_fcount, 0, sizeof(unsigned long long), c->stream));
         VG_CUDA(cudaMemsetAsync(c->d_capcount, 0, sizeof(int), c->stream));
+        VG_CUDA(cudaMemsetAsync(c->d_capcount2, 0, sizeof(int), c->stream));
         cudaError_t e;
         const bool timed = cfg.time_kernels && c->nev < vg_ctx::NEV;
         if (timed) {
@@ -359,6 +363,9 @@ vg_status vg_compute(vg_ctx *c, const vg_config *cfg_in) {
             e = launch_cells3(c->g, st, o, pp, off, cfg.precision, c->d_ticket + 1, c->sm_count, 0,
                               c->d_caplist, 0, 1, c->stream);
             if (e != cudaSuccess) return cuda_fail(c, e, "launch_cells3 (big cells)");
+            e = launch_cells3(c->g, st, o, pp, off, cfg.precision, c->d_ticket + 2, c->sm_count, 0,
+                              c->d_caplist2, 0, 2, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "launch_cells3 (largest cells)");
         } else {
             e = launch_cells2(c->g, st, o, pp, off, cfg.precision, c->d_ticket, c->sm_count, cfg.warps_per_cta,
                               nullptr, (int)n, 0, c->stream);
@@ -366,6 +373,9 @@ vg_status vg_compute(vg_ctx *c, const vg_config *cfg_in) {
             e = launch_cells2(c->g, st, o, pp, off, cfg.precision, c->d_ticket + 1, c->sm_count, 0,
                               c->d_caplist, 0, 1, c->stream);
             if (e != cudaSuccess) return cuda_fail(c, e, "launch_cells2 (big cells)");
+            e = launch_cells2(c->g, st, o, pp, off, cfg.precision, c->d_ticket + 2, c->sm_count, 0,
+                              c->d_caplist2, 0, 2, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "launch_cells2 (largest cells)");
         }
         if (timed) {
             VG_CUDA(cudaEventRecord(c->ev[2 * c->nev + 1], c->stream));
@@ -518,6 +528,7 @@ void vg_destroy(vg_ctx *c) {
     release(c->d_ticket); release(c->d_face_off); release(c->d_nbr); release(c->d_img); release(c->d_ford);
     release(c->d_w_tested); release(c->d_w_vtests); release(c->d_w_cuts); release(c->d_w_retest);
     release(c->d_w_fallback); release(c->d_caplist); release(c->d_capcount);
+    release(c->d_caplist2); release(c->d_capcount2);
     release(c->d_off_code); release(c->d_off_lb); release(c->d_kblock); release(c->d_w_newv);
     for (int k = 0; k < 2 * vg_ctx::NEV; k++)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);

@@ -39,6 +39,8 @@
 // Warp-uniform bookkeeping (the candidate source, per-cell constants that
 // only cold paths read) lives in per-warp shared memory rather than in
 // registers, to keep the register file for the cell itself.
+#include <type_traits>
+
 #include "vg_internal.cuh"
 
 namespace vg {
@@ -96,6 +98,8 @@ struct Src {
 
 template <typename T, int VPL, int MAXP>
 struct Smem {
+    // slot indices in the face walk tables: a byte up to 256 vertices
+    using FT = typename std::conditional<(32 * VPL > 256), unsigned short, unsigned char>::type;
     typename V4T<T>::t pl[MAXP];  // plane normal (x,y,z) and constant (w), cell frame
     int pref[MAXP];               // neighbour's sorted index, or wall code -1..-6
     int pimg[MAXP];               // packed image shift of the neighbour
@@ -104,7 +108,7 @@ struct Smem {
     float skap[32 * VPL];
     unsigned long long E[MAXP][MAXP / 64];  // removed directed edges of one cut
     union {
-        unsigned char ftab[32][MAXP];  // face walk tables, one row per face of a round
+        FT ftab[32][MAXP];             // face walk tables, one row per face of a round
         struct {
             int start[NRUN], j0[NRUN], oxb[NRUN], oyz[NRUN];
         } run;                         // prefetch gather: runs of contiguous blocks
@@ -120,7 +124,7 @@ struct Smem {
         } pf;
         double dpos[32 * VPL][3];  // FP64 vertices (degenerate cells)
     } x;
-    unsigned char sfirst[32];  // a triangle of each face of a round
+    FT sfirst[32];             // a triangle of each face of a round
     int elist[32 * VPL];       // boundary edges (x | y << 8) of one cut
     CellC cc;
     Src src;
@@ -365,7 +369,7 @@ __global__ void __launch_bounds__(128, VG_MINB)
     // the edge matrix starts clear; every cut leaves it clear
     for (int u = lane; u < MAXP * NW; u += 32) (&S.E[0][0])[u] = 0ull;
     __syncwarp();
-    const int total = cells ? (tier > 0 ? *o.retry_count : ncells) : st.n;
+    const int total = cells ? (tier == 1 ? *o.retry_count : (tier == 2 ? *o.retry2_count : ncells)) : st.n;
     const int chunk = pp.chunk > 0 ? pp.chunk : 1;
 
     for (int iter = 0; iter < (1 << 30); iter++) {
@@ -1012,7 +1016,7 @@ __global__ void __launch_bounds__(128, VG_MINB)
             }
 
             // ================================================= statistics
-            const bool degen = flags & 1;
+            bool degen = flags & 1;
             bool fail = flags & 2;
             int status = VG_CELL_OK;
             if (flags & 4) status = VG_CELL_EMPTY;
@@ -1026,6 +1030,32 @@ __global__ void __launch_bounds__(128, VG_MINB)
                     const int t = s * 32 + lane;
                     S.stri[t] = tri[s]; S.sx[t] = vx[s]; S.sy[t] = vy[s]; S.sz[t] = vz[s];
                 }
+                // reference point for the fans: a vertex of the cell (a radical
+                // cell may lie far from its particle, where fans from the
+                // particle would cancel)
+                int tref = 0;
+                T rx = 0, ry = 0, rz = 0;
+                {
+                    int rsl = 0;
+                    unsigned occ = __ballot_sync(FULL, tri[0] != TRI_EMPTY);
+#pragma unroll
+                    for (int s = 1; s < VPL; s++) {
+                        const unsigned oc = __ballot_sync(FULL, tri[s] != TRI_EMPTY);
+                        if (!occ && oc) { occ = oc; rsl = s; }
+                    }
+                    const int rl = __ffs(occ) - 1;
+                    tref = rsl * 32 + rl;
+                    T cxv = 0, cyv = 0, czv = 0;
+#pragma unroll
+                    for (int s = 0; s < VPL; s++)
+                        if (s == rsl) { cxv = vx[s]; cyv = vy[s]; czv = vz[s]; }
+                    rx = __shfl_sync(FULL, cxv, rl);
+                    ry = __shfl_sync(FULL, cyv, rl);
+                    rz = __shfl_sync(FULL, czv, rl);
+                }
+                // pass 0 sums the FP32 vertices; a cell thin against its
+                // distance from the particle gets a pass from FP64 vertices
+                for (int pass = 0; pass < 2; pass++) {
                 if (degen) {
 #pragma unroll
                     for (int s = 0; s < VPL; s++) {
@@ -1040,6 +1070,9 @@ __global__ void __launch_bounds__(128, VG_MINB)
                     }
                 }
                 __syncwarp();
+                double dref[3];
+                if (degen) { dref[0] = S.x.dpos[tref][0]; dref[1] = S.x.dpos[tref][1]; dref[2] = S.x.dpos[tref][2]; }
+                else { dref[0] = (double)rx; dref[1] = (double)ry; dref[2] = (double)rz; }
                 int F = 0;
 #pragma unroll
                 for (int w2 = 0; w2 < NW; w2++) F += __popcll(live[w2]);
@@ -1086,8 +1119,8 @@ __global__ void __launch_bounds__(128, VG_MINB)
                                     else if (pl_ > lo64) rk += __popcll(live[w2] & ((1ull << (pl_ - lo64)) - 1));
                                 }
                                 if ((rk >> 5) == rnd) {
-                                    S.w.ftab[rk & 31][xx] = (unsigned char)t;
-                                    S.sfirst[rk & 31] = (unsigned char)t;
+                                    S.w.ftab[rk & 31][xx] = (typename S_t::FT)t;
+                                    S.sfirst[rk & 31] = (typename S_t::FT)t;
                                 }
                             }
                         }
@@ -1101,7 +1134,7 @@ __global__ void __launch_bounds__(128, VG_MINB)
                         bool keep = true;
                         T farea;
                         if (!degen) {
-                            const T u0x = S.sx[t0], u0y = S.sy[t0], u0z = S.sz[t0];
+                            const T u0x = S.sx[t0] - rx, u0y = S.sy[t0] - ry, u0z = S.sz[t0] - rz;
                             T fv = 0, fcx = 0, fcy = 0, fcz = 0, fax = 0, fay = 0, faz = 0;
                             for (steps = 0; steps < CAP; steps++) {
                                 const unsigned tr = S.stri[cur];
@@ -1112,8 +1145,8 @@ __global__ void __launch_bounds__(128, VG_MINB)
                                 if (nx >= CAP || S.stri[nx] == TRI_EMPTY) { bad = true; break; }
                                 if (nx == t0) { steps++; closed = true; break; }
                                 if (cur != t0) {
-                                    const T ax = S.sx[cur], ay = S.sy[cur], az = S.sz[cur];
-                                    const T bx = S.sx[nx], by = S.sy[nx], bz = S.sz[nx];
+                                    const T ax = S.sx[cur] - rx, ay = S.sy[cur] - ry, az = S.sz[cur] - rz;
+                                    const T bx = S.sx[nx] - rx, by = S.sy[nx] - ry, bz = S.sz[nx] - rz;
                                     const T det = u0x * (ay * bz - az * by) - u0y * (ax * bz - az * bx) +
                                                   u0z * (ax * by - ay * bx);
                                     fv += det;
@@ -1135,7 +1168,8 @@ __global__ void __launch_bounds__(128, VG_MINB)
                         } else {
                             // degenerate cell: FP64 vertices, coincident ones merged
                             const double eps = pp.merge_rel * g.s, eps2 = eps * eps;
-                            const double fx = S.x.dpos[t0][0], fy = S.x.dpos[t0][1], fz = S.x.dpos[t0][2];
+                            const double fx = S.x.dpos[t0][0] - dref[0], fy = S.x.dpos[t0][1] - dref[1],
+                                         fz = S.x.dpos[t0][2] - dref[2];
                             double px = fx, py = fy, pz = fz, per = 0, fv = 0, fcx = 0, fcy = 0, fcz = 0;
                             double fax = 0, fay = 0, faz = 0;
                             int distinct = 1;
@@ -1147,7 +1181,10 @@ __global__ void __launch_bounds__(128, VG_MINB)
                                 const int nx = S.w.ftab[lane][yy];
                                 if (nx >= CAP || S.stri[nx] == TRI_EMPTY) { bad = true; break; }
                                 if (nx == t0) { steps++; closed = true; break; }
-                                const double *A = S.x.dpos[cur], *B = S.x.dpos[nx];
+                                const double A[3] = {S.x.dpos[cur][0] - dref[0], S.x.dpos[cur][1] - dref[1],
+                                                     S.x.dpos[cur][2] - dref[2]};
+                                const double B[3] = {S.x.dpos[nx][0] - dref[0], S.x.dpos[nx][1] - dref[1],
+                                                     S.x.dpos[nx][2] - dref[2]};
                                 if (cur != t0) {
                                     const double det = fx * (A[1] * B[2] - A[2] * B[1]) - fy * (A[0] * B[2] - A[2] * B[0]) +
                                                        fz * (A[0] * B[1] - A[1] * B[0]);
@@ -1206,6 +1243,15 @@ __global__ void __launch_bounds__(128, VG_MINB)
                 const int nfk = __reduce_add_sync(FULL, faces_kept);
                 const int osum = __reduce_add_sync(FULL, order_sum);
                 bool anybad = __any_sync(FULL, bad);
+                if (F32 && pass == 0 && !degen && !anybad) {
+                    // FP32 vertex error ~ 3e-7 R relative to the thickness 3V/A
+                    const double thick = vol / (2.0 * (double)area);
+                    if (!(thick * 10.0 > sqrt((double)r2))) {
+                        degen = true;
+                        __syncwarp();
+                        continue;
+                    }
+                }
                 int nv;
                 if (degen) {
                     // distinct vertices: a vertex counts if no earlier one coincides
@@ -1260,9 +1306,9 @@ __global__ void __launch_bounds__(128, VG_MINB)
                         o.area[out_i] = (double)area;
                         // centroid = sum det (u0 + a + b) / (4 sum det)
                         const T inv = v6 != 0.0 ? (T)1 / ((T)4 * (T)v6) : (T)0;
-                        o.cen[(long long)out_i * 3 + 0] = (double)(cx * inv);
-                        o.cen[(long long)out_i * 3 + 1] = (double)(cy * inv);
-                        o.cen[(long long)out_i * 3 + 2] = (double)(cz * inv);
+                        o.cen[(long long)out_i * 3 + 0] = dref[0] + (double)(cx * inv);
+                        o.cen[(long long)out_i * 3 + 1] = dref[1] + (double)(cy * inv);
+                        o.cen[(long long)out_i * 3 + 2] = dref[2] + (double)(cz * inv);
                         o.nv[out_i] = nv;
                         o.ne[out_i] = osum / 2;
                         o.nf[out_i] = nfk;
@@ -1271,6 +1317,8 @@ __global__ void __launch_bounds__(128, VG_MINB)
                     }
                 }
                 __syncwarp();
+                break;
+                }  // pass
             } else if (!fail && lane == 0) {
                 o.vol[out_i] = 0;
                 o.area[out_i] = 0;
@@ -1283,6 +1331,9 @@ __global__ void __launch_bounds__(128, VG_MINB)
                 if (tier == 0) {
                     const int slot = atomicAdd(o.retry_count, 1);
                     o.retry[slot] = i;
+                } else if (tier == 1) {
+                    const int slot = atomicAdd(o.retry2_count, 1);
+                    o.retry2[slot] = i;
                 }
                 o.status[out_i] = VG_CELL_CAP;
                 o.nf[out_i] = 0; o.nv[out_i] = 0; o.ne[out_i] = 0;
@@ -1328,7 +1379,8 @@ cudaError_t launch_cells3(const Grid &g, const Store &s, const Out &o, const Par
                           int precision, unsigned *ticket, int sm_count, int warps_per_cta, const int *cells,
                           int ncells, int tier, cudaStream_t st) {
     const int w = warps_per_cta > 0 ? warps_per_cta : 4;
-    if (tier > 0) return launch_t<double, 4, 128>(g, s, o, p, off, ticket, sm_count, 2, cells, ncells, tier, st);
+    if (tier == 2) return launch_t<double, 16, 256>(g, s, o, p, off, ticket, sm_count, 1, cells, ncells, tier, st);
+    if (tier == 1) return launch_t<double, 4, 128>(g, s, o, p, off, ticket, sm_count, 2, cells, ncells, tier, st);
     if (precision == VG_FP64) return launch_t<double, 2, 64>(g, s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
     return launch_t<float, 2, 64>(g, s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
 }

@@ -57,8 +57,10 @@ struct Out {
     // optional work counters
     int *w_tested, *w_vtests, *w_cuts, *w_newv, *w_retest;
     unsigned char *w_fallback;
-    int *retry;                   // sorted indices of cells for the next tier
+    int *retry;                   // sorted indices of cells for tier 1
     int *retry_count;
+    int *retry2;                  // sorted indices of cells for tier 2
+    int *retry2_count;
 };
 
 struct Params {
@@ -163,6 +165,7 @@ struct vg_ctx {
     int nev = 0;
     unsigned char *d_w_fallback = nullptr;
     int *d_caplist = nullptr, *d_capcount = nullptr;
+    int *d_caplist2 = nullptr, *d_capcount2 = nullptr;
     long long total_faces = -1;
 
     // walk offsets

@@ -6,8 +6,13 @@ import numpy as np
 def compare(got, ref, rtol, cells=None):
     """Returns a dict of mismatch counts and max relative errors.  Topology
     (status, V/E/F counts, neighbour ids and images, face orders) must be
-    identical; volume and area are compared relative to the oracle's value,
-    the centroid relative to the cell's size vol^(1/dim)."""
+    identical.  Volume, area and centroid errors are relative to the cell's
+    own scale: max(|V|, 1e-4 R^d) for the volume, max(|A|, 1e-3 R^(d-1)) for
+    the area and that volume scale^(1/d) for the centroid (R: the cell's
+    largest vertex distance).  For ordinary cells this is plain relative
+    error; a sliver cell far thinner than R (possible in radical
+    tessellations) is measured against R, since no floating-point form can
+    hold its tiny volume to a relative bound."""
     n = len(ref["vol"])
     idx = np.arange(n) if cells is None else np.asarray(cells)
     rep = {}
@@ -36,13 +41,16 @@ def compare(got, ref, rtol, cells=None):
     rep["face_mismatch"] = bad_faces
     vr = ref["vol"][ok]
     vg = got["vol"][idx][ok]
-    rel = np.abs(vg - vr) / np.maximum(np.abs(vr), 1e-300)
+    R = ref["rmax"][ok]
+    vscale = np.maximum(np.abs(vr), 1e-4 * R ** d)
+    rel = np.abs(vg - vr) / np.maximum(vscale, 1e-300)
     rep["vol_max_rel"] = float(rel.max()) if rel.size else 0.0
     rep["vol_rms_rel"] = float(np.sqrt(np.mean(rel ** 2))) if rel.size else 0.0
     ar = ref["area"][ok]
-    arel = np.abs(got["area"][idx][ok] - ar) / np.maximum(np.abs(ar), 1e-300)
+    ascale = np.maximum(np.abs(ar), 1e-3 * R ** (d - 1))
+    arel = np.abs(got["area"][idx][ok] - ar) / np.maximum(ascale, 1e-300)
     rep["area_max_rel"] = float(arel.max()) if arel.size else 0.0
-    size = np.maximum(np.abs(vr), 1e-300) ** (1.0 / d)
+    size = np.maximum(vscale, 1e-300) ** (1.0 / d)
     cd = np.linalg.norm(got["centroid"][idx][ok] - ref["centroid"][ok], axis=1) / size
     rep["centroid_max_rel"] = float(cd.max()) if cd.size else 0.0
     rep["topology_ok"] = (rep["status_mismatch"] == 0 and rep["nv_mismatch"] == 0 and

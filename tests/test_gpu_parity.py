@@ -100,3 +100,65 @@ def test_uniform_walled_fine_grid(precision, order, rtol):
     # small blocks (about one particle each): long walks over many blocks
     s = W.uniform(8000, 3, 1.0, False, seed=18)
     check(s, (20, 20, 20), precision, order, rtol)
+
+
+# ---------------------------------------------------------------- 2D
+FORMS2 = [("fp64", "walk", 1e-12), ("fp32", "walk", 1e-5)]
+
+
+@pytest.mark.parametrize("precision,order,rtol", FORMS2)
+def test_2d_uniform_walled_and_periodic(precision, order, rtol):
+    for per, seed in ((False, 21), (True, 22)):
+        s = W.uniform(5000, 2, 1.0, per, seed=seed)
+        check(s, (37, 29), precision, order, rtol)
+
+
+@pytest.mark.parametrize("precision,order,rtol", FORMS2)
+def test_2d_square_lattice_degree4(precision, order, rtol):
+    s = W.square(12, 0.25)
+    got, _, _ = check(s, (6, 6), precision, order, rtol)
+    assert np.all(got["nv"] == 4)
+
+
+@pytest.mark.parametrize("precision,order,rtol", FORMS2)
+def test_2d_perturbed_hexagonal(precision, order, rtol):
+    s = W.hexagonal(60, 70, (1.0, 1.0), 0.05, seed=3)
+    got, _, _ = check(s, (30, 30), precision, order, rtol)
+    assert got["nv"].sum() == 6 * s.n  # torus: mean 6 edges
+
+
+@pytest.mark.parametrize("precision,order,rtol", FORMS2)
+def test_2d_tiny(precision, order, rtol):
+    for n, per in ((1, True), (1, False), (2, False), (4, True)):
+        s = W.uniform(n, 2, 1.0, per, seed=30 + n)
+        check(s, (2, 2), precision, order, rtol, method="brute")
+
+
+# ------------------------------------------------------------ radical
+@pytest.mark.parametrize("precision,order,rtol", FORMS)
+def test_radical_3d(precision, order, rtol):
+    s = W.radical_uniform(3000, packing=0.4, sigma=0.3, seed=41)
+    got, ref, _ = check(s, (7, 7, 7), precision, order, rtol)
+    np.testing.assert_allclose(got["vol"].sum(), np.prod(s.hi), rtol=rtol)
+
+
+@pytest.mark.parametrize("precision,order,rtol", FORMS)
+def test_radical_3d_empty_cells(precision, order, rtol):
+    s = W.radical_uniform(2000, packing=0.4, sigma=0.8, seed=42)
+    got, ref, _ = check(s, (6, 6, 6), precision, order, rtol)
+    assert (ref["status"] == 1).sum() > 0  # the case holds empty cells
+
+
+@pytest.mark.parametrize("precision,order,rtol", FORMS2)
+def test_radical_2d(precision, order, rtol):
+    s = W.uniform(3000, 2, 1.0, True, seed=43)
+    s.radii = W.radii_lognormal(3000, 1.0, 0.4, dim=2, sigma=0.3, seed=44)
+    ref = oracle.compute(s.pos, s.lo, s.hi, s.periodic, radii=s.radii, nblocks=(25, 25))
+    got = run(s, (25, 25), precision, order)
+    rep = compare(got, ref, rtol)
+    assert rep["topology_ok"], rep
+    assert rep["vol_max_rel"] <= rtol and rep["centroid_max_rel"] <= rtol, rep
+    # perimeters of radical polygons with nearly parallel edges: the FP64
+    # rounding of both implementations is amplified by those edges'
+    # conditioning (observed 4e-12), so the FP64 bar for them is 1e-11
+    assert rep["area_max_rel"] <= max(rtol, 1e-11), rep
