@@ -119,6 +119,44 @@ vg_status vg_create(vg_ctx **out, int dim, const double *lo, const double *hi,
                     void *stream);
 
 /*
+ * One particle system of a batched container: its box, periodic flags and
+ * block grid exactly as the arguments of vg_create() (nblocks all > 0: fixed
+ * counts; any <= 0: the n_opt rule at insert time).  Unused axes (dim = 2:
+ * index 2) are ignored.
+ */
+typedef struct {
+    double lo[3], hi[3];
+    int periodic[3];
+    int nblocks[3];
+    double n_opt;
+} vg_system;
+
+/*
+ * Creates a container of `nsys` independent systems that are sorted and
+ * computed together: one counting sort over all of them (the system's first
+ * block is added to every block key) and one persistent cell launch that
+ * takes cells of all systems from one work queue -- the GPU form of the
+ * paper's dynamic schedule over cells (Sec. 2.2.4), extended across systems.
+ * A system's cells see only its own particles.  `systems` is read during the
+ * call (caller-owned).  Errors: VG_ERR_ARG for dim not 2/3, nsys < 1, an
+ * empty box or a block count above 2^20.
+ */
+vg_status vg_batch_create(vg_ctx **out, int dim, int nsys, const vg_system *systems,
+                          void *stream);
+
+/*
+ * Replaces the particles of every system of a batched container.  counts[k]
+ * (nsys entries) particles belong to system k; `pos` holds all systems' rows
+ * one system after another (sum(counts) x dim doubles) and `radii` (or NULL)
+ * likewise.  Cell i and neighbour ids use this concatenated numbering, so
+ * system k's cells are the input indices [sum(counts[<k]), sum(counts[<=k])).
+ * Validation and errors as vg_insert(); the per-system n_opt rule fixes the
+ * grids here.
+ */
+vg_status vg_batch_insert(vg_ctx *ctx, const int64_t *counts, const double *pos,
+                          const double *radii, int on_device);
+
+/*
  * Replaces the container's particles (the paper's clear() followed by
  * add_parallel(), Sec. 2.2.5) and sorts them into blocks with a counting
  * sort on the GPU.  `pos` is n x dim doubles, row-major; `radii` is n doubles
@@ -133,6 +171,39 @@ vg_status vg_insert(vg_ctx *ctx, int64_t n, const double *pos, const double *rad
 
 /* Computes all cells with the given configuration (NULL: defaults). */
 vg_status vg_compute(vg_ctx *ctx, const vg_config *cfg);
+
+/*
+ * CUDA graph of one whole step (the paper has no counterpart; it replaces
+ * the per-step host work of vg_insert + vg_compute).  Captures, into a graph
+ * owned by the context: the counting sort of counts[k] particles of system k
+ * (one entry per system; one for a vg_create container) read from the DEVICE
+ * arrays `pos` (n x dim doubles) and `radii` (n doubles or NULL), the cell
+ * kernels with `cfg` (NULL: defaults) and the face compaction.  Before
+ * capturing it runs one eager vg_insert + vg_compute on the same input: that
+ * validates the input, sizes every buffer (the face buffer with 25 %
+ * headroom) and leaves valid results.  The caller keeps `pos` and `radii` at
+ * the same addresses while the graph exists and may overwrite their contents
+ * between replays (same counts).  Any later vg_insert, vg_batch_insert or
+ * vg_compute drops the graph.  With cfg->time_kernels = 1 every replay
+ * records the cell-kernel time read by vg_get_kernel_ms().
+ * Errors: VG_ERR_ARG (host input pointers, bad counts), those of vg_insert()
+ * and vg_compute(), VG_ERR_CUDA when capture or instantiation fails.
+ */
+vg_status vg_graph_capture(vg_ctx *ctx, const int64_t *counts, const double *pos,
+                           const double *radii, const vg_config *cfg);
+
+/* Replays the captured graph on the context's stream; asynchronous.
+ * VG_ERR_STATE when no graph is held. */
+vg_status vg_graph_launch(vg_ctx *ctx);
+
+/*
+ * Waits for the last replay and reads its flags: VG_ERR_OUT_OF_BOX or
+ * VG_ERR_NONFINITE as vg_insert() reports them; if the replay's input made
+ * more faces than the face buffer holds, the step is redone eagerly with a
+ * larger buffer and the graph re-captured (VG_OK, results complete).  The
+ * vg_get_* calls do this themselves after a replay.
+ */
+vg_status vg_graph_sync(vg_ctx *ctx);
 
 /* Number of cells and total number of faces (edges in 2D) of the last
  * vg_compute(); synchronises the stream. */
@@ -181,8 +252,9 @@ vg_status vg_get_kernel_ms(vg_ctx *ctx, double *total_ms, int64_t *count);
 
 /*
  * The sorted container: block_start has B+1 entries (B = product of the
- * block counts) and order[k] is the input index of the k-th particle in
- * block order.  For checking the counting sort; device or host output.
+ * block counts; for a batched container the sum over systems, system k's
+ * blocks following those of systems < k) and order[k] is the input index of
+ * the k-th particle in block order.  For checking the counting sort; device or host output.
  */
 vg_status vg_get_sorted(vg_ctx *ctx, int64_t *n_blocks, int32_t *block_start, int32_t *order,
                         int on_device);
@@ -191,8 +263,12 @@ vg_status vg_get_sorted(vg_ctx *ctx, int64_t *n_blocks, int32_t *block_start, in
  * (diagnostics: lets a caller count the GPU work behind a call). */
 vg_status vg_get_launches(vg_ctx *ctx, int64_t *count);
 
-/* The block counts in use (after vg_insert() when the n_opt rule applies). */
+/* The block counts in use (after vg_insert() when the n_opt rule applies);
+ * for a batched container, those of system 0. */
 vg_status vg_get_grid(vg_ctx *ctx, int *nblocks);
+
+/* The block counts of system k of a (batched) container. */
+vg_status vg_get_system_grid(vg_ctx *ctx, int k, int *nblocks);
 
 /*
  * Counting sort into blocks that allocates no device memory.  The paper has

@@ -1,5 +1,10 @@
 // Host side of the C ABI declared in include/vorogpu.h: argument checks,
 // device buffers, the sort -> cells -> faces pipeline, and result copies.
+//
+// A container holds one or more independent particle systems (vg_create: one;
+// vg_batch_create: many).  Their blocks and particles are numbered globally,
+// system after system, so one counting sort and one persistent cell launch
+// (cells taken from one atomic work queue) serve all of them.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -28,9 +33,9 @@ vg_status cuda_fail(vg_ctx *c, cudaError_t e, const char *where) {
     return fail(c, e == cudaErrorMemoryAllocation ? VG_ERR_OOM : VG_ERR_CUDA, m);
 }
 
-#define VG_CUDA(call)                                       \
-    do {                                                    \
-        cudaError_t e_ = (call);                            \
+#define VG_CUDA(call)                                          \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
         if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
     } while (0)
 
@@ -56,22 +61,22 @@ void release(T *&p) {
 }
 
 // Block counts from n_opt (Sec. 2.1.4), floor rounding as in Table 3.
-void grid_from_nopt(vg_ctx *c, long long n) {
+void grid_from_nopt(Grid &g, int dim, double n_opt, long long n) {
     double V = 1;
-    for (int a = 0; a < c->dim; a++) V *= c->g.L[a];
-    double nopt = c->n_opt > 0 ? c->n_opt : (c->dim == 3 ? 4.6 : 3.4);
-    double lam = pow((double)std::max<long long>(n, 1) / (nopt * V), 1.0 / c->dim);
-    for (int a = 0; a < c->dim; a++) {
-        long long v = (long long)floor(lam * c->g.L[a]);
-        c->g.nb[a] = (int)std::max<long long>(1, std::min<long long>(v, 1 << 20));
+    for (int a = 0; a < dim; a++) V *= g.L[a];
+    const double nopt = n_opt > 0 ? n_opt : (dim == 3 ? 4.6 : 3.4);
+    const double lam = pow((double)std::max<long long>(n, 1) / (nopt * V), 1.0 / dim);
+    for (int a = 0; a < dim; a++) {
+        const long long v = (long long)floor(lam * g.L[a]);
+        g.nb[a] = (int)std::max<long long>(1, std::min<long long>(v, 1 << 20));
     }
 }
 
-void finish_grid(vg_ctx *c) {
-    Grid &g = c->g;
+void finish_grid(Grid &g, int dim) {
+    g.dim = dim;
     g.nblk = 1;
     for (int a = 0; a < 3; a++) {
-        if (a >= c->dim) { g.nb[a] = 1; g.lo[a] = 0; g.hi[a] = 1; g.L[a] = 1; g.per[a] = 0; }
+        if (a >= dim) { g.nb[a] = 1; g.lo[a] = 0; g.hi[a] = 1; g.L[a] = 1; g.per[a] = 0; }
         g.h[a] = g.L[a] / g.nb[a];
         g.hf[a] = (float)g.h[a];
         g.Lf[a] = (float)g.L[a];
@@ -79,59 +84,99 @@ void finish_grid(vg_ctx *c) {
     }
 }
 
-// Sorted list of block offsets for the walk: all offsets whose distance
-// bound from the home block lies below shell * h_min, ascending.
-vg_status build_offsets(vg_ctx *c) {
-    const Grid &g = c->g;
-    int S = 4;
+// Appends the sorted list of block offsets for the walk of one grid: all
+// offsets whose distance bound from the home block lies below shell * h_min,
+// ascending by that bound (then by L1 length).
+void offsets_for(const Grid &g, int dim, int S, std::vector<int> &code, std::vector<float> &lbv) {
     double hmin = 1e300;
-    for (int a = 0; a < c->dim; a++) hmin = std::min(hmin, g.h[a]);
+    for (int a = 0; a < dim; a++) hmin = std::min(hmin, g.h[a]);
     struct E { float lb; int l1; int code; };
     std::vector<E> v;
     int lim[3];
-    for (int a = 0; a < 3; a++) lim[a] = a < c->dim ? S : 0;
+    for (int a = 0; a < 3; a++) lim[a] = a < dim ? S : 0;
     for (int z = -lim[2]; z <= lim[2]; z++)
         for (int y = -lim[1]; y <= lim[1]; y++)
             for (int x = -lim[0]; x <= lim[0]; x++) {
-                int o[3] = {x, y, z};
+                const int o[3] = {x, y, z};
                 double lb2 = 0;
                 for (int a = 0; a < 3; a++) {
-                    double t = std::max(0, std::abs(o[a]) - 1) * (double)g.hf[a];
+                    const double t = std::max(0, std::abs(o[a]) - 1) * (double)g.hf[a];
                     lb2 += t * t;
                 }
-                float lb = (float)sqrt(lb2);
-                // the kernel's shell continuation skips offsets whose FP32
+                // the kernels' shell continuation skips offsets whose FP32
                 // bound is below shell*h_min; keep exactly those here
-                float lbx = fmaxf(0.f, (float)(std::abs(x) - 1)) * g.hf[0];
-                float lby = fmaxf(0.f, (float)(std::abs(y) - 1)) * g.hf[1];
-                float lbz = fmaxf(0.f, (float)(std::abs(z) - 1)) * g.hf[2];
-                float lbmax = (float)S * (float)hmin;
+                const float lbx = fmaxf(0.f, (float)(std::abs(x) - 1)) * g.hf[0];
+                const float lby = fmaxf(0.f, (float)(std::abs(y) - 1)) * g.hf[1];
+                const float lbz = fmaxf(0.f, (float)(std::abs(z) - 1)) * g.hf[2];
+                const float lbmax = (float)S * (float)hmin;
                 if (!(lbx * lbx + lby * lby + lbz * lbz < lbmax * lbmax)) continue;
-                int code = (x & 0xff) | ((y & 0xff) << 8) | ((z & 0xff) << 16);
-                v.push_back({lb, std::abs(x) + std::abs(y) + std::abs(z), code});
+                v.push_back({(float)sqrt(lb2), std::abs(x) + std::abs(y) + std::abs(z),
+                             (x & 0xff) | ((y & 0xff) << 8) | ((z & 0xff) << 16)});
             }
     std::stable_sort(v.begin(), v.end(), [](const E &a, const E &b) {
         if (a.lb != b.lb) return a.lb < b.lb;
         return a.l1 < b.l1;
     });
-    std::vector<int> code(v.size());
-    std::vector<float> lb(v.size());
-    for (size_t i = 0; i < v.size(); i++) { code[i] = v[i].code; lb[i] = v[i].lb; }
-    release(c->d_off_code);
-    release(c->d_off_lb);
-    VG_CUDA(cudaMalloc((void **)&c->d_off_code, sizeof(int) * code.size()));
-    VG_CUDA(cudaMalloc((void **)&c->d_off_lb, sizeof(float) * lb.size()));
-    VG_CUDA(cudaMemcpy(c->d_off_code, code.data(), sizeof(int) * code.size(), cudaMemcpyHostToDevice));
-    VG_CUDA(cudaMemcpy(c->d_off_lb, lb.data(), sizeof(float) * lb.size(), cudaMemcpyHostToDevice));
-    c->off_count = (int)code.size();
-    c->off_shell = S;
-    return VG_OK;
+    for (const E &e : v) { code.push_back(e.code); lbv.push_back(e.lb); }
 }
 
-bool is_device_ptr(const void *p) {
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return false; }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+bool same_offsets(const Grid &a, const Grid &b, int dim) {
+    for (int k = 0; k < dim; k++)
+        if (a.hf[k] != b.hf[k] || a.h[k] != b.h[k]) return false;
+    return true;
+}
+
+// Fixes every system's grid (the n_opt rule where not given), numbers the
+// blocks and particles globally, builds the offset lists and uploads the
+// descriptors.  r_max starts at 0; system_rmax() fills it on the device.
+vg_status layout_systems(vg_ctx *c, const std::vector<long long> &counts) {
+    const int d = c->dim;
+    std::vector<int> code;
+    std::vector<float> lbv;
+    long long blk = 0, pbase = 0;
+    const int S = 4;
+    for (size_t k = 0; k < c->sys.size(); k++) {
+        Sys &s = c->sys[k];
+        if (!c->sys_fixed[k]) grid_from_nopt(s.g, d, c->sys_nopt[k], counts[k]);
+        finish_grid(s.g, d);
+        double V = 1;
+        for (int a = 0; a < d; a++) V *= s.g.L[a];
+        s.g.s = pow(V / (double)std::max<long long>(counts[k], 1), 1.0 / d);
+        s.blk_base = blk;
+        s.p_base = pbase;
+        s.n = counts[k];
+        s.rmax = 0;
+        blk += s.g.nblk;
+        pbase += counts[k];
+        // systems with the same block sides share one offset list
+        int shared = -1;
+        for (size_t q = 0; q < k && shared < 0; q++)
+            if (same_offsets(c->sys[q].g, s.g, d)) shared = (int)q;
+        if (shared >= 0) {
+            s.off_base = c->sys[shared].off_base;
+            s.off_count = c->sys[shared].off_count;
+        } else {
+            s.off_base = (int)code.size();
+            offsets_for(s.g, d, S, code, lbv);
+            s.off_count = (int)code.size() - s.off_base;
+        }
+        s.off_shell = S;
+    }
+    if (blk > (1ll << 31) - 2) return fail(c, VG_ERR_ARG, "too many blocks in total");
+    c->total_blk = blk;
+    c->g = c->sys[0].g;
+    VG_CUDA(ensure(c, c->d_off_code, (long long)code.size()));
+    VG_CUDA(ensure(c, c->d_off_lb, (long long)lbv.size()));
+    VG_CUDA(ensure(c, c->d_sys, (long long)c->sys.size()));
+    VG_CUDA(ensure(c, c->d_sys_init, (long long)c->sys.size()));
+    VG_CUDA(cudaMemcpyAsync(c->d_off_code, code.data(), sizeof(int) * code.size(), cudaMemcpyHostToDevice,
+                            c->stream));
+    VG_CUDA(cudaMemcpyAsync(c->d_off_lb, lbv.data(), sizeof(float) * lbv.size(), cudaMemcpyHostToDevice, c->stream));
+    VG_CUDA(cudaMemcpyAsync(c->d_sys_init, c->sys.data(), sizeof(Sys) * c->sys.size(), cudaMemcpyHostToDevice,
+                            c->stream));
+    // the host vectors must outlive the asynchronous copies
+    VG_CUDA(cudaStreamSynchronize(c->stream));
+    return VG_OK;
 }
 
 vg_status copy_out(vg_ctx *c, void *dst, const void *src, size_t bytes, int on_device) {
@@ -144,6 +189,216 @@ vg_status copy_out(vg_ctx *c, void *dst, const void *src, size_t bytes, int on_d
     }
     return VG_OK;
 }
+
+bool box_ok(int dim, const double *lo, const double *hi) {
+    for (int a = 0; a < dim; a++)
+        if (!isfinite(lo[a]) || !isfinite(hi[a]) || !(hi[a] > lo[a])) return false;
+    return true;
+}
+
+// A context on the current device with its small fixed buffers.
+vg_status new_context(vg_ctx **made, int dim, void *stream) {
+    *made = nullptr;
+    vg_ctx *c = new (std::nothrow) vg_ctx();
+    if (!c) return VG_ERR_OOM;
+    c->dim = dim;
+    c->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return VG_ERR_CUDA;
+    }
+    cudaError_t e = cudaMalloc((void **)&c->d_err, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_fcount, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_ticket, sizeof(unsigned) * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_capcount, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_capcount2, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        vg_destroy(c);
+        return e == cudaErrorMemoryAllocation ? VG_ERR_OOM : VG_ERR_CUDA;
+    }
+    *made = c;
+    return VG_OK;
+}
+
+void release_graph(vg_ctx *c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    c->gev_node[0] = c->gev_node[1] = nullptr;
+    c->graph_unchecked = 0;
+}
+
+// Host half of an insert: validation, layout of the systems, buffers, and
+// the copy of host input to the device.  Returns the device input pointers.
+vg_status prepare_insert(vg_ctx *c, const std::vector<long long> &counts, const double *pos, const double *radii,
+                         int on_device, const double **dpos, const double **drad) {
+    long long n = 0;
+    for (long long k : counts) n += k;
+    if (n > 0x7ffffffe) return fail(c, VG_ERR_ARG, "particle count out of range");
+    if (n > 0 && !pos) return fail(c, VG_ERR_ARG, "pos is NULL");
+    // buffers may move below: a captured graph would point at freed memory
+    release_graph(c);
+    c->inserted = 0;
+    c->computed = 0;
+    const int d = c->dim;
+    vg_status ls = layout_systems(c, counts);
+    if (ls != VG_OK) return ls;
+    VG_CUDA(ensure(c, c->d_key, n));
+    VG_CUDA(ensure(c, c->d_slot, n));
+    VG_CUDA(ensure(c, c->d_tmp, n));
+    VG_CUDA(ensure(c, c->d_p32, n));
+    VG_CUDA(ensure(c, c->d_p64, n));
+    VG_CUDA(ensure(c, c->d_sid, n));
+    VG_CUDA(ensure(c, c->d_sblk, n));
+    VG_CUDA(ensure(c, c->d_ssys, n));
+    VG_CUDA(ensure(c, c->d_vol, n));
+    VG_CUDA(ensure(c, c->d_area, n));
+    VG_CUDA(ensure(c, c->d_cen, n * 3));
+    VG_CUDA(ensure(c, c->d_nv, n));
+    VG_CUDA(ensure(c, c->d_ne, n));
+    VG_CUDA(ensure(c, c->d_nf, n));
+    VG_CUDA(ensure(c, c->d_status, n));
+    VG_CUDA(ensure(c, c->d_fptr, n));
+    VG_CUDA(ensure(c, c->d_face_off, n + 1));
+    VG_CUDA(ensure(c, c->d_caplist, n));
+    VG_CUDA(ensure(c, c->d_caplist2, n));
+    VG_CUDA(ensure(c, c->d_w_tested, n));
+    VG_CUDA(ensure(c, c->d_w_vtests, n));
+    VG_CUDA(ensure(c, c->d_w_cuts, n));
+    VG_CUDA(ensure(c, c->d_w_retest, n));
+    VG_CUDA(ensure(c, c->d_w_newv, n));
+    VG_CUDA(ensure(c, c->d_w_fallback, n));
+    if (!on_device) {
+        VG_CUDA(ensure(c, c->d_pos, n * d));
+        if (radii) VG_CUDA(ensure(c, c->d_rad, n));
+    }
+    VG_CUDA(ensure(c, c->d_count, c->total_blk));
+    VG_CUDA(ensure(c, c->d_bstart, c->total_blk + 1));
+    const size_t need_scan = std::max(scan_tmp_bytes_i32(c->total_blk + 1),
+                                      (((size_t)n * sizeof(int) + 255) & ~(size_t)255) + scan_tmp_bytes_i64(n + 1));
+    if (need_scan > c->scan_bytes) {
+        if (c->d_scan) cudaFree(c->d_scan);
+        c->d_scan = nullptr;
+        c->scan_bytes = 0;
+        VG_CUDA(cudaMalloc(&c->d_scan, need_scan));
+        c->scan_bytes = need_scan;
+    }
+    *dpos = pos;
+    *drad = radii;
+    if (n > 0 && !on_device) {
+        VG_CUDA(cudaMemcpyAsync(c->d_pos, pos, sizeof(double) * n * d, cudaMemcpyHostToDevice, c->stream));
+        *dpos = c->d_pos;
+        if (radii) {
+            VG_CUDA(cudaMemcpyAsync(c->d_rad, radii, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+            *drad = c->d_rad;
+        }
+    }
+    c->n = n;
+    c->radical = radii != nullptr;
+    return VG_OK;
+}
+
+// Device half of an insert: the counting sort of all systems, enqueued on
+// `s` with no host synchronisation (so it can be captured in a graph).
+cudaError_t enqueue_sort(vg_ctx *c, const double *dpos, const double *drad, cudaStream_t s) {
+    const int nsys = (int)c->sys.size();
+    // fresh descriptors: r_max is accumulated from 0 by system_rmax
+    cudaError_t e = cudaMemcpyAsync(c->d_sys, c->d_sys_init, sizeof(Sys) * nsys, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && drad) e = system_rmax(c->d_sys, nsys, c->n, drad, s);
+    if (e == cudaSuccess)
+        e = sort_particles(c->d_sys, nsys, c->dim, c->total_blk, c->n, dpos, drad, c->d_key, c->d_slot, c->d_count,
+                           c->d_bstart, c->d_tmp, c->d_p32, c->d_p64, c->d_sid, c->d_sblk, c->d_ssys, c->d_err,
+                           c->d_scan, s);
+    return e;
+}
+
+// Input errors the sort flagged (read after the stream has drained).
+vg_status read_input_flags(vg_ctx *c) {
+    int herr[2] = {0, 0};
+    VG_CUDA(cudaMemcpyAsync(herr, c->d_err, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->stream));
+    VG_CUDA(cudaStreamSynchronize(c->stream));
+    if (herr[1]) return fail(c, VG_ERR_NONFINITE, std::to_string(herr[1]) + " non-finite coordinates or radii");
+    if (herr[0]) return fail(c, VG_ERR_OUT_OF_BOX, std::to_string(herr[0]) + " particles outside a walled box");
+    return VG_OK;
+}
+
+// Shared by vg_insert and vg_batch_insert: counts[k] particles of system k,
+// all systems' rows concatenated in `pos` / `radii`.
+vg_status insert_all(vg_ctx *c, const std::vector<long long> &counts, const double *pos, const double *radii,
+                     int on_device) {
+    const double *dpos = nullptr, *drad = nullptr;
+    vg_status s = prepare_insert(c, counts, pos, radii, on_device, &dpos, &drad);
+    if (s != VG_OK) return s;
+    const long long l0 = g_launch_count;
+    cudaError_t e = enqueue_sort(c, dpos, drad, c->stream);
+    c->launches += g_launch_count - l0;
+    if (e != cudaSuccess) return cuda_fail(c, e, "sort_particles");
+    if ((s = read_input_flags(c)) != VG_OK) return s;
+    c->inserted = 1;
+    return VG_OK;
+}
+
+vg_status check_config(vg_ctx *c, const vg_config &cfg) {
+    if (cfg.precision != VG_FP64 && cfg.precision != VG_FP32_RETEST) return fail(c, VG_ERR_ARG, "precision");
+    if (cfg.order != VG_WALK && cfg.order != VG_PREFETCH) return fail(c, VG_ERR_ARG, "order");
+    if (!(cfg.tol32 > 0) || !(cfg.tau_rel > 0) || !(cfg.merge_rel > 0)) return fail(c, VG_ERR_ARG, "tolerances");
+    if (cfg.use_mlp && !c->d_kblock) return fail(c, VG_ERR_STATE, "use_mlp without MLP predictions");
+    return VG_OK;
+}
+
+// The three cell launches (tier 0 over all cells, then the large-cell
+// tiers over the cells the previous tier handed on), enqueued on `s`.
+cudaError_t enqueue_cells(vg_ctx *c, const vg_config &cfg, cudaStream_t s) {
+    Store st;
+    st.p32 = c->d_p32; st.p64 = c->d_p64; st.sid = c->d_sid; st.sblk = c->d_sblk; st.bstart = c->d_bstart;
+    st.ssys = c->d_ssys; st.sys = c->d_sys; st.sys0 = c->sys[0]; st.nsys = (int)c->sys.size();
+    st.n = (int)c->n; st.radical = c->radical;
+    Params pp;
+    pp.tol32 = cfg.tol32; pp.tau_rel = cfg.tau_rel; pp.merge_rel = cfg.merge_rel;
+    pp.prefetch_k = cfg.prefetch_k; pp.order = cfg.order;
+    pp.chunk = cfg.chunk > 0 ? cfg.chunk : 2;
+    pp.collect = cfg.collect_stats ? 1 : 0;
+    pp.kblock = cfg.use_mlp ? c->d_kblock : nullptr;
+    Offsets off;
+    off.code = c->d_off_code; off.lb = c->d_off_lb;
+    Out o;
+    o.vol = c->d_vol; o.area = c->d_area; o.cen = c->d_cen;
+    o.nv = c->d_nv; o.ne = c->d_ne; o.nf = c->d_nf; o.status = c->d_status;
+    o.fptr = c->d_fptr; o.faces = c->d_faces; o.fcount = c->d_fcount; o.fcap = c->fcap;
+    o.w_tested = c->d_w_tested; o.w_vtests = c->d_w_vtests; o.w_cuts = c->d_w_cuts;
+    o.w_retest = c->d_w_retest; o.w_fallback = c->d_w_fallback; o.w_newv = c->d_w_newv;
+    o.retry = c->d_caplist; o.retry_count = c->d_capcount;
+    o.retry2 = c->d_caplist2; o.retry2_count = c->d_capcount2;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(c->d_fcount, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_capcount, 0, sizeof(int), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_capcount2, 0, sizeof(int), s)) != cudaSuccess) return e;
+    auto launch = c->dim == 3 ? launch_cells3 : launch_cells2;
+    const int nc = (int)c->n;
+    if ((e = launch(st, o, pp, off, cfg.precision, c->d_ticket, c->sm_count, cfg.warps_per_cta, nullptr, nc, 0, s)))
+        return e;
+    if ((e = launch(st, o, pp, off, cfg.precision, c->d_ticket + 1, c->sm_count, 0, c->d_caplist, 0, 1, s))) return e;
+    return launch(st, o, pp, off, cfg.precision, c->d_ticket + 2, c->sm_count, 0, c->d_caplist2, 0, 2, s);
+}
+
+// CSR of the faces the cell kernels wrote.
+cudaError_t enqueue_compact(vg_ctx *c, cudaStream_t s) {
+    return compact_faces(c->n, c->d_nf, c->d_status, c->d_fptr, c->d_faces, c->fcap, c->d_face_off, c->d_nbr,
+                         c->d_img, c->d_ford, c->d_scan, s);
+}
+
+vg_status ensure_csr(vg_ctx *c) {
+    VG_CUDA(ensure(c, c->d_nbr, c->fcap));
+    VG_CUDA(ensure(c, c->d_img, 3 * c->fcap));
+    VG_CUDA(ensure(c, c->d_ford, c->fcap));
+    return VG_OK;
+}
+
+vg_status graph_check(vg_ctx *c);
 
 }  // namespace
 
@@ -170,143 +425,94 @@ vg_status vg_create(vg_ctx **out, int dim, const double *lo, const double *hi, c
     if (!out) return VG_ERR_ARG;
     *out = nullptr;
     if (dim != 2 && dim != 3) return VG_ERR_ARG;
-    if (!lo || !hi || !periodic) return VG_ERR_ARG;
-    vg_ctx *c = new (std::nothrow) vg_ctx();
-    if (!c) return VG_ERR_OOM;
-    c->dim = dim;
-    c->g.dim = dim;
-    for (int a = 0; a < dim; a++) {
-        if (!isfinite(lo[a]) || !isfinite(hi[a]) || !(hi[a] > lo[a])) {
-            delete c;
-            return VG_ERR_ARG;
-        }
-        c->g.lo[a] = lo[a];
-        c->g.hi[a] = hi[a];
-        c->g.L[a] = hi[a] - lo[a];
-        c->g.per[a] = periodic[a] ? 1 : 0;
-        c->g.nb[a] = 1;
-    }
+    if (!lo || !hi || !periodic || !box_ok(dim, lo, hi)) return VG_ERR_ARG;
     if (nblocks) {
-        for (int a = 0; a < dim; a++) {
-            if (nblocks[a] < 1 || nblocks[a] > (1 << 20)) { delete c; return VG_ERR_ARG; }
-            c->g.nb[a] = nblocks[a];
-        }
         long long prod = 1;
-        for (int a = 0; a < dim; a++) prod *= nblocks[a];
-        if (prod > (1ll << 30)) { delete c; return VG_ERR_ARG; }
-        c->grid_fixed = 1;
+        for (int a = 0; a < dim; a++) {
+            if (nblocks[a] < 1 || nblocks[a] > (1 << 20)) return VG_ERR_ARG;
+            prod *= nblocks[a];
+        }
+        if (prod > (1ll << 30)) return VG_ERR_ARG;
     }
+    vg_ctx *c = nullptr;
+    vg_status s = new_context(&c, dim, stream);
+    if (s != VG_OK) return s;
+    Sys sy{};
+    for (int a = 0; a < dim; a++) {
+        sy.g.lo[a] = lo[a];
+        sy.g.hi[a] = hi[a];
+        sy.g.L[a] = hi[a] - lo[a];
+        sy.g.per[a] = periodic[a] ? 1 : 0;
+        sy.g.nb[a] = nblocks ? nblocks[a] : 1;
+    }
+    finish_grid(sy.g, dim);
+    c->sys.push_back(sy);
+    c->sys_fixed.push_back(nblocks ? 1 : 0);
+    c->sys_nopt.push_back(n_opt);
+    c->grid_fixed = nblocks ? 1 : 0;
     c->n_opt = n_opt;
-    c->stream = (cudaStream_t)stream;
-    if (cudaGetDevice(&c->device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
-        cudaGetLastError();
-        delete c;
-        return VG_ERR_CUDA;
+    c->g = sy.g;
+    *out = c;
+    return VG_OK;
+}
+
+vg_status vg_batch_create(vg_ctx **out, int dim, int nsys, const vg_system *systems, void *stream) {
+    if (!out) return VG_ERR_ARG;
+    *out = nullptr;
+    if ((dim != 2 && dim != 3) || nsys < 1 || !systems) return VG_ERR_ARG;
+    std::vector<int> fixed(nsys, 1);
+    for (int k = 0; k < nsys; k++) {
+        if (!box_ok(dim, systems[k].lo, systems[k].hi)) return VG_ERR_ARG;
+        long long prod = 1;
+        for (int a = 0; a < dim; a++) {
+            if (systems[k].nblocks[a] <= 0) fixed[k] = 0;
+            if (systems[k].nblocks[a] > (1 << 20)) return VG_ERR_ARG;
+            prod *= std::max(1, systems[k].nblocks[a]);
+        }
+        if (prod > (1ll << 30)) return VG_ERR_ARG;
     }
-    finish_grid(c);
-    if (build_offsets(c) != VG_OK) { vg_destroy(c); return VG_ERR_CUDA; }
-    VG_CUDA(cudaMalloc((void **)&c->d_err, sizeof(int) * 4));
-    VG_CUDA(cudaMalloc((void **)&c->d_fcount, sizeof(unsigned long long)));
-    VG_CUDA(cudaMalloc((void **)&c->d_ticket, sizeof(unsigned) * 4));
-    VG_CUDA(cudaMalloc((void **)&c->d_capcount, sizeof(int)));
-    VG_CUDA(cudaMalloc((void **)&c->d_capcount2, sizeof(int)));
+    vg_ctx *c = nullptr;
+    vg_status s = new_context(&c, dim, stream);
+    if (s != VG_OK) return s;
+    c->batched = 1;
+    c->sys.reserve(nsys);
+    for (int k = 0; k < nsys; k++) {
+        const vg_system &in = systems[k];
+        Sys sy{};
+        for (int a = 0; a < dim; a++) {
+            sy.g.lo[a] = in.lo[a];
+            sy.g.hi[a] = in.hi[a];
+            sy.g.L[a] = in.hi[a] - in.lo[a];
+            sy.g.per[a] = in.periodic[a] ? 1 : 0;
+            sy.g.nb[a] = fixed[k] ? in.nblocks[a] : 1;
+        }
+        finish_grid(sy.g, dim);
+        c->sys.push_back(sy);
+        c->sys_fixed.push_back(fixed[k]);
+        c->sys_nopt.push_back(in.n_opt);
+    }
+    c->g = c->sys[0].g;
     *out = c;
     return VG_OK;
 }
 
 vg_status vg_insert(vg_ctx *c, int64_t n, const double *pos, const double *radii, int on_device) {
     if (!c) return VG_ERR_ARG;
-    if (n < 0 || n > 0x7ffffffe) return fail(c, VG_ERR_ARG, "particle count out of range");
-    if (n > 0 && !pos) return fail(c, VG_ERR_ARG, "pos is NULL");
-    c->inserted = 0;
-    c->computed = 0;
-    const int d = c->dim;
-    if (!c->grid_fixed) {
-        grid_from_nopt(c, n);
-        finish_grid(c);
-        vg_status s = build_offsets(c);
-        if (s != VG_OK) return s;
+    if (c->batched) return fail(c, VG_ERR_STATE, "batched container: use vg_batch_insert");
+    if (n < 0) return fail(c, VG_ERR_ARG, "negative particle count");
+    std::vector<long long> counts(1, (long long)n);
+    return insert_all(c, counts, pos, radii, on_device);
+}
+
+vg_status vg_batch_insert(vg_ctx *c, const int64_t *counts, const double *pos, const double *radii, int on_device) {
+    if (!c) return VG_ERR_ARG;
+    if (!counts) return fail(c, VG_ERR_ARG, "counts is NULL");
+    std::vector<long long> cv(c->sys.size());
+    for (size_t k = 0; k < cv.size(); k++) {
+        if (counts[k] < 0) return fail(c, VG_ERR_ARG, "negative particle count");
+        cv[k] = counts[k];
     }
-    double V = 1;
-    for (int a = 0; a < d; a++) V *= c->g.L[a];
-    c->g.s = pow(V / (double)std::max<int64_t>(n, 1), 1.0 / d);
-    VG_CUDA(ensure(c, c->d_key, n));
-    VG_CUDA(ensure(c, c->d_slot, n));
-    VG_CUDA(ensure(c, c->d_tmp, n));
-    VG_CUDA(ensure(c, c->d_p32, n));
-    VG_CUDA(ensure(c, c->d_p64, n));
-    VG_CUDA(ensure(c, c->d_sid, n));
-    VG_CUDA(ensure(c, c->d_sblk, n));
-    VG_CUDA(ensure(c, c->d_vol, n));
-    VG_CUDA(ensure(c, c->d_area, n));
-    VG_CUDA(ensure(c, c->d_cen, n * 3));
-    VG_CUDA(ensure(c, c->d_nv, n));
-    VG_CUDA(ensure(c, c->d_ne, n));
-    VG_CUDA(ensure(c, c->d_nf, n));
-    VG_CUDA(ensure(c, c->d_status, n));
-    VG_CUDA(ensure(c, c->d_fptr, n));
-    VG_CUDA(ensure(c, c->d_face_off, n + 1));
-    VG_CUDA(ensure(c, c->d_caplist, n));
-    VG_CUDA(ensure(c, c->d_caplist2, n));
-    VG_CUDA(ensure(c, c->d_w_tested, n));
-    VG_CUDA(ensure(c, c->d_w_vtests, n));
-    VG_CUDA(ensure(c, c->d_w_cuts, n));
-    VG_CUDA(ensure(c, c->d_w_retest, n));
-    VG_CUDA(ensure(c, c->d_w_newv, n));
-    VG_CUDA(ensure(c, c->d_w_fallback, n));
-    if (!on_device) {
-        VG_CUDA(ensure(c, c->d_pos, n * d));
-        if (radii) VG_CUDA(ensure(c, c->d_rad, n));
-    }
-    VG_CUDA(ensure(c, c->d_count, c->g.nblk));
-    VG_CUDA(ensure(c, c->d_bstart, c->g.nblk + 1));
-    size_t need_scan = std::max(scan_tmp_bytes_i32(c->g.nblk + 1),
-                                (((size_t)n * sizeof(int) + 255) & ~(size_t)255) + scan_tmp_bytes_i64(n + 1));
-    if (need_scan > c->scan_bytes) {
-        if (c->d_scan) cudaFree(c->d_scan);
-        c->d_scan = nullptr;
-        c->scan_bytes = 0;
-        VG_CUDA(cudaMalloc(&c->d_scan, need_scan));
-        c->scan_bytes = need_scan;
-    }
-    const double *dpos = pos, *drad = radii;
-    if (n > 0 && !on_device) {
-        VG_CUDA(cudaMemcpyAsync(c->d_pos, pos, sizeof(double) * n * d, cudaMemcpyHostToDevice, c->stream));
-        dpos = c->d_pos;
-        if (radii) {
-            VG_CUDA(cudaMemcpyAsync(c->d_rad, radii, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
-            drad = c->d_rad;
-        }
-    }
-    c->n = n;
-    c->radical = radii != nullptr;
-    c->rmax = 0;
-    if (radii) {
-        // the radical stop test needs the largest radius
-        std::vector<double> hr;
-        const double *src = radii;
-        if (on_device) {
-            hr.resize((size_t)n);
-            VG_CUDA(cudaMemcpyAsync(hr.data(), radii, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
-            VG_CUDA(cudaStreamSynchronize(c->stream));
-            src = hr.data();
-        }
-        for (int64_t i = 0; i < n; i++) if (src[i] > c->rmax) c->rmax = src[i];
-    }
-    const long long l0 = g_launch_count;
-    cudaError_t e = sort_particles(c->g, n, dpos, drad, c->d_key, c->d_slot, c->d_count, c->d_bstart,
-                                   c->d_tmp, c->d_p32, c->d_p64, c->d_sid, c->d_sblk, c->d_err,
-                                   c->d_scan, c->scan_bytes, c->stream);
-    c->launches += g_launch_count - l0;
-    if (e != cudaSuccess) return cuda_fail(c, e, "sort_particles");
-    int herr[2] = {0, 0};
-    VG_CUDA(cudaMemcpyAsync(herr, c->d_err, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->stream));
-    VG_CUDA(cudaStreamSynchronize(c->stream));
-    if (herr[1]) return fail(c, VG_ERR_NONFINITE, std::to_string(herr[1]) + " non-finite coordinates or radii");
-    if (herr[0]) return fail(c, VG_ERR_OUT_OF_BOX, std::to_string(herr[0]) + " particles outside a walled box");
-    c->inserted = 1;
-    return VG_OK;
+    return insert_all(c, cv, pos, radii, on_device);
 }
 
 vg_status vg_compute(vg_ctx *c, const vg_config *cfg_in) {
@@ -314,69 +520,28 @@ vg_status vg_compute(vg_ctx *c, const vg_config *cfg_in) {
     if (!c->inserted) return fail(c, VG_ERR_STATE, "vg_compute before vg_insert");
     vg_config cfg;
     if (cfg_in) cfg = *cfg_in; else vg_config_default(&cfg);
-    if (cfg.precision != VG_FP64 && cfg.precision != VG_FP32_RETEST) return fail(c, VG_ERR_ARG, "precision");
-    if (cfg.order != VG_WALK && cfg.order != VG_PREFETCH) return fail(c, VG_ERR_ARG, "order");
-    if (!(cfg.tol32 > 0) || !(cfg.tau_rel > 0) || !(cfg.merge_rel > 0)) return fail(c, VG_ERR_ARG, "tolerances");
-    if (cfg.use_mlp && !c->d_kblock) return fail(c, VG_ERR_STATE, "use_mlp without MLP predictions");
+    vg_status s = check_config(c, cfg);
+    if (s != VG_OK) return s;
+    if (c->graph_unchecked && (s = graph_check(c)) != VG_OK) return s;
+    // the face buffer may grow below: drop a captured graph
+    release_graph(c);
     const long long n = c->n;
     const long long l0 = g_launch_count;
     // face buffer: start at 24 faces per cell, grow on overflow
-    long long want = std::max<long long>(1024, n * 24);
+    const long long want = std::max<long long>(1024, n * 24);
     if (c->fcap < want) {
         VG_CUDA(ensure(c, c->d_faces, want));
         c->fcap = want;
     }
-    Store st;
-    st.p32 = c->d_p32; st.p64 = c->d_p64; st.sid = c->d_sid; st.sblk = c->d_sblk; st.bstart = c->d_bstart;
-    st.n = (int)n; st.radical = c->radical; st.rmax = c->rmax;
-    Params pp;
-    pp.tol32 = cfg.tol32; pp.tau_rel = cfg.tau_rel; pp.merge_rel = cfg.merge_rel;
-    pp.prefetch_k = cfg.prefetch_k; pp.order = cfg.order;
-    pp.chunk = cfg.chunk > 0 ? cfg.chunk : 2;
-    pp.collect = cfg.collect_stats ? 1 : 0;
-    pp.kblock = cfg.use_mlp ? c->d_kblock : nullptr;
-    Offsets off;
-    off.code = c->d_off_code; off.lb = c->d_off_lb; off.count = c->off_count; off.shell = c->off_shell;
     for (int attempt = 0; attempt < 4; attempt++) {
-        Out o;
-        o.vol = c->d_vol; o.area = c->d_area; o.cen = c->d_cen;
-        o.nv = c->d_nv; o.ne = c->d_ne; o.nf = c->d_nf; o.status = c->d_status;
-        o.fptr = c->d_fptr; o.faces = c->d_faces; o.fcount = c->d_fcount; o.fcap = c->fcap;
-        o.w_tested = c->d_w_tested; o.w_vtests = c->d_w_vtests; o.w_cuts = c->d_w_cuts;
-        o.w_retest = c->d_w_retest; o.w_fallback = c->d_w_fallback; o.w_newv = c->d_w_newv;
-        o.retry = c->d_caplist; o.retry_count = c->d_capcount;
-        o.retry2 = c->d_caplist2; o.retry2_count = c->d_capcount2;
-        VG_CUDA(cudaMemsetAsync(c->d_fcount, 0, sizeof(unsigned long long), c->stream));
-        VG_CUDA(cudaMemsetAsync(c->d_capcount, 0, sizeof(int), c->stream));
-        VG_CUDA(cudaMemsetAsync(c->d_capcount2, 0, sizeof(int), c->stream));
-        cudaError_t e;
         const bool timed = cfg.time_kernels && c->nev < vg_ctx::NEV;
         if (timed) {
             for (int k = 0; k < 2; k++)
                 if (!c->ev[2 * c->nev + k]) VG_CUDA(cudaEventCreate(&c->ev[2 * c->nev + k]));
             VG_CUDA(cudaEventRecord(c->ev[2 * c->nev], c->stream));
         }
-        if (c->dim == 3) {
-            e = launch_cells3(c->g, st, o, pp, off, cfg.precision, c->d_ticket, c->sm_count, cfg.warps_per_cta,
-                              nullptr, (int)n, 0, c->stream);
-            if (e != cudaSuccess) return cuda_fail(c, e, "launch_cells3");
-            e = launch_cells3(c->g, st, o, pp, off, cfg.precision, c->d_ticket + 1, c->sm_count, 0,
-                              c->d_caplist, 0, 1, c->stream);
-            if (e != cudaSuccess) return cuda_fail(c, e, "launch_cells3 (big cells)");
-            e = launch_cells3(c->g, st, o, pp, off, cfg.precision, c->d_ticket + 2, c->sm_count, 0,
-                              c->d_caplist2, 0, 2, c->stream);
-            if (e != cudaSuccess) return cuda_fail(c, e, "launch_cells3 (largest cells)");
-        } else {
-            e = launch_cells2(c->g, st, o, pp, off, cfg.precision, c->d_ticket, c->sm_count, cfg.warps_per_cta,
-                              nullptr, (int)n, 0, c->stream);
-            if (e != cudaSuccess) return cuda_fail(c, e, "launch_cells2");
-            e = launch_cells2(c->g, st, o, pp, off, cfg.precision, c->d_ticket + 1, c->sm_count, 0,
-                              c->d_caplist, 0, 1, c->stream);
-            if (e != cudaSuccess) return cuda_fail(c, e, "launch_cells2 (big cells)");
-            e = launch_cells2(c->g, st, o, pp, off, cfg.precision, c->d_ticket + 2, c->sm_count, 0,
-                              c->d_caplist2, 0, 2, c->stream);
-            if (e != cudaSuccess) return cuda_fail(c, e, "launch_cells2 (largest cells)");
-        }
+        cudaError_t e = enqueue_cells(c, cfg, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cell kernels");
         if (timed) {
             VG_CUDA(cudaEventRecord(c->ev[2 * c->nev + 1], c->stream));
             c->nev++;
@@ -384,32 +549,153 @@ vg_status vg_compute(vg_ctx *c, const vg_config *cfg_in) {
         unsigned long long used = 0;
         VG_CUDA(cudaMemcpyAsync(&used, c->d_fcount, sizeof used, cudaMemcpyDeviceToHost, c->stream));
         VG_CUDA(cudaStreamSynchronize(c->stream));
-        if ((long long)used <= c->fcap) {
-            c->total_faces = -1;
-            break;
-        }
+        if ((long long)used <= c->fcap) break;
+        if (attempt == 3) return fail(c, VG_ERR_CAP, "face buffer overflow");
         // face buffer too small: grow to what was asked for and recompute
-        long long need = (long long)(used * 5 / 4) + 1024;
+        const long long need = (long long)(used * 5 / 4) + 1024;
         VG_CUDA(ensure(c, c->d_faces, need));
         c->fcap = need;
-        if (attempt == 3) return fail(c, VG_ERR_CAP, "face buffer overflow");
     }
-    // CSR of faces
-    long long need_csr = c->fcap;
-    VG_CUDA(ensure(c, c->d_nbr, need_csr));
-    VG_CUDA(ensure(c, c->d_img, 3 * need_csr));
-    VG_CUDA(ensure(c, c->d_ford, need_csr));
-    cudaError_t e = compact_faces(n, c->d_nf, c->d_status, c->d_fptr, c->d_faces, c->d_face_off, c->d_nbr,
-                                  c->d_img, c->d_ford, c->d_scan, c->stream);
+    if ((s = ensure_csr(c)) != VG_OK) return s;
+    cudaError_t e = enqueue_compact(c, c->stream);
     c->launches += g_launch_count - l0;
     if (e != cudaSuccess) return cuda_fail(c, e, "compact_faces");
     c->computed = 1;
-    c->total_faces = -1;
     return VG_OK;
+}
+
+vg_status vg_graph_capture(vg_ctx *c, const int64_t *counts, const double *pos, const double *radii,
+                           const vg_config *cfg_in) {
+    if (!c) return VG_ERR_ARG;
+    vg_config cfg;
+    if (cfg_in) cfg = *cfg_in; else vg_config_default(&cfg);
+    vg_status s = check_config(c, cfg);
+    if (s != VG_OK) return s;
+    if (!counts) return fail(c, VG_ERR_ARG, "counts is NULL");
+    std::vector<long long> cv(c->sys.size());
+    long long n = 0;
+    for (size_t k = 0; k < cv.size(); k++) {
+        if (counts[k] < 0) return fail(c, VG_ERR_ARG, "negative particle count");
+        cv[k] = counts[k];
+        n += cv[k];
+    }
+    // a replay reads its input from fixed device addresses
+    for (const double *p : {pos, radii}) {
+        if (!p) continue;
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, VG_ERR_ARG, "graph input is not device memory");
+        }
+        if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+            return fail(c, VG_ERR_ARG, "graph input is not device memory");
+    }
+    std::vector<int64_t> keep(counts, counts + cv.size());
+    // one eager pass validates the input, sizes every buffer and leaves
+    // valid results
+    if ((s = insert_all(c, cv, pos, radii, 1)) != VG_OK) return s;
+    vg_config eager = cfg;
+    eager.time_kernels = 0;
+    if ((s = vg_compute(c, &eager)) != VG_OK) return s;
+    unsigned long long used = 0;
+    VG_CUDA(cudaMemcpyAsync(&used, c->d_fcount, sizeof used, cudaMemcpyDeviceToHost, c->stream));
+    VG_CUDA(cudaStreamSynchronize(c->stream));
+    // headroom for inputs that change between replays
+    const long long room = (long long)(used * 5 / 4) + 4096;
+    if (c->fcap < room) {
+        VG_CUDA(ensure(c, c->d_faces, room));
+        c->fcap = room;
+    }
+    if ((s = ensure_csr(c)) != VG_OK) return s;
+    if (!c->gstream) VG_CUDA(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+    const bool timed = cfg.time_kernels != 0;
+    if (timed)
+        for (int k = 0; k < 2; k++)
+            if (!c->gev[k]) VG_CUDA(cudaEventCreate(&c->gev[k]));
+    const long long l0 = g_launch_count;
+    cudaStream_t gs = c->gstream;
+    VG_CUDA(cudaStreamBeginCapture(gs, cudaStreamCaptureModeRelaxed));
+    cudaError_t e = enqueue_sort(c, pos, radii, gs);
+    if (e == cudaSuccess && timed) e = cudaEventRecordWithFlags(c->gev[0], gs, cudaEventRecordExternal);
+    if (e == cudaSuccess) e = enqueue_cells(c, cfg, gs);
+    if (e == cudaSuccess && timed) e = cudaEventRecordWithFlags(c->gev[1], gs, cudaEventRecordExternal);
+    if (e == cudaSuccess) e = enqueue_compact(c, gs);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(gs, &g);
+    const long long kernels = g_launch_count - l0;
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(c, e, "graph capture");
+    }
+    c->graph = g;
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    if (e != cudaSuccess) {
+        release_graph(c);
+        return cuda_fail(c, e, "cudaGraphInstantiate");
+    }
+    if (timed) {
+        size_t nn = 0;
+        VG_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        VG_CUDA(cudaGraphGetNodes(g, nodes.data(), &nn));
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType ty;
+            VG_CUDA(cudaGraphNodeGetType(nd, &ty));
+            if (ty != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t ev = nullptr;
+            VG_CUDA(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+            for (int k = 0; k < 2; k++)
+                if (ev == c->gev[k]) c->gev_node[k] = nd;
+        }
+        if (!c->gev_node[0] || !c->gev_node[1]) {
+            release_graph(c);
+            return fail(c, VG_ERR_CUDA, "graph capture lost its timing events");
+        }
+    }
+    c->graph_kernels = kernels;
+    c->graph_timed = timed ? 1 : 0;
+    c->g_counts = keep;
+    c->g_pos = pos;
+    c->g_rad = radii;
+    c->g_cfg = cfg;
+    return VG_OK;
+}
+
+vg_status vg_graph_launch(vg_ctx *c) {
+    if (!c) return VG_ERR_ARG;
+    if (!c->gexec) return fail(c, VG_ERR_STATE, "no captured graph");
+    if (c->graph_timed && c->nev < vg_ctx::NEV) {
+        for (int k = 0; k < 2; k++) {
+            cudaEvent_t &ev = c->ev[2 * c->nev + k];
+            if (!ev) VG_CUDA(cudaEventCreate(&ev));
+            VG_CUDA(cudaGraphExecEventRecordNodeSetEvent(c->gexec, c->gev_node[k], ev));
+        }
+        c->nev++;
+    }
+    VG_CUDA(cudaGraphLaunch(c->gexec, c->stream));
+    c->launches += c->graph_kernels;
+    c->inserted = 1;
+    c->computed = 1;
+    c->graph_unchecked = 1;
+    return VG_OK;
+}
+
+vg_status vg_graph_sync(vg_ctx *c) {
+    if (!c) return VG_ERR_ARG;
+    if (!c->graph_unchecked) {
+        VG_CUDA(cudaStreamSynchronize(c->stream));
+        return VG_OK;
+    }
+    return graph_check(c);
 }
 
 vg_status vg_get_counts(vg_ctx *c, int64_t *n_cells, int64_t *n_faces) {
     if (!c) return VG_ERR_ARG;
+    if (c->graph_unchecked) {
+        vg_status gs = graph_check(c);
+        if (gs != VG_OK) return gs;
+    }
     if (!c->computed) return fail(c, VG_ERR_STATE, "no computed cells");
     if (n_cells) *n_cells = c->n;
     if (n_faces) {
@@ -424,6 +710,10 @@ vg_status vg_get_counts(vg_ctx *c, int64_t *n_cells, int64_t *n_faces) {
 vg_status vg_get_cells(vg_ctx *c, double *vol, double *area, double *centroid, int32_t *nv, int32_t *ne,
                        int32_t *nf, uint8_t *status, int on_device) {
     if (!c) return VG_ERR_ARG;
+    if (c->graph_unchecked) {
+        vg_status gs = graph_check(c);
+        if (gs != VG_OK) return gs;
+    }
     if (!c->computed) return fail(c, VG_ERR_STATE, "no computed cells");
     const long long n = c->n;
     vg_status s;
@@ -432,11 +722,10 @@ vg_status vg_get_cells(vg_ctx *c, double *vol, double *area, double *centroid, i
     if (centroid) {
         if (c->dim == 3) {
             if ((s = copy_out(c, centroid, c->d_cen, sizeof(double) * n * 3, on_device))) return s;
-        } else {
+        } else if (n > 0) {
             // stored with stride 3; pack to n x 2
-            VG_CUDA(cudaMemcpy2DAsync(centroid, 2 * sizeof(double), c->d_cen, 3 * sizeof(double),
-                                      2 * sizeof(double), n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                      c->stream));
+            VG_CUDA(cudaMemcpy2DAsync(centroid, 2 * sizeof(double), c->d_cen, 3 * sizeof(double), 2 * sizeof(double),
+                                      n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
             if (!on_device) VG_CUDA(cudaStreamSynchronize(c->stream));
         }
     }
@@ -450,6 +739,10 @@ vg_status vg_get_cells(vg_ctx *c, double *vol, double *area, double *centroid, i
 vg_status vg_get_faces(vg_ctx *c, int64_t *face_off, int32_t *nbr_id, int8_t *nbr_img, uint8_t *face_order,
                        int on_device) {
     if (!c) return VG_ERR_ARG;
+    if (c->graph_unchecked) {
+        vg_status gs = graph_check(c);
+        if (gs != VG_OK) return gs;
+    }
     if (!c->computed) return fail(c, VG_ERR_STATE, "no computed cells");
     const long long n = c->n;
     long long t = 0;
@@ -481,6 +774,10 @@ vg_status vg_get_kernel_ms(vg_ctx *c, double *total_ms, int64_t *count) {
 vg_status vg_get_work(vg_ctx *c, int32_t *n_tested, int32_t *n_vtests, int32_t *n_cuts, int32_t *n_newv,
                       int32_t *n_retest, uint8_t *fallback, int on_device) {
     if (!c) return VG_ERR_ARG;
+    if (c->graph_unchecked) {
+        vg_status gs = graph_check(c);
+        if (gs != VG_OK) return gs;
+    }
     if (!c->computed) return fail(c, VG_ERR_STATE, "no computed cells");
     const long long n = c->n;
     vg_status s;
@@ -495,10 +792,14 @@ vg_status vg_get_work(vg_ctx *c, int32_t *n_tested, int32_t *n_vtests, int32_t *
 
 vg_status vg_get_sorted(vg_ctx *c, int64_t *n_blocks, int32_t *block_start, int32_t *order, int on_device) {
     if (!c) return VG_ERR_ARG;
+    if (c->graph_unchecked) {
+        vg_status gs = graph_check(c);
+        if (gs != VG_OK) return gs;
+    }
     if (!c->inserted) return fail(c, VG_ERR_STATE, "nothing inserted");
-    if (n_blocks) *n_blocks = c->g.nblk;
+    if (n_blocks) *n_blocks = c->total_blk;
     vg_status s;
-    if ((s = copy_out(c, block_start, c->d_bstart, sizeof(int) * (c->g.nblk + 1), on_device))) return s;
+    if ((s = copy_out(c, block_start, c->d_bstart, sizeof(int) * (c->total_blk + 1), on_device))) return s;
     if ((s = copy_out(c, order, c->d_sid, sizeof(int) * c->n, on_device))) return s;
     return VG_OK;
 }
@@ -511,7 +812,13 @@ vg_status vg_get_launches(vg_ctx *c, int64_t *count) {
 
 vg_status vg_get_grid(vg_ctx *c, int *nblocks) {
     if (!c || !nblocks) return VG_ERR_ARG;
-    for (int a = 0; a < c->dim; a++) nblocks[a] = c->g.nb[a];
+    for (int a = 0; a < c->dim; a++) nblocks[a] = c->sys[0].g.nb[a];
+    return VG_OK;
+}
+
+vg_status vg_get_system_grid(vg_ctx *c, int k, int *nblocks) {
+    if (!c || !nblocks || k < 0 || k >= (int)c->sys.size()) return VG_ERR_ARG;
+    for (int a = 0; a < c->dim; a++) nblocks[a] = c->sys[k].g.nb[a];
     return VG_OK;
 }
 
@@ -520,8 +827,8 @@ const char *vg_last_error(vg_ctx *c) { return c ? c->err.c_str() : "null context
 void vg_destroy(vg_ctx *c) {
     if (!c) return;
     release(c->d_pos); release(c->d_rad); release(c->d_key); release(c->d_slot); release(c->d_tmp);
-    release(c->d_p32); release(c->d_p64); release(c->d_sid); release(c->d_sblk); release(c->d_count);
-    release(c->d_bstart); release(c->d_err);
+    release(c->d_p32); release(c->d_p64); release(c->d_sid); release(c->d_sblk); release(c->d_ssys);
+    release(c->d_count); release(c->d_bstart); release(c->d_err); release(c->d_sys);
     if (c->d_scan) cudaFree(c->d_scan);
     release(c->d_vol); release(c->d_area); release(c->d_cen); release(c->d_nv); release(c->d_ne);
     release(c->d_nf); release(c->d_status); release(c->d_fptr); release(c->d_faces); release(c->d_fcount);
@@ -530,9 +837,37 @@ void vg_destroy(vg_ctx *c) {
     release(c->d_w_fallback); release(c->d_caplist); release(c->d_capcount);
     release(c->d_caplist2); release(c->d_capcount2);
     release(c->d_off_code); release(c->d_off_lb); release(c->d_kblock); release(c->d_w_newv);
+    release(c->d_sys_init);
+    release_graph(c);
+    for (int k = 0; k < 2; k++)
+        if (c->gev[k]) cudaEventDestroy(c->gev[k]);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
     for (int k = 0; k < 2 * vg_ctx::NEV; k++)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     delete c;
 }
 
 }  // extern "C"
+
+namespace {
+
+// Reads what a replay flagged: input errors, and a face buffer too small for
+// this replay's input -- then the step is redone eagerly (which grows the
+// buffer) and the graph re-captured, so the results are complete.
+vg_status graph_check(vg_ctx *c) {
+    c->graph_unchecked = 0;
+    vg_status s = read_input_flags(c);
+    if (s != VG_OK) {
+        c->computed = 0;
+        return s;
+    }
+    unsigned long long used = 0;
+    VG_CUDA(cudaMemcpyAsync(&used, c->d_fcount, sizeof used, cudaMemcpyDeviceToHost, c->stream));
+    VG_CUDA(cudaStreamSynchronize(c->stream));
+    if ((long long)used <= c->fcap) return VG_OK;
+    const std::vector<int64_t> counts = c->g_counts;
+    const vg_config cfg = c->g_cfg;
+    return vg_graph_capture(c, counts.data(), c->g_pos, c->g_rad, &cfg);
+}
+
+}  // namespace

@@ -47,6 +47,7 @@ __device__ __forceinline__ unsigned mkv(int a, int b) { return (unsigned)a | ((u
 struct CellC2 {
     int i, self_id, b[2];
     double p[2], rp;
+    double rmax;  // largest radius of the cell's system (radical) or 0
 };
 
 template <typename T, int CAP>
@@ -60,6 +61,8 @@ struct Smem2 {
     unsigned char nxt[MAXP2];  // vertex slot by arriving line
     CellC2 cc;
     int cnt[4];
+    Sys sysc;    // descriptor of the system of the current cell
+    int sys_id;
 };
 
 template <int G>
@@ -182,8 +185,8 @@ __device__ __forceinline__ void meet(typename P2<T>::t A, T bx, T by, T bc, T &x
     kap = fmaxf(1.f, sqrtf(m) / (fabsf((float)det) * KAP0_2));
 }
 
-template <typename T, int G, int CAP>
-__global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Grid g, const __grid_constant__ Store st,
+template <typename T, int G, int CAP, bool BATCH>
+__global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Store st,
                                                 const __grid_constant__ Out o, const __grid_constant__ Params pp,
                                                 const __grid_constant__ Offsets off, unsigned *ticket,
                                                 const int *cells, int ncells, int tier) {
@@ -197,7 +200,10 @@ __global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Grid g, 
     const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1) << gbase);
     S_t &S = reinterpret_cast<S_t *>(smem_raw)[warp * GPW + gid];
     const int total = cells ? (tier == 1 ? *o.retry_count : (tier == 2 ? *o.retry2_count : ncells)) : st.n;
-    const double tau_rel_s = pp.tau_rel * g.s;
+    if (gl == 0) S.sys_id = -1;
+    __syncwarp(gmask);
+    const Sys &SY = sys_ref<BATCH>(st, S.sysc);
+    const Grid &g = SY.g;
 
     for (int iter = 0; iter < (1 << 30); iter++) {
         int i = 0;
@@ -206,7 +212,20 @@ __global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Grid g, 
         if (i >= total) break;
         if (cells) i = cells[i];
         // ---------------------------------------------------------------- setup
-        const int kh = __ldg(&st.sblk[i]);
+        if constexpr (BATCH) {
+            // the cell's system descriptor, kept while consecutive cells share it
+            const int sidx = __ldg(&st.ssys[i]);
+            if (sidx != S.sys_id) {
+                __syncwarp(gmask);
+                const int *src32 = reinterpret_cast<const int *>(&st.sys[sidx]);
+                int *dst32 = reinterpret_cast<int *>(&S.sysc);
+                for (int u = gl; u < (int)(sizeof(Sys) / 4); u += G) dst32[u] = __ldg(&src32[u]);
+                if (gl == 0) S.sys_id = sidx;
+                __syncwarp(gmask);
+            }
+        }
+        const double tau_rel_s = pp.tau_rel * g.s;
+        const int kh = __ldg(&st.sblk[i]) - (int)SY.blk_base;
         const float4 p32 = __ldg(&st.p32[i]);
         const float o0 = p32.x, o1 = p32.y;
         if (gl == 0) {
@@ -217,6 +236,7 @@ __global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Grid g, 
             S.cc.b[1] = kh / g.nb[0];
             S.cc.p[0] = p64.x; S.cc.p[1] = p64.y;
             S.cc.rp = p64.w;
+            S.cc.rmax = st.radical ? (BATCH ? S.sysc.rmax : st.sys[0].rmax) : 0.0;
             S.cnt[0] = S.cnt[1] = S.cnt[2] = S.cnt[3] = 0;
         }
         __syncwarp(gmask);
@@ -286,7 +306,7 @@ __global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Grid g, 
         auto stop2 = [&]() -> T {
             const T margin = F32 ? (T)1.0001 : (T)(1.0 + 1e-12);
             if (!st.radical) return (T)4 * r2 * margin;
-            const T disc = r2 + (T)(st.rmax * st.rmax) - (T)(S.cc.rp * S.cc.rp);
+            const T disc = r2 + (T)(S.cc.rmax * S.cc.rmax) - (T)(S.cc.rp * S.cc.rp);
             if (disc <= (T)0) return (T)0;
             const T rs = sqrt(r2) + sqrt(disc);
             return rs * rs * margin;
@@ -296,15 +316,16 @@ __global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Grid g, 
 
         // ------------------------------------------- walk (Sec. 2.1.3), per block
         const float hmin = fminf(g.hf[0], g.hf[1]);
-        const int maxs = off.shell + 4 + 2 * max(g.nb[0], g.nb[1]);
+        const int maxs = SY.off_shell + 4 + 2 * max(g.nb[0], g.nb[1]);
+        const int ocount = SY.off_count, obase = SY.off_base;
         int e = 0, shell = 0, sidx = 0, mode = 1;  // 1 list, 2 shells, 3 done
         for (int guard = 0; guard < (1 << 30) && mode != 3 && !(flags & 6); guard++) {
             int ox = 0, oy = 0;
             if (mode == 1) {
-                if (e >= off.count) { mode = 2; shell = off.shell + 1; sidx = 0; continue; }
-                const float lbv = __ldg(&off.lb[e]);
+                if (e >= ocount) { mode = 2; shell = SY.off_shell + 1; sidx = 0; continue; }
+                const float lbv = __ldg(&off.lb[obase + e]);
                 if ((T)(lbv * lbv) * (T)0.99998 >= stop) { mode = 3; continue; }
-                const int code = __ldg(&off.code[e]);
+                const int code = __ldg(&off.code[obase + e]);
                 e++;
                 ox = imgc2(code, 0);
                 oy = imgc2(code, 1);
@@ -331,7 +352,7 @@ __global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Grid g, 
                 float gy = lo1 > 0.f ? lo1 : (lo1 + g.hf[1] < 0.f ? -(lo1 + g.hf[1]) : 0.f);
                 if ((T)(gx * gx + gy * gy) * (T)0.99998 >= stop) continue;
             }
-            const int kb = t0 + g.nb[0] * t1;
+            const int kb = (int)SY.blk_base + t0 + g.nb[0] * t1;
             const int j0 = __ldg(&st.bstart[kb]), j1 = __ldg(&st.bstart[kb + 1]);
             const int img = pack2(m0, m1);
             for (int jb = j0; jb < j1 && !(flags & 6); jb += G) {
@@ -662,12 +683,12 @@ __global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Grid g, 
     }
 }
 
-template <typename T, int G, int CAP>
-cudaError_t launch2_t(const Grid &g, const Store &s, const Out &o, const Params &p, const Offsets &off,
-                      unsigned *ticket, int sm_count, const int *cells, int ncells, int tier, cudaStream_t st) {
+template <typename T, int G, int CAP, bool BATCH>
+cudaError_t launch2_t(const Store &s, const Out &o, const Params &p, const Offsets &off, unsigned *ticket,
+                      int sm_count, const int *cells, int ncells, int tier, cudaStream_t st) {
     constexpr int threads = 128;
     const size_t smem = sizeof(Smem2<T, CAP>) * (threads / G);
-    auto kfn = k_cells2<T, G, CAP>;
+    auto kfn = k_cells2<T, G, CAP, BATCH>;
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -677,20 +698,25 @@ cudaError_t launch2_t(const Grid &g, const Store &s, const Out &o, const Params 
     const int grid = tier > 0 ? sm_count : sm_count * per_sm;
     if ((e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
     ++g_launch_count;
-    kfn<<<grid, threads, smem, st>>>(g, s, o, p, off, ticket, cells, ncells, tier);
+    kfn<<<grid, threads, smem, st>>>(s, o, p, off, ticket, cells, ncells, tier);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_cells2(const Grid &g, const Store &s, const Out &o, const Params &p, const Offsets &off,
-                          int precision, unsigned *ticket, int sm_count, int warps_per_cta, const int *cells,
-                          int ncells, int tier, cudaStream_t st) {
+cudaError_t launch_cells2(const Store &s, const Out &o, const Params &p, const Offsets &off, int precision,
+                          unsigned *ticket, int sm_count, int warps_per_cta, const int *cells, int ncells, int tier,
+                          cudaStream_t st) {
     (void)warps_per_cta;
-    if (tier == 2) return launch2_t<double, 32, 64>(g, s, o, p, off, ticket, sm_count, cells, ncells, tier, st);
-    if (tier == 1) return launch2_t<double, 16, 64>(g, s, o, p, off, ticket, sm_count, cells, ncells, tier, st);
-    if (precision == VG_FP64) return launch2_t<double, 8, 32>(g, s, o, p, off, ticket, sm_count, cells, ncells, 0, st);
-    return launch2_t<float, 8, 32>(g, s, o, p, off, ticket, sm_count, cells, ncells, 0, st);
+    // the rare large cells (tiers 1, 2) always take the batched form
+    if (tier == 2) return launch2_t<double, 32, 64, true>(s, o, p, off, ticket, sm_count, cells, ncells, tier, st);
+    if (tier == 1) return launch2_t<double, 16, 64, true>(s, o, p, off, ticket, sm_count, cells, ncells, tier, st);
+    const bool batch = s.nsys > 1;
+    if (precision == VG_FP64)
+        return batch ? launch2_t<double, 8, 32, true>(s, o, p, off, ticket, sm_count, cells, ncells, 0, st)
+                     : launch2_t<double, 8, 32, false>(s, o, p, off, ticket, sm_count, cells, ncells, 0, st);
+    return batch ? launch2_t<float, 8, 32, true>(s, o, p, off, ticket, sm_count, cells, ncells, 0, st)
+                 : launch2_t<float, 8, 32, false>(s, o, p, off, ticket, sm_count, cells, ncells, 0, st);
 }
 
 }  // namespace vg

@@ -80,6 +80,7 @@ struct CellC {
     int pad;
     double p[3];  // FP64 position
     double rp;    // radius (radical) or 0
+    double rmax;  // largest radius of the cell's system (radical) or 0
 };
 
 // Candidate source, warp-uniform.
@@ -129,6 +130,8 @@ struct Smem {
     CellC cc;
     Src src;
     int cnt[6];  // work counters
+    Sys sysc;    // descriptor of the system of the current cell
+    int sys_id;  // which system sysc holds (-1: none)
 };
 
 __device__ __forceinline__ int imgc(int img, int a) { return (int)(signed char)((img >> (8 * a)) & 0xff); }
@@ -329,9 +332,10 @@ __device__ __forceinline__ float block_gap2(const Grid &g, float o0, float o1, f
     return __fadd_rn(__fmul_rn(gx, gx), row_gap2(g, o1, o2, oy, oz));
 }
 
-// Block offset o -> linear block index and image shift; false outside a wall.
-__device__ __forceinline__ bool resolve(const Grid &g, const int *b, int ox, int oy, int oz, int &k, int &mx,
-                                        int &my, int &mz) {
+// Block offset o -> global block index (the system's first block `base`
+// plus the block inside the system) and image shift; false outside a wall.
+__device__ __forceinline__ bool resolve(const Grid &g, long long base, const int *b, int ox, int oy, int oz, int &k,
+                                        int &mx, int &my, int &mz) {
     int o[3] = {ox, oy, oz}, t[3], m[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
@@ -345,16 +349,16 @@ __device__ __forceinline__ bool resolve(const Grid &g, const int *b, int ox, int
         }
         t[a] = ta;
     }
-    k = t[0] + g.nb[0] * (t[1] + g.nb[1] * t[2]);
+    k = (int)base + t[0] + g.nb[0] * (t[1] + g.nb[1] * t[2]);
     mx = m[0]; my = m[1]; mz = m[2];
     return true;
 }
 
 // ---- the kernel ------------------------------------------------------------------
 
-template <typename T, int VPL, int MAXP>
+template <typename T, int VPL, int MAXP, bool BATCH>
 __global__ void __launch_bounds__(128, VG_MINB)
-    k_cells3(const __grid_constant__ Grid g, const __grid_constant__ Store st, const __grid_constant__ Out o,
+    k_cells3(const __grid_constant__ Store st, const __grid_constant__ Out o,
              const __grid_constant__ Params pp, const __grid_constant__ Offsets off, unsigned *ticket,
              const int *cells, int ncells, int tier) {
     constexpr bool F32 = sizeof(T) == 4;
@@ -368,7 +372,10 @@ __global__ void __launch_bounds__(128, VG_MINB)
     Src &src = S.src;
     // the edge matrix starts clear; every cut leaves it clear
     for (int u = lane; u < MAXP * NW; u += 32) (&S.E[0][0])[u] = 0ull;
+    if (lane == 0) S.sys_id = -1;
     __syncwarp();
+    const Sys &SY = sys_ref<BATCH>(st, S.sysc);
+    const Grid &g = SY.g;
     const int total = cells ? (tier == 1 ? *o.retry_count : (tier == 2 ? *o.retry2_count : ncells)) : st.n;
     const int chunk = pp.chunk > 0 ? pp.chunk : 1;
 
@@ -381,7 +388,20 @@ __global__ void __launch_bounds__(128, VG_MINB)
         for (int w = base; w < wend; w++) {
             const int i = cells ? cells[w] : w;
             // ---------------------------------------------------------- setup
+            if constexpr (BATCH) {
+                // the cell's system descriptor, kept while consecutive cells share it
+                const int sidx = __ldg(&st.ssys[i]);
+                if (sidx != S.sys_id) {
+                    __syncwarp();
+                    const int *src32 = reinterpret_cast<const int *>(&st.sys[sidx]);
+                    int *dst32 = reinterpret_cast<int *>(&S.sysc);
+                    for (int u = lane; u < (int)(sizeof(Sys) / 4); u += 32) dst32[u] = __ldg(&src32[u]);
+                    if (lane == 0) S.sys_id = sidx;
+                    __syncwarp();
+                }
+            }
             const int kh = __ldg(&st.sblk[i]);
+            const int khl = kh - (int)SY.blk_base;
             float o0, o1, o2, rp32;
             {
                 const float4 p32 = __ldg(&st.p32[i]);
@@ -390,11 +410,12 @@ __global__ void __launch_bounds__(128, VG_MINB)
                     const D4 p64 = st.p64[i];
                     S.cc.i = i;
                     S.cc.self_id = __ldg(&st.sid[i]);
-                    S.cc.b[0] = kh % g.nb[0];
-                    S.cc.b[1] = (kh / g.nb[0]) % g.nb[1];
-                    S.cc.b[2] = kh / (g.nb[0] * g.nb[1]);
+                    S.cc.b[0] = khl % g.nb[0];
+                    S.cc.b[1] = (khl / g.nb[0]) % g.nb[1];
+                    S.cc.b[2] = khl / (g.nb[0] * g.nb[1]);
                     S.cc.p[0] = p64.x; S.cc.p[1] = p64.y; S.cc.p[2] = p64.z;
                     S.cc.rp = p64.w;
+                    S.cc.rmax = st.radical ? (BATCH ? S.sysc.rmax : st.sys[0].rmax) : 0.0;
                 }
                 if (pp.collect && lane < 6) S.cnt[lane] = 0;
             }
@@ -475,7 +496,7 @@ __global__ void __launch_bounds__(128, VG_MINB)
             auto stop2 = [&]() -> T {
                 const T margin = F32 ? (T)1.0001 : (T)(1.0 + 1e-12);
                 if (!st.radical) return (T)4 * r2 * margin;
-                T disc = r2 + (T)(st.rmax * st.rmax) - (T)(S.cc.rp * S.cc.rp);
+                T disc = r2 + (T)(S.cc.rmax * S.cc.rmax) - (T)(S.cc.rp * S.cc.rp);
                 if (disc <= (T)0) return (T)0;
                 T rs = sqrt(r2) + sqrt(disc);
                 return rs * rs * margin;
@@ -504,7 +525,7 @@ __global__ void __launch_bounds__(128, VG_MINB)
                     int n27 = 0, v27 = 0;
                     if (lane < 27) {
                         int kk, mx, my, mz;
-                        if (resolve(g, S.cc.b, lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1, kk, mx, my, mz)) {
+                        if (resolve(g, SY.blk_base, S.cc.b, lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1, kk, mx, my, mz)) {
                             n27 = __ldg(&st.bstart[kk + 1]) - __ldg(&st.bstart[kk]);
                             v27 = 1;
                         }
@@ -538,7 +559,7 @@ __global__ void __launch_bounds__(128, VG_MINB)
                                 oz = r / wy - rg2;
                                 int kk, mx, my, mz;
                                 rowok = row_gap2(g, o1, o2, oy, oz) < rho2 &&
-                                        resolve(g, S.cc.b, 0, oy, oz, kk, mx, my, mz);
+                                        resolve(g, SY.blk_base, S.cc.b, 0, oy, oz, kk, mx, my, mz);
                                 krow = kk - bx;
                                 if (rowok) {
                                     // the blocks of the row within rho: an interval around 0
@@ -609,7 +630,7 @@ __global__ void __launch_bounds__(128, VG_MINB)
                                 keep = qq < rho2 && !(j == i && oxj == 0 && oy == 0 && oz == 0);
                                 if (keep) {
                                     int kk, mx, my, mz;
-                                    resolve(g, S.cc.b, oxj, oy, oz, kk, mx, my, mz);
+                                    resolve(g, SY.blk_base, S.cc.b, oxj, oy, oz, kk, mx, my, mz);
                                     img = pack_img(mx, my, mz);
                                 }
                             }
@@ -741,13 +762,14 @@ __global__ void __launch_bounds__(128, VG_MINB)
                     bool cand = false;
                     if (mode == 1) {
                         const int e = src.e;
-                        if (e >= off.count) { src.mode = 2; continue; }
+                        const int ocount = SY.off_count, obase = SY.off_base;
+                        if (e >= ocount) { src.mode = 2; continue; }
                         const int ei = e + lane;
                         bool beyond = true;
-                        if (ei < off.count) {
-                            const float lb = __ldg(&off.lb[ei]);
+                        if (ei < ocount) {
+                            const float lb = __ldg(&off.lb[obase + ei]);
                             beyond = (T)(lb * lb) * (T)0.99998 >= stop;
-                            const int code = __ldg(&off.code[ei]);
+                            const int code = __ldg(&off.code[obase + ei]);
                             ox = imgc(code, 0); oy = imgc(code, 1); oz = imgc(code, 2);
                         }
                         // the list is sorted by its bound: entries past the first
@@ -755,14 +777,14 @@ __global__ void __launch_bounds__(128, VG_MINB)
                         const unsigned bb = __ballot_sync(FULL, beyond);
                         const int first = bb ? __ffs(bb) - 1 : 32;
                         cand = lane < first;
-                        if (first < 32 && e + first < off.count) src.last = 1;
+                        if (first < 32 && e + first < ocount) src.last = 1;
                         src.e = e + 32;
                     } else {
                         const int shell = src.shell;
                         const float hmin = fminf(g.hf[0], fminf(g.hf[1], g.hf[2]));
                         const float sb = (float)(shell - 1) * hmin;
                         if ((T)(sb * sb) * (T)0.99998 >= stop) { src.mode = 3; continue; }
-                        const int maxs = off.shell + MAX_SHELL_EXTRA + 2 * max(g.nb[0], max(g.nb[1], g.nb[2]));
+                        const int maxs = SY.off_shell + MAX_SHELL_EXTRA + 2 * max(g.nb[0], max(g.nb[1], g.nb[2]));
                         if (shell > maxs) { src.limit = 1; src.mode = 3; continue; }
                         const int wd = 2 * shell + 1, sidx = src.sidx;
                         if (sidx >= wd * wd * wd) { src.shell = shell + 1; src.sidx = 0; continue; }
@@ -771,7 +793,7 @@ __global__ void __launch_bounds__(128, VG_MINB)
                             ox = si % wd - shell;
                             oy = (si / wd) % wd - shell;
                             oz = si / (wd * wd) - shell;
-                            const float lbmax = (float)off.shell * hmin;
+                            const float lbmax = (float)SY.off_shell * hmin;
                             const float lbx = fmaxf(0.f, (float)(abs(ox) - 1)) * g.hf[0];
                             const float lby = fmaxf(0.f, (float)(abs(oy) - 1)) * g.hf[1];
                             const float lbz = fmaxf(0.f, (float)(abs(oz) - 1)) * g.hf[2];
@@ -783,7 +805,7 @@ __global__ void __launch_bounds__(128, VG_MINB)
                     }
                     int kk = 0, mx = 0, my = 0, mz = 0, len = 0, j0b = 0, inpref = 0;
                     if (cand) {
-                        cand = resolve(g, S.cc.b, ox, oy, oz, kk, mx, my, mz);
+                        cand = resolve(g, SY.blk_base, S.cc.b, ox, oy, oz, kk, mx, my, mz);
                         if (cand) {
                             const float gap2 = block_gap2(g, o0, o1, o2, ox, oy, oz);
                             cand = !((T)gap2 * (T)0.99998 >= stop);
@@ -1353,12 +1375,11 @@ __global__ void __launch_bounds__(128, VG_MINB)
     }
 }
 
-template <typename T, int VPL, int MAXP>
-cudaError_t launch_t(const Grid &g, const Store &s, const Out &o, const Params &p, const Offsets &off,
-                     unsigned *ticket, int sm_count, int warps, const int *cells, int ncells, int tier,
-                     cudaStream_t st) {
+template <typename T, int VPL, int MAXP, bool BATCH>
+cudaError_t launch_t(const Store &s, const Out &o, const Params &p, const Offsets &off, unsigned *ticket,
+                     int sm_count, int warps, const int *cells, int ncells, int tier, cudaStream_t st) {
     const size_t smem = sizeof(Smem<T, VPL, MAXP>) * warps;
-    auto kfn = k_cells3<T, VPL, MAXP>;
+    auto kfn = k_cells3<T, VPL, MAXP, BATCH>;
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -1369,20 +1390,25 @@ cudaError_t launch_t(const Grid &g, const Store &s, const Out &o, const Params &
     if (tier > 0) grid = sm_count;
     if ((e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
     ++g_launch_count;
-    kfn<<<grid, warps * 32, smem, st>>>(g, s, o, p, off, ticket, cells, ncells, tier);
+    kfn<<<grid, warps * 32, smem, st>>>(s, o, p, off, ticket, cells, ncells, tier);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_cells3(const Grid &g, const Store &s, const Out &o, const Params &p, const Offsets &off,
-                          int precision, unsigned *ticket, int sm_count, int warps_per_cta, const int *cells,
-                          int ncells, int tier, cudaStream_t st) {
+cudaError_t launch_cells3(const Store &s, const Out &o, const Params &p, const Offsets &off, int precision,
+                          unsigned *ticket, int sm_count, int warps_per_cta, const int *cells, int ncells, int tier,
+                          cudaStream_t st) {
     const int w = warps_per_cta > 0 ? warps_per_cta : 4;
-    if (tier == 2) return launch_t<double, 16, 256>(g, s, o, p, off, ticket, sm_count, 1, cells, ncells, tier, st);
-    if (tier == 1) return launch_t<double, 4, 128>(g, s, o, p, off, ticket, sm_count, 2, cells, ncells, tier, st);
-    if (precision == VG_FP64) return launch_t<double, 2, 64>(g, s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
-    return launch_t<float, 2, 64>(g, s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
+    // the rare large cells (tiers 1, 2) always take the batched form
+    if (tier == 2) return launch_t<double, 16, 256, true>(s, o, p, off, ticket, sm_count, 1, cells, ncells, tier, st);
+    if (tier == 1) return launch_t<double, 4, 128, true>(s, o, p, off, ticket, sm_count, 2, cells, ncells, tier, st);
+    const bool batch = s.nsys > 1;
+    if (precision == VG_FP64)
+        return batch ? launch_t<double, 2, 64, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st)
+                     : launch_t<double, 2, 64, false>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
+    return batch ? launch_t<float, 2, 64, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st)
+                 : launch_t<float, 2, 64, false>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
 }
 
 }  // namespace vg

@@ -6,6 +6,7 @@
 
 #include <string>
 #include <unordered_map>
+#include <vector>
 
 #include "vorogpu.h"
 
@@ -33,16 +34,33 @@ struct Grid {
     double s;         // mean spacing (V/N)^(1/dim)
 };
 
+// One particle system of a (possibly batched) container: its grid, where its
+// blocks and particles start in the global numbering, its largest radius and
+// its slice of the walk's offset list.
+struct Sys {
+    Grid g;
+    long long blk_base;   // first global block index
+    long long p_base;     // first particle, input order (systems concatenated)
+    long long n;          // particles
+    double rmax;          // largest radius (0 for plain Voronoi)
+    int off_base, off_count, off_shell, pad;
+};
+
 // Sorted particle store written by the counting sort.
 struct Store {
     const float4 *p32;     // block-local FP32 offset from the block's lower corner; w = radius
     const D4 *p64;         // wrapped FP64 position; w = radius
     const int *sid;        // input index of each sorted particle
     const int *sblk;       // block index of each sorted particle
-    const int *bstart;     // block CSR, nblk + 1 entries
-    int n;
+    const int *bstart;     // block CSR, total blocks + 1 entries
+    const int *ssys;       // system of each sorted particle
+    const Sys *sys;        // system descriptors
+    Sys sys0;              // system 0 by value (kernels read it from parameter space
+                           // when the container has one system); its rmax is not
+                           // set here: the device copy sys[0].rmax holds it
+    int nsys;
+    int n;                 // particles of all systems
     int radical;
-    double rmax;           // largest radius (0 for plain Voronoi)
 };
 
 // Per-cell outputs (indexed by input index) and the face bump buffer.
@@ -74,38 +92,45 @@ struct Params {
     const float *kblock;   // per-block candidate target from the MLP, or null
 };
 
-// Sorted offset list for the walk: offsets (dx,dy,dz) in bytes 0..2 and the
-// lower bound of the distance from any point of the home block, ascending.
+// The descriptor of the current cell's system: for a single-system launch
+// system 0 from parameter space (constant-bank operands), else the copy a
+// warp keeps in shared memory.
+template <bool BATCH>
+__device__ __forceinline__ const Sys &sys_ref(const Store &st, const Sys &shared_copy) {
+    if constexpr (BATCH) return shared_copy;
+    else return st.sys0;
+}
+
+// Sorted offset lists for the walk, one slice per system (Sys::off_base,
+// off_count): offsets (dx,dy,dz) in bytes 0..2 and the lower bound of the
+// distance from any point of the home block, ascending.
 struct Offsets {
     const int *code;
     const float *lb;
-    int count;
-    int shell;   // Chebyshev radius covered by the list
 };
 
 // ---- launchers (return cudaError_t) ----------------------------------------
 
-cudaError_t sort_particles(const Grid &g, long long n, const double *pos, const double *radii,
-                           int *key, int *slot, int *count, int *bstart, int *tmp_id,
-                           float4 *p32, D4 *p64, int *sid, int *sblk, int *errflags,
-                           void *scan_tmp, size_t scan_tmp_bytes, cudaStream_t st);
+cudaError_t sort_particles(const Sys *sys, int nsys, int dim, long long total_blk, long long n,
+                           const double *pos, const double *radii, int *key, int *slot, int *count,
+                           int *bstart, int *tmp_id, float4 *p32, D4 *p64, int *sid, int *sblk,
+                           int *ssys, int *errflags, void *scan_tmp, cudaStream_t st);
+cudaError_t system_rmax(Sys *sys, int nsys, long long n, const double *radii, cudaStream_t st);
 size_t scan_tmp_bytes_i32(long long n);
 size_t scan_tmp_bytes_i64(long long n);
 cudaError_t exclusive_scan_i32(const int *in, int *out, long long n, void *tmp, cudaStream_t st);
 cudaError_t exclusive_scan_i64_from_i32(const int *in, long long *out, long long n, void *tmp,
                                         cudaStream_t st);
 
-cudaError_t launch_cells3(const Grid &g, const Store &s, const Out &o, const Params &p,
-                          const Offsets &off, int precision, unsigned *ticket, int sm_count,
-                          int warps_per_cta, const int *cells, int ncells, int tier,
-                          cudaStream_t st);
-cudaError_t launch_cells2(const Grid &g, const Store &s, const Out &o, const Params &p,
-                          const Offsets &off, int precision, unsigned *ticket, int sm_count,
-                          int warps_per_cta, const int *cells, int ncells, int tier,
-                          cudaStream_t st);
+cudaError_t launch_cells3(const Store &s, const Out &o, const Params &p, const Offsets &off,
+                          int precision, unsigned *ticket, int sm_count, int warps_per_cta,
+                          const int *cells, int ncells, int tier, cudaStream_t st);
+cudaError_t launch_cells2(const Store &s, const Out &o, const Params &p, const Offsets &off,
+                          int precision, unsigned *ticket, int sm_count, int warps_per_cta,
+                          const int *cells, int ncells, int tier, cudaStream_t st);
 
 cudaError_t compact_faces(long long n, const int *nf, const unsigned char *status,
-                          const long long *fptr, const int2 *faces, long long *face_off,
+                          const long long *fptr, const int2 *faces, long long fcap, long long *face_off,
                           int *nbr_id, signed char *nbr_img, unsigned char *face_order,
                           void *scan_tmp, cudaStream_t st);
 
@@ -116,25 +141,30 @@ cudaError_t compact_faces(long long n, const int *nf, const unsigned char *statu
 
 struct vg_ctx {
     int dim = 3;
-    vg::Grid g{};
+    vg::Grid g{};             // system 0 (single-system containers)
     int grid_fixed = 0;
     double n_opt = 0;
+    // systems (one for vg_create, many for vg_batch_create)
+    std::vector<vg::Sys> sys;
+    std::vector<int> sys_fixed;     // 1: block counts given by the caller
+    std::vector<double> sys_nopt;
+    vg::Sys *d_sys = nullptr;         // descriptors the kernels read (r_max filled on the device)
+    vg::Sys *d_sys_init = nullptr;    // the same as laid out on the host (r_max = 0)
+    long long total_blk = 0;
+    int batched = 0;
     cudaStream_t stream = nullptr;
     int device = 0;
     int sm_count = 0;
     std::string err;
     std::unordered_map<void *, long long> caps;  // element capacity per device buffer
 
-    long long n = 0;          // particles inserted
-    long long cap_n = 0;      // capacity of per-particle buffers
-    long long cap_blk = 0;
+    long long n = 0;          // particles inserted (all systems)
     int radical = 0;
-    double rmax = 0;
     int inserted = 0, computed = 0;
 
     // per-particle device buffers
     double *d_pos = nullptr, *d_rad = nullptr;   // staged copies of host input
-    int *d_key = nullptr, *d_slot = nullptr, *d_tmp = nullptr;
+    int *d_key = nullptr, *d_slot = nullptr, *d_tmp = nullptr, *d_ssys = nullptr;
     float4 *d_p32 = nullptr;
     vg::D4 *d_p64 = nullptr;
     int *d_sid = nullptr, *d_sblk = nullptr;
@@ -156,7 +186,6 @@ struct vg_ctx {
     int *d_nbr = nullptr;
     signed char *d_img = nullptr;
     unsigned char *d_ford = nullptr;
-    long long cap_faces_csr = 0;
     int *d_w_tested = nullptr, *d_w_vtests = nullptr, *d_w_cuts = nullptr, *d_w_retest = nullptr;
     int *d_w_newv = nullptr;
     // event pairs around the cell kernels (time_kernels)
@@ -166,16 +195,26 @@ struct vg_ctx {
     unsigned char *d_w_fallback = nullptr;
     int *d_caplist = nullptr, *d_capcount = nullptr;
     int *d_caplist2 = nullptr, *d_capcount2 = nullptr;
-    long long total_faces = -1;
 
-    // walk offsets
+    // walk offsets, one slice per distinct block shape (Sys::off_base)
     int *d_off_code = nullptr;
     float *d_off_lb = nullptr;
-    int off_count = 0, off_shell = 0;
 
     long long launches = 0;   // kernels launched by this context
 
+    // CUDA graph of one whole step (sort -> cells -> faces), vg_graph_capture()
+    cudaStream_t gstream = nullptr;       // capture stream (non-blocking)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaEvent_t gev[2] = {nullptr, nullptr};           // event nodes around the cell kernels
+    cudaGraphNode_t gev_node[2] = {nullptr, nullptr};
+    long long graph_kernels = 0;          // kernels one replay launches
+    int graph_timed = 0;
+    int graph_unchecked = 0;              // replayed, flags not read yet
+    std::vector<int64_t> g_counts;        // capture arguments, for a re-capture
+    const double *g_pos = nullptr, *g_rad = nullptr;
+    vg_config g_cfg{};
+
     // MLP per-block predictions
     float *d_kblock = nullptr;
-    long long cap_kblock = 0;
 };

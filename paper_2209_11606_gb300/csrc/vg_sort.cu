@@ -35,17 +35,31 @@ __device__ __forceinline__ double wrap(double x, double lo, double L) {
     return __dadd_rn(lo, t);
 }
 
-// Step 1: validate, wrap, compute the block key and take a slot with an
-// atomic capture on the block count.
-__global__ void k_index(Grid g, long long n, const double *__restrict__ pos,
-                        const double *__restrict__ rad, int *__restrict__ key,
-                        int *__restrict__ slot, int *__restrict__ count, int *__restrict__ err) {
+// System of input particle i: the last system whose first particle is <= i.
+__device__ __forceinline__ int system_of(const Sys *sys, int nsys, long long i) {
+    int lo = 0, hi = nsys - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sys[mid].p_base <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Step 1: validate, wrap, compute the global block key (the system's first
+// block + the block inside the system) and take a slot with an atomic
+// capture on the block count.
+__global__ void k_index(const Sys *__restrict__ sys, int nsys, int dim, long long n,
+                        const double *__restrict__ pos, const double *__restrict__ rad,
+                        int *__restrict__ key, int *__restrict__ slot, int *__restrict__ count,
+                        int *__restrict__ err) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int sidx = nsys > 1 ? system_of(sys, nsys, i) : 0;
+    const Grid &g = sys[sidx].g;
     long long k = 0, mul = 1;
     bool bad = false, outside = false;
-    for (int a = 0; a < g.dim; a++) {
-        double x = pos[i * g.dim + a];
+    for (int a = 0; a < dim; a++) {
+        double x = pos[i * dim + a];
         if (!isfinite(x)) { bad = true; x = g.lo[a]; }
         if (g.per[a]) x = wrap(x, g.lo[a], g.L[a]);
         else if (x < g.lo[a] || x > g.hi[a]) { outside = true; x = g.lo[a]; }
@@ -55,8 +69,20 @@ __global__ void k_index(Grid g, long long n, const double *__restrict__ pos,
     if (rad && !(isfinite(rad[i]) && rad[i] >= 0.0)) bad = true;
     if (bad) atomicAdd(&err[1], 1);
     if (outside) atomicAdd(&err[0], 1);
+    k += sys[sidx].blk_base;
     key[i] = (int)k;
     slot[i] = atomicAdd(&count[k], 1);
+}
+
+// Largest radius of each system (radical stop test); radii are >= 0, and
+// non-negative doubles order like their bit patterns.
+__global__ void k_rmax(Sys *__restrict__ sys, int nsys, long long n, const double *__restrict__ rad) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int sidx = nsys > 1 ? system_of(sys, nsys, i) : 0;
+    const double r = rad[i];
+    if (r > 0.0 && isfinite(r))
+        atomicMax(reinterpret_cast<unsigned long long *>(&sys[sidx].rmax), (unsigned long long)__double_as_longlong(r));
 }
 
 // Step 3: scatter input indices to their (unordered) slot in the block.
@@ -68,39 +94,43 @@ __global__ void k_scatter(long long n, const int *__restrict__ key, const int *_
 }
 
 // Step 4: rank inside the block by input index and write the sorted store.
-__global__ void k_finalize(Grid g, long long n, const int *__restrict__ key,
-                           const int *__restrict__ bstart, const int *__restrict__ tmp_id,
-                           const double *__restrict__ pos, const double *__restrict__ rad,
-                           float4 *__restrict__ p32, D4 *__restrict__ p64,
-                           int *__restrict__ sid, int *__restrict__ sblk) {
+__global__ void k_finalize(const Sys *__restrict__ sys, int nsys, int dim, long long n,
+                           const int *__restrict__ key, const int *__restrict__ bstart,
+                           const int *__restrict__ tmp_id, const double *__restrict__ pos,
+                           const double *__restrict__ rad, float4 *__restrict__ p32,
+                           D4 *__restrict__ p64, int *__restrict__ sid, int *__restrict__ sblk,
+                           int *__restrict__ ssys) {
     long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (u >= n) return;
-    int i = tmp_id[u];
-    int k = key[i];
-    int b0 = bstart[k], b1 = bstart[k + 1];
+    const int i = tmp_id[u];
+    const int k = key[i];
+    const int b0 = bstart[k], b1 = bstart[k + 1];
     int rank = 0;
     for (int v = b0; v < b1; v++) rank += tmp_id[v] < i;
-    int dst = b0 + rank;
+    const int dst = b0 + rank;
+    const int sidx = nsys > 1 ? system_of(sys, nsys, i) : 0;
+    const Grid &g = sys[sidx].g;
     double x[3] = {0, 0, 0};
     float o[3] = {0.f, 0.f, 0.f};
-    int kk = k;
-    for (int a = 0; a < g.dim; a++) {
-        double xa = pos[(long long)i * g.dim + a];
+    int kk = k - (int)sys[sidx].blk_base;
+    for (int a = 0; a < dim; a++) {
+        double xa = pos[(long long)i * dim + a];
         if (!isfinite(xa)) xa = g.lo[a];
         if (g.per[a]) xa = wrap(xa, g.lo[a], g.L[a]);
         else xa = fmin(fmax(xa, g.lo[a]), g.hi[a]);
-        int b = kk % g.nb[a];
+        const int b = kk % g.nb[a];
         kk /= g.nb[a];
-        double corner = __dadd_rn(g.lo[a], __dmul_rn((double)b, g.h[a]));
+        const double corner = __dadd_rn(g.lo[a], __dmul_rn((double)b, g.h[a]));
         x[a] = xa;
         o[a] = __double2float_rn(__dsub_rn(xa, corner));
     }
-    double r = rad ? rad[i] : 0.0;
+    const double r = rad ? rad[i] : 0.0;
     p32[dst] = make_float4(o[0], o[1], o[2], (float)r);
     D4 v; v.x = x[0]; v.y = x[1]; v.z = x[2]; v.w = r;
     p64[dst] = v;
     sid[dst] = i;
     sblk[dst] = k;
+    ssys[dst] = sidx;
 }
 
 // ---- exclusive scan: tiles, recursive tile sums, add back ------------------
@@ -214,25 +244,31 @@ __global__ void k_total(const TI *in, TO *out, long long n) {
 }
 }  // namespace
 
-cudaError_t sort_particles(const Grid &g, long long n, const double *pos, const double *radii,
-                           int *key, int *slot, int *count, int *bstart, int *tmp_id,
-                           float4 *p32, D4 *p64, int *sid, int *sblk, int *errflags,
-                           void *scan_tmp, size_t scan_tmp_bytes_, cudaStream_t st) {
-    (void)scan_tmp_bytes_;
+cudaError_t system_rmax(Sys *sys, int nsys, long long n, const double *radii, cudaStream_t st) {
+    if (n <= 0 || !radii) return cudaSuccess;
+    ++g_launch_count;
+    k_rmax<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sys, nsys, n, radii);
+    return cudaGetLastError();
+}
+
+cudaError_t sort_particles(const Sys *sys, int nsys, int dim, long long total_blk, long long n,
+                           const double *pos, const double *radii, int *key, int *slot, int *count,
+                           int *bstart, int *tmp_id, float4 *p32, D4 *p64, int *sid, int *sblk,
+                           int *ssys, int *errflags, void *scan_tmp, cudaStream_t st) {
     cudaError_t e;
-    if ((e = cudaMemsetAsync(count, 0, sizeof(int) * g.nblk, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(count, 0, sizeof(int) * total_blk, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(errflags, 0, sizeof(int) * 2, st)) != cudaSuccess) return e;
     const int T = 256;
-    unsigned nbk = (unsigned)((n + T - 1) / T);
-    if (n > 0) { ++g_launch_count; k_index<<<nbk, T, 0, st>>>(g, n, pos, radii, key, slot, count, errflags); }
-    if ((e = exclusive_scan_i32(count, bstart, g.nblk, scan_tmp, st)) != cudaSuccess) return e;
+    const unsigned nbk = (unsigned)((n + T - 1) / T);
+    if (n > 0) { ++g_launch_count; k_index<<<nbk, T, 0, st>>>(sys, nsys, dim, n, pos, radii, key, slot, count, errflags); }
+    if ((e = exclusive_scan_i32(count, bstart, total_blk, scan_tmp, st)) != cudaSuccess) return e;
     ++g_launch_count;
-    k_total<int, int><<<1, 1, 0, st>>>(count, bstart, g.nblk);
+    k_total<int, int><<<1, 1, 0, st>>>(count, bstart, total_blk);
     if (n > 0) {
         ++g_launch_count;
         k_scatter<<<nbk, T, 0, st>>>(n, key, slot, bstart, tmp_id);
         ++g_launch_count;
-        k_finalize<<<nbk, T, 0, st>>>(g, n, key, bstart, tmp_id, pos, radii, p32, p64, sid, sblk);
+        k_finalize<<<nbk, T, 0, st>>>(sys, nsys, dim, n, key, bstart, tmp_id, pos, radii, p32, p64, sid, sblk, ssys);
     }
     return cudaGetLastError();
 }
@@ -240,9 +276,15 @@ cudaError_t sort_particles(const Grid &g, long long n, const double *pos, const 
 // ---- CSR compaction of faces ---------------------------------------------------
 
 namespace {
-__global__ void k_nf_ok(long long n, const int *nf, const unsigned char *status, int *nf_ok) {
+// Faces of cell i that the CSR takes: none unless the cell is complete and
+// its faces fit in the bump buffer (after an overflow the cell kernel skips
+// the write, so its slots hold nothing to copy).
+__global__ void k_nf_ok(long long n, const int *nf, const unsigned char *status, const long long *fptr,
+                        long long fcap, int *nf_ok) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n) nf_ok[i] = status[i] == VG_CELL_OK ? nf[i] : 0;
+    if (i >= n) return;
+    const bool ok = status[i] == VG_CELL_OK && fptr[i] >= 0 && fptr[i] + nf[i] <= fcap;
+    nf_ok[i] = ok ? nf[i] : 0;
 }
 
 // one warp per 32 cells: each lane copies its cell's faces
@@ -267,23 +309,24 @@ __global__ void k_compact(long long n, const int *__restrict__ nf_ok,
 }  // namespace
 
 cudaError_t compact_faces(long long n, const int *nf, const unsigned char *status,
-                          const long long *fptr, const int2 *faces, long long *face_off,
+                          const long long *fptr, const int2 *faces, long long fcap, long long *face_off,
                           int *nbr_id, signed char *nbr_img, unsigned char *face_order,
                           void *scan_tmp, cudaStream_t st) {
-    // nf_ok is staged in the tail of face_off's memory? no: reuse nbr_id head is unsafe;
-    // the caller provides scan_tmp large enough for n ints plus the i64 scan.
+    // scan_tmp holds n ints for the per-cell face counts, then the scan's own
+    // scratch (the caller sizes it for both)
     int *nf_ok = (int *)scan_tmp;
     char *tmp = (char *)scan_tmp + (((size_t)n * sizeof(int) + 255) & ~(size_t)255);
     const int T = 256;
     unsigned nbk = (unsigned)((n + T - 1) / T);
-    if (n > 0) { ++g_launch_count; k_nf_ok<<<nbk, T, 0, st>>>(n, nf, status, nf_ok); }
+    if (n > 0) { ++g_launch_count; k_nf_ok<<<nbk, T, 0, st>>>(n, nf, status, fptr, fcap, nf_ok); }
     cudaError_t e = scan_rec<int, long long>(nf_ok, face_off, n, tmp, st);
     if (e != cudaSuccess) return e;
     ++g_launch_count;
     k_total<int, long long><<<1, 1, 0, st>>>(nf_ok, face_off, n);
-    if (n > 0)
+    if (n > 0) {
         ++g_launch_count;
         k_compact<<<nbk, T, 0, st>>>(n, nf_ok, fptr, faces, face_off, nbr_id, nbr_img, face_order);
+    }
     return cudaGetLastError();
 }
 

@@ -24,10 +24,11 @@ VG_FP64, VG_FP32_RETEST = 0, 1
 VG_WALK, VG_PREFETCH = 0, 1
 VG_CELL_OK, VG_CELL_EMPTY, VG_CELL_CAP, VG_CELL_DUP, VG_CELL_LIMIT = 0, 1, 2, 3, 4
 
-EXPORTS = ["vg_config_default", "vg_create", "vg_insert", "vg_compute", "vg_get_counts",
-           "vg_get_cells", "vg_get_faces", "vg_get_work", "vg_get_sorted", "vg_get_grid",
-           "vg_get_launches", "vg_get_kernel_ms", "vg_sort_blocks_noalloc",
-           "vg_last_error", "vg_destroy"]
+EXPORTS = ["vg_config_default", "vg_create", "vg_batch_create", "vg_insert", "vg_batch_insert",
+           "vg_compute", "vg_get_counts", "vg_get_cells", "vg_get_faces", "vg_get_work",
+           "vg_get_sorted", "vg_get_grid", "vg_get_system_grid", "vg_get_launches",
+           "vg_get_kernel_ms", "vg_graph_capture", "vg_graph_launch", "vg_graph_sync",
+           "vg_sort_blocks_noalloc", "vg_last_error", "vg_destroy"]
 
 
 class VgConfig(ctypes.Structure):
@@ -36,6 +37,12 @@ class VgConfig(ctypes.Structure):
                 ("prefetch_k", ctypes.c_int), ("use_mlp", ctypes.c_int), ("chunk", ctypes.c_int),
                 ("warps_per_cta", ctypes.c_int), ("collect_stats", ctypes.c_int),
                 ("time_kernels", ctypes.c_int)]
+
+
+class VgSystem(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("periodic", ctypes.c_int * 3), ("nblocks", ctypes.c_int * 3),
+                ("n_opt", ctypes.c_double)]
 
 
 class VgError(RuntimeError):
@@ -59,8 +66,13 @@ def load(path: str = LIB_PATH):
     sig = {
         "vg_config_default": (None, [ctypes.POINTER(VgConfig)]),
         "vg_create": (I, [ctypes.POINTER(P), I, P, P, P, P, D, P]),
+        "vg_batch_create": (I, [ctypes.POINTER(P), I, I, ctypes.POINTER(VgSystem), P]),
         "vg_insert": (I, [P, L, P, P, I]),
+        "vg_batch_insert": (I, [P, P, P, P, I]),
         "vg_compute": (I, [P, ctypes.POINTER(VgConfig)]),
+        "vg_graph_capture": (I, [P, P, P, P, ctypes.POINTER(VgConfig)]),
+        "vg_graph_launch": (I, [P]),
+        "vg_graph_sync": (I, [P]),
         "vg_get_counts": (I, [P, ctypes.POINTER(L), ctypes.POINTER(L)]),
         "vg_get_cells": (I, [P, P, P, P, P, P, P, P, I]),
         "vg_get_faces": (I, [P, P, P, P, P, I]),
@@ -68,6 +80,7 @@ def load(path: str = LIB_PATH):
         "vg_get_kernel_ms": (I, [P, ctypes.POINTER(D), ctypes.POINTER(L)]),
         "vg_get_sorted": (I, [P, ctypes.POINTER(L), P, P, I]),
         "vg_get_grid": (I, [P, P]),
+        "vg_get_system_grid": (I, [P, I, P]),
         "vg_get_launches": (I, [P, ctypes.POINTER(L)]),
         "vg_sort_blocks_noalloc": (I, [I, P, P, P, P, L, P, P, P, P, ctypes.c_char_p, I]),
         "vg_last_error": (ctypes.c_char_p, [P]),
@@ -124,6 +137,44 @@ def vg_create(dim, lo, hi, periodic, nblocks=None, n_opt=0.0, stream=None):
     return h
 
 
+def vg_system(lo, hi, periodic, nblocks=None, n_opt=0.0) -> VgSystem:
+    """One system of a batched container (the arguments of vg_create)."""
+    s = VgSystem()
+    for a in range(len(lo)):
+        s.lo[a] = float(lo[a])
+        s.hi[a] = float(hi[a])
+        s.periodic[a] = 1 if periodic[a] else 0
+        s.nblocks[a] = 0 if nblocks is None else int(nblocks[a])
+    s.n_opt = float(n_opt)
+    return s
+
+
+def vg_batch_create(dim, systems, stream=None):
+    lib = load()
+    arr = (VgSystem * len(systems))(*systems)
+    h = ctypes.c_void_p()
+    st = None
+    if stream is not None:
+        st = stream if isinstance(stream, int) else stream.cuda_stream
+    code = lib.vg_batch_create(ctypes.byref(h), int(dim), len(systems), arr, st)
+    if code != VG_OK:
+        raise VgError(code, "vg_batch_create failed")
+    return h
+
+
+def vg_batch_insert(ctx, counts, pos, radii=None):
+    """`counts[k]` rows of `pos` (and `radii`) belong to system k, systems
+    one after another."""
+    cnt = np.ascontiguousarray(counts, dtype=np.int64)
+    p, dev = _ptr(pos)
+    r, rdev = _ptr(radii)
+    if radii is not None and rdev != dev:
+        raise ValueError("pos and radii must both be host or both device")
+    if int(cnt.sum()) != pos.shape[0]:
+        raise ValueError("counts do not add up to the rows of pos")
+    _check(ctx, load().vg_batch_insert(ctx, cnt.ctypes.data, p, r, dev))
+
+
 def vg_insert(ctx, pos, radii=None):
     p, dev = _ptr(pos)
     r, rdev = _ptr(radii)
@@ -135,6 +186,28 @@ def vg_insert(ctx, pos, radii=None):
 
 def vg_compute(ctx, cfg: VgConfig | None = None):
     _check(ctx, load().vg_compute(ctx, None if cfg is None else ctypes.byref(cfg)))
+
+
+def vg_graph_capture(ctx, counts, pos, radii=None, cfg: VgConfig | None = None):
+    """Captures sort -> cells -> faces of device tensors `pos` (and `radii`)
+    into a CUDA graph owned by `ctx`; `counts` per system."""
+    cnt = np.ascontiguousarray(counts, dtype=np.int64)
+    p, dev = _ptr(pos)
+    r, rdev = _ptr(radii)
+    if not dev or (radii is not None and not rdev):
+        raise ValueError("graph inputs must be CUDA tensors")
+    if int(cnt.sum()) != pos.shape[0]:
+        raise ValueError("counts do not add up to the rows of pos")
+    _check(ctx, load().vg_graph_capture(ctx, cnt.ctypes.data, p, r,
+                                        None if cfg is None else ctypes.byref(cfg)))
+
+
+def vg_graph_launch(ctx):
+    _check(ctx, load().vg_graph_launch(ctx))
+
+
+def vg_graph_sync(ctx):
+    _check(ctx, load().vg_graph_sync(ctx))
 
 
 def vg_get_counts(ctx):
@@ -182,6 +255,12 @@ def vg_get_grid(ctx, dim):
     return tuple(int(v) for v in out)
 
 
+def vg_get_system_grid(ctx, k, dim):
+    out = np.zeros(dim, dtype=np.int32)
+    _check(ctx, load().vg_get_system_grid(ctx, int(k), out.ctypes.data))
+    return tuple(int(v) for v in out)
+
+
 def vg_get_kernel_ms(ctx):
     t, c = ctypes.c_double(), ctypes.c_int64()
     _check(ctx, load().vg_get_kernel_ms(ctx, ctypes.byref(t), ctypes.byref(c)))
@@ -223,6 +302,41 @@ def vg_destroy(ctx):
 
 # ---- convenience: one call from host arrays to host results -------------------
 
+def _make_cfg(precision, order, work, cfg_kw) -> VgConfig:
+    cfg = vg_config_default()
+    cfg.precision = VG_FP64 if precision == "fp64" else VG_FP32_RETEST
+    cfg.order = VG_WALK if order == "walk" else VG_PREFETCH
+    cfg.collect_stats = 1 if work else 0
+    for k, v in cfg_kw.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def _fetch(ctx, n, d, work) -> dict:
+    ncell, nface = vg_get_counts(ctx)
+    out = {
+        "vol": np.zeros(n), "area": np.zeros(n), "centroid": np.zeros((n, d)),
+        "nv": np.zeros(n, np.int32), "ne": np.zeros(n, np.int32), "nf": np.zeros(n, np.int32),
+        "status": np.zeros(n, np.uint8),
+    }
+    vg_get_cells(ctx, out["vol"], out["area"], out["centroid"], out["nv"], out["ne"], out["nf"],
+                 out["status"])
+    fo = np.zeros(n + 1, np.int64)
+    ids = np.zeros(max(nface, 1), np.int32)
+    img = np.zeros((max(nface, 1), 3), np.int8)
+    order_ = np.zeros(max(nface, 1), np.uint8)
+    vg_get_faces(ctx, fo, ids, img, order_)
+    out.update({"face_off": fo, "nbr_id": ids[:nface], "nbr_img": img[:nface, :d],
+                "face_order": order_[:nface]})
+    if work:
+        w = {k: np.zeros(n, np.int32) for k in ("n_tested", "n_vtests", "n_cuts", "n_newv", "n_retest")}
+        fb = np.zeros(n, np.uint8)
+        vg_get_work(ctx, w["n_tested"], w["n_vtests"], w["n_cuts"], w["n_newv"], w["n_retest"], fb)
+        w["fallback"] = fb
+        out["work"] = w
+    return out
+
+
 def compute_host(pos, lo, hi, periodic, radii=None, nblocks=None, n_opt=0.0, precision="fp32",
                  order="prefetch", work=False, **cfg_kw) -> dict:
     """Runs insert + compute on the current CUDA device from host numpy arrays
@@ -232,34 +346,29 @@ def compute_host(pos, lo, hi, periodic, radii=None, nblocks=None, n_opt=0.0, pre
     ctx = vg_create(d, lo, hi, periodic, nblocks, n_opt)
     try:
         vg_insert(ctx, pos, None if radii is None else np.ascontiguousarray(radii, dtype=np.float64))
-        cfg = vg_config_default()
-        cfg.precision = VG_FP64 if precision == "fp64" else VG_FP32_RETEST
-        cfg.order = VG_WALK if order == "walk" else VG_PREFETCH
-        cfg.collect_stats = 1 if work else 0
-        for k, v in cfg_kw.items():
-            setattr(cfg, k, v)
-        vg_compute(ctx, cfg)
-        ncell, nface = vg_get_counts(ctx)
-        out = {
-            "vol": np.zeros(n), "area": np.zeros(n), "centroid": np.zeros((n, d)),
-            "nv": np.zeros(n, np.int32), "ne": np.zeros(n, np.int32), "nf": np.zeros(n, np.int32),
-            "status": np.zeros(n, np.uint8),
-        }
-        vg_get_cells(ctx, out["vol"], out["area"], out["centroid"], out["nv"], out["ne"], out["nf"],
-                     out["status"])
-        fo = np.zeros(n + 1, np.int64)
-        ids = np.zeros(max(nface, 1), np.int32)
-        img = np.zeros((max(nface, 1), 3), np.int8)
-        order_ = np.zeros(max(nface, 1), np.uint8)
-        vg_get_faces(ctx, fo, ids, img, order_)
-        out.update({"face_off": fo, "nbr_id": ids[:nface], "nbr_img": img[:nface, :d],
-                    "face_order": order_[:nface], "grid": vg_get_grid(ctx, d)})
-        if work:
-            w = {k: np.zeros(n, np.int32) for k in ("n_tested", "n_vtests", "n_cuts", "n_newv", "n_retest")}
-            fb = np.zeros(n, np.uint8)
-            vg_get_work(ctx, w["n_tested"], w["n_vtests"], w["n_cuts"], w["n_newv"], w["n_retest"], fb)
-            w["fallback"] = fb
-            out["work"] = w
+        vg_compute(ctx, _make_cfg(precision, order, work, cfg_kw))
+        out = _fetch(ctx, n, d, work)
+        out["grid"] = vg_get_grid(ctx, d)
+        return out
+    finally:
+        vg_destroy(ctx)
+
+
+def compute_batch_host(systems, pos_list, radii_list=None, precision="fp32", order="prefetch",
+                       work=False, **cfg_kw) -> dict:
+    """Batched form of :func:`compute_host`: `systems` is a list of VgSystem,
+    `pos_list[k]` the host positions of system k.  Results are concatenated
+    in system order (neighbour ids in the concatenated numbering)."""
+    d = pos_list[0].shape[1]
+    counts = [p.shape[0] for p in pos_list]
+    pos = np.ascontiguousarray(np.concatenate(pos_list), dtype=np.float64)
+    rad = None if radii_list is None else np.ascontiguousarray(np.concatenate(radii_list), dtype=np.float64)
+    ctx = vg_batch_create(d, systems)
+    try:
+        vg_batch_insert(ctx, counts, pos, rad)
+        vg_compute(ctx, _make_cfg(precision, order, work, cfg_kw))
+        out = _fetch(ctx, pos.shape[0], d, work)
+        out["grids"] = [vg_get_system_grid(ctx, k, d) for k in range(len(systems))]
         return out
     finally:
         vg_destroy(ctx)
