@@ -95,7 +95,7 @@ typedef struct {
     int prefetch_k;    /* VG_PREFETCH: target candidate count; <= 0: the
                           library default (3D 72, 2D 24) */
     int use_mlp;       /* VG_PREFETCH: 1 = take the per-block candidate count
-                          from the loaded MLP (vg_mlp_set_weights) */
+                          written by vg_mlp_predict() after the last insert */
     int chunk;         /* cells taken per work-queue ticket; <= 0: default */
     int warps_per_cta; /* <= 0: default */
     int collect_stats; /* 1 = fill the per-cell work counters */
@@ -237,11 +237,19 @@ vg_status vg_get_faces(vg_ctx *ctx, int64_t *face_off, int32_t *nbr_id, int8_t *
  * Per-cell work counters of the last vg_compute() with collect_stats = 1,
  * n entries each (any may be NULL): candidates offered to the cut routine,
  * vertex-plane tests, cuts that removed something, vertices those cuts
- * created, FP64 re-tests, and whether the prefetch form fell back to the
- * walk (0/1).
+ * created, FP64 re-tests, whether the prefetch form fell back to the walk
+ * (0/1), and how many candidates the prefetch preloaded (0 for the walk).
  */
 vg_status vg_get_work(vg_ctx *ctx, int32_t *n_tested, int32_t *n_vtests, int32_t *n_cuts,
-                      int32_t *n_newv, int32_t *n_retest, uint8_t *fallback, int on_device);
+                      int32_t *n_newv, int32_t *n_retest, uint8_t *fallback, int32_t *n_prefetch,
+                      int on_device);
+
+/*
+ * R of every cell of the last vg_compute(): its largest vertex distance from
+ * the particle (FP32; 0 for empty or failed cells), the radius whose double
+ * bounds the neighbour search (Sec. 2.1.3).  n floats, input order.
+ */
+vg_status vg_get_radius(vg_ctx *ctx, float *rmax, int on_device);
 
 /*
  * Device time of the cell-kernel phase of every vg_compute() made with
@@ -269,6 +277,82 @@ vg_status vg_get_grid(vg_ctx *ctx, int *nblocks);
 
 /* The block counts of system k of a (batched) container. */
 vg_status vg_get_system_grid(vg_ctx *ctx, int k, int *nblocks);
+
+/* ---- learned candidate count ---------------------------------------------
+ *
+ * The paper has no learned part; its cells take candidates from the block
+ * walk with the radius bound (Sec. 2.1.3).  The prefetch form of the cell
+ * kernel preloads, in one batch, the candidates in a ball expected to hold k
+ * of them (k from the local density of the 27 surrounding blocks), sorts them
+ * by distance and cuts them in order; the radius bound still decides and a
+ * shortfall falls back to the walk, so cells never depend on k.  These calls
+ * train and run a small network that predicts k per block from the 27 block
+ * counts:
+ *
+ *   features  x_j = log(1 + c_j) / 4, c_j the count of block b + (dx,dy,dz),
+ *             j = (dx+1) + 3 (dy+1) + 9 (dz+1), wrapped on periodic axes,
+ *             0 past a wall;
+ *   network   y = W3 . relu(W2 relu(W1 x + b1) + b2) + b3, hidden widths 32
+ *             and 32, W1 W2 W3 in FP16, biases FP32, FP32 accumulation;
+ *             predicted count exp(y);
+ *   label     k*_i = candidates (particle, periodic image) within 2 R_i of
+ *             cell i (R_i from vg_get_radius), the particle itself excluded;
+ *   target    t_b = log(max(1, max k* over block b's cells));
+ *   loss      (1/M) sum_b w_b (y_b - t_b)^2, w_b = u if y_b < t_b else 1;
+ *   update    Adam, beta1 0.9, beta2 0.999, eps 1e-8, on FP32 master
+ *             weights; the FP16 copy is refreshed after every step.
+ *
+ * Parameters are 1985 floats packed as W1 (32 x 27, row per hidden unit),
+ * b1 (32), W2 (32 x 32), b2 (32), W3 (32), b3 (1).
+ */
+typedef struct vg_mlp vg_mlp;
+
+/* A predictor with all parameters 0; its work goes on `stream`. */
+vg_status vg_mlp_create(vg_mlp **out, void *stream);
+void vg_mlp_destroy(vg_mlp *mlp);
+const char *vg_mlp_last_error(vg_mlp *mlp);
+
+/* Sets the FP32 master parameters (1985 host floats), refreshes the FP16
+ * copy and clears the Adam state. */
+vg_status vg_mlp_set_params(vg_mlp *mlp, const float *params);
+/* Copies the FP32 master parameters to 1985 host floats. */
+vg_status vg_mlp_get_params(vg_mlp *mlp, float *params);
+
+/* Features of every block of an inserted container (all systems, global
+ * block order): total blocks x 27 floats, row-major. */
+vg_status vg_mlp_features(vg_ctx *ctx, float *X, int on_device);
+
+/* k* of every cell of the last vg_compute() (n int32, input order). */
+vg_status vg_mlp_labels(vg_ctx *ctx, int32_t *kstar, int on_device);
+
+/*
+ * Training rows from the last vg_compute(): one per block holding a
+ * particle, in block order: features into X (DEVICE, room for total blocks
+ * x 27 floats) and targets into t (DEVICE, room for total blocks floats);
+ * *m receives the number of rows.
+ */
+vg_status vg_mlp_dataset(vg_ctx *ctx, float *X, float *t, int64_t *m);
+
+/* Loss and gradient over M device rows (X: M x 27, t: M) at the current
+ * FP16 weights, without an update; grad is 1985 host floats (may be NULL). */
+vg_status vg_mlp_loss_grad(vg_mlp *mlp, const float *X, const float *t, int64_t M, float u,
+                           double *loss, float *grad);
+
+/* `steps` full-batch Adam steps over M device rows with learning rate lr
+ * and under-prediction weight u; losses (host, `steps` floats, may be NULL)
+ * receives the loss before each step. */
+vg_status vg_mlp_train(vg_mlp *mlp, const float *X, const float *t, int64_t M, float u, float lr,
+                       int steps, float *losses);
+
+/* Network output y for M device rows of features (y: M device floats). */
+vg_status vg_mlp_infer(vg_mlp *mlp, const float *X, int64_t M, float *y);
+
+/*
+ * Per-block preload targets for the inserted container: clamp(alpha exp(y),
+ * kmin, kmax) for every block, used by vg_compute() with use_mlp = 1 until
+ * the next insert.  VG_ERR_STATE before an insert.
+ */
+vg_status vg_mlp_predict(vg_ctx *ctx, vg_mlp *mlp, float alpha, float kmin, float kmax);
 
 /*
  * Counting sort into blocks that allocates no device memory.  The paper has

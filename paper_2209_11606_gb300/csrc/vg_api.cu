@@ -243,6 +243,7 @@ vg_status prepare_insert(vg_ctx *c, const std::vector<long long> &counts, const 
     // buffers may move below: a captured graph would point at freed memory
     release_graph(c);
     c->inserted = 0;
+    c->kblock_valid = 0;
     c->computed = 0;
     const int d = c->dim;
     vg_status ls = layout_systems(c, counts);
@@ -271,6 +272,8 @@ vg_status prepare_insert(vg_ctx *c, const std::vector<long long> &counts, const 
     VG_CUDA(ensure(c, c->d_w_cuts, n));
     VG_CUDA(ensure(c, c->d_w_retest, n));
     VG_CUDA(ensure(c, c->d_w_newv, n));
+    VG_CUDA(ensure(c, c->d_w_pref, n));
+    VG_CUDA(ensure(c, c->d_rfin, n));
     VG_CUDA(ensure(c, c->d_w_fallback, n));
     if (!on_device) {
         VG_CUDA(ensure(c, c->d_pos, n * d));
@@ -346,7 +349,7 @@ vg_status check_config(vg_ctx *c, const vg_config &cfg) {
     if (cfg.precision != VG_FP64 && cfg.precision != VG_FP32_RETEST) return fail(c, VG_ERR_ARG, "precision");
     if (cfg.order != VG_WALK && cfg.order != VG_PREFETCH) return fail(c, VG_ERR_ARG, "order");
     if (!(cfg.tol32 > 0) || !(cfg.tau_rel > 0) || !(cfg.merge_rel > 0)) return fail(c, VG_ERR_ARG, "tolerances");
-    if (cfg.use_mlp && !c->d_kblock) return fail(c, VG_ERR_STATE, "use_mlp without MLP predictions");
+    if (cfg.use_mlp && !c->kblock_valid) return fail(c, VG_ERR_STATE, "use_mlp without vg_mlp_predict after the insert");
     return VG_OK;
 }
 
@@ -366,11 +369,12 @@ cudaError_t enqueue_cells(vg_ctx *c, const vg_config &cfg, cudaStream_t s) {
     Offsets off;
     off.code = c->d_off_code; off.lb = c->d_off_lb;
     Out o;
-    o.vol = c->d_vol; o.area = c->d_area; o.cen = c->d_cen;
+    o.vol = c->d_vol; o.area = c->d_area; o.cen = c->d_cen; o.rfin = c->d_rfin;
     o.nv = c->d_nv; o.ne = c->d_ne; o.nf = c->d_nf; o.status = c->d_status;
     o.fptr = c->d_fptr; o.faces = c->d_faces; o.fcount = c->d_fcount; o.fcap = c->fcap;
     o.w_tested = c->d_w_tested; o.w_vtests = c->d_w_vtests; o.w_cuts = c->d_w_cuts;
     o.w_retest = c->d_w_retest; o.w_fallback = c->d_w_fallback; o.w_newv = c->d_w_newv;
+    o.w_pref = c->d_w_pref;
     o.retry = c->d_caplist; o.retry_count = c->d_capcount;
     o.retry2 = c->d_caplist2; o.retry2_count = c->d_capcount2;
     cudaError_t e;
@@ -772,7 +776,7 @@ vg_status vg_get_kernel_ms(vg_ctx *c, double *total_ms, int64_t *count) {
 }
 
 vg_status vg_get_work(vg_ctx *c, int32_t *n_tested, int32_t *n_vtests, int32_t *n_cuts, int32_t *n_newv,
-                      int32_t *n_retest, uint8_t *fallback, int on_device) {
+                      int32_t *n_retest, uint8_t *fallback, int32_t *n_prefetch, int on_device) {
     if (!c) return VG_ERR_ARG;
     if (c->graph_unchecked) {
         vg_status gs = graph_check(c);
@@ -787,7 +791,18 @@ vg_status vg_get_work(vg_ctx *c, int32_t *n_tested, int32_t *n_vtests, int32_t *
     if ((s = copy_out(c, n_newv, c->d_w_newv, sizeof(int) * n, on_device))) return s;
     if ((s = copy_out(c, n_retest, c->d_w_retest, sizeof(int) * n, on_device))) return s;
     if ((s = copy_out(c, fallback, c->d_w_fallback, n, on_device))) return s;
+    if ((s = copy_out(c, n_prefetch, c->d_w_pref, sizeof(int) * n, on_device))) return s;
     return VG_OK;
+}
+
+vg_status vg_get_radius(vg_ctx *c, float *rmax, int on_device) {
+    if (!c) return VG_ERR_ARG;
+    if (c->graph_unchecked) {
+        vg_status gs = graph_check(c);
+        if (gs != VG_OK) return gs;
+    }
+    if (!c->computed) return fail(c, VG_ERR_STATE, "no computed cells");
+    return copy_out(c, rmax, c->d_rfin, sizeof(float) * c->n, on_device);
 }
 
 vg_status vg_get_sorted(vg_ctx *c, int64_t *n_blocks, int32_t *block_start, int32_t *order, int on_device) {
@@ -837,6 +852,8 @@ void vg_destroy(vg_ctx *c) {
     release(c->d_w_fallback); release(c->d_caplist); release(c->d_capcount);
     release(c->d_caplist2); release(c->d_capcount2);
     release(c->d_off_code); release(c->d_off_lb); release(c->d_kblock); release(c->d_w_newv);
+    release(c->d_w_pref); release(c->d_rfin);
+    release(c->d_kstar); release(c->d_kmax); release(c->d_feat);
     release(c->d_sys_init);
     release_graph(c);
     for (int k = 0; k < 2; k++)

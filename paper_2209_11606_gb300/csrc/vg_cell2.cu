@@ -637,6 +637,7 @@ __global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Store st
                 }
                 if (gl == 0) {
                     o.vol[out_i] = 0.5 * area;
+                    o.rfin[out_i] = (float)sqrt((double)r2);
                     o.area[out_i] = (double)per;
                     const T inv = (T)1 / ((T)3 * (T)area);
                     o.cen[(long long)out_i * 3 + 0] = (double)rx + (double)(cxs * inv);
@@ -652,7 +653,7 @@ __global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Store st
             break;
             }  // pass
         } else if (!fail && gl == 0) {
-            o.vol[out_i] = 0; o.area[out_i] = 0;
+            o.vol[out_i] = 0; o.area[out_i] = 0; o.rfin[out_i] = 0.f;
             for (int a = 0; a < 3; a++) o.cen[(long long)out_i * 3 + a] = 0;
             o.nv[out_i] = o.ne[out_i] = o.nf[out_i] = 0;
             o.status[out_i] = (unsigned char)status;
@@ -668,7 +669,7 @@ __global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Store st
             }
             o.status[out_i] = VG_CELL_CAP;
             o.nv[out_i] = o.ne[out_i] = o.nf[out_i] = 0;
-            o.vol[out_i] = 0; o.area[out_i] = 0;
+            o.vol[out_i] = 0; o.area[out_i] = 0; o.rfin[out_i] = 0.f;
             o.fptr[out_i] = 0;
         }
         if (pp.collect && gl == 0) {
@@ -678,6 +679,7 @@ __global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Store st
             o.w_newv[out_i] = 2 * S.cnt[2];
             o.w_retest[out_i] = S.cnt[3];
             o.w_fallback[out_i] = 0;
+            o.w_pref[out_i] = 0;
         }
         __syncwarp(gmask);
     }

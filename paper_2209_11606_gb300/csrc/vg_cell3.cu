@@ -672,6 +672,7 @@ __global__ void __launch_bounds__(128, VG_MINB)
                         }
                         src.mode = 0;
                         src.count = count;
+                        if (pp.collect && lane == 0) S.cnt[5] = count;
                         src.rho2 = rho2;
                         src.rg[0] = rg0; src.rg[1] = rg1; src.rg[2] = rg2;
                     }
@@ -1325,6 +1326,7 @@ __global__ void __launch_bounds__(128, VG_MINB)
                     if (lane == 0) {
                         const double v6 = vol;
                         o.vol[out_i] = v6 * (1.0 / 6.0);
+                        o.rfin[out_i] = (float)sqrt((double)r2);
                         o.area[out_i] = (double)area;
                         // centroid = sum det (u0 + a + b) / (4 sum det)
                         const T inv = v6 != 0.0 ? (T)1 / ((T)4 * (T)v6) : (T)0;
@@ -1344,6 +1346,7 @@ __global__ void __launch_bounds__(128, VG_MINB)
             } else if (!fail && lane == 0) {
                 o.vol[out_i] = 0;
                 o.area[out_i] = 0;
+                o.rfin[out_i] = 0.f;
                 for (int a = 0; a < 3; a++) o.cen[(long long)out_i * 3 + a] = 0;
                 o.nv[out_i] = 0; o.ne[out_i] = 0; o.nf[out_i] = 0;
                 o.status[out_i] = (unsigned char)status;
@@ -1359,7 +1362,7 @@ __global__ void __launch_bounds__(128, VG_MINB)
                 }
                 o.status[out_i] = VG_CELL_CAP;
                 o.nf[out_i] = 0; o.nv[out_i] = 0; o.ne[out_i] = 0;
-                o.vol[out_i] = 0; o.area[out_i] = 0;
+                o.vol[out_i] = 0; o.area[out_i] = 0; o.rfin[out_i] = 0.f;
                 o.fptr[out_i] = 0;
             }
             if (pp.collect && lane == 0) {
@@ -1369,6 +1372,7 @@ __global__ void __launch_bounds__(128, VG_MINB)
                 o.w_newv[out_i] = S.cnt[3];
                 o.w_retest[out_i] = S.cnt[4];
                 o.w_fallback[out_i] = (unsigned char)src.fell_back;
+                o.w_pref[out_i] = S.cnt[5];
             }
             __syncwarp();
         }

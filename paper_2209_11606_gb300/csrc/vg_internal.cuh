@@ -66,6 +66,7 @@ struct Store {
 // Per-cell outputs (indexed by input index) and the face bump buffer.
 struct Out {
     double *vol, *area, *cen;     // cen: n x dim
+    float *rfin;                  // R: largest vertex distance of the final cell
     int *nv, *ne, *nf;
     unsigned char *status;
     long long *fptr;              // offset of the cell's faces in `faces`
@@ -73,7 +74,7 @@ struct Out {
     unsigned long long *fcount;   // bump counter
     long long fcap;               // capacity of `faces`
     // optional work counters
-    int *w_tested, *w_vtests, *w_cuts, *w_newv, *w_retest;
+    int *w_tested, *w_vtests, *w_cuts, *w_newv, *w_retest, *w_pref;
     unsigned char *w_fallback;
     int *retry;                   // sorted indices of cells for tier 1
     int *retry_count;
@@ -187,7 +188,8 @@ struct vg_ctx {
     signed char *d_img = nullptr;
     unsigned char *d_ford = nullptr;
     int *d_w_tested = nullptr, *d_w_vtests = nullptr, *d_w_cuts = nullptr, *d_w_retest = nullptr;
-    int *d_w_newv = nullptr;
+    int *d_w_newv = nullptr, *d_w_pref = nullptr;
+    float *d_rfin = nullptr;
     // event pairs around the cell kernels (time_kernels)
     static constexpr int NEV = 256;
     cudaEvent_t ev[2 * NEV] = {};
@@ -215,6 +217,12 @@ struct vg_ctx {
     const double *g_pos = nullptr, *g_rad = nullptr;
     vg_config g_cfg{};
 
-    // MLP per-block predictions
+    // learned preload targets, one per block (valid until the next insert)
     float *d_kblock = nullptr;
+    long long cap_kblock = 0;
+    int kblock_valid = 0;
+    // training data of the predictor: k* per cell, largest k* and features per block
+    int *d_kstar = nullptr, *d_kmax = nullptr;
+    float *d_feat = nullptr;
+    long long cap_kstar = 0, cap_kmax = 0, cap_feat = 0;
 };

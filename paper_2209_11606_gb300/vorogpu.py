@@ -26,9 +26,13 @@ VG_CELL_OK, VG_CELL_EMPTY, VG_CELL_CAP, VG_CELL_DUP, VG_CELL_LIMIT = 0, 1, 2, 3,
 
 EXPORTS = ["vg_config_default", "vg_create", "vg_batch_create", "vg_insert", "vg_batch_insert",
            "vg_compute", "vg_get_counts", "vg_get_cells", "vg_get_faces", "vg_get_work",
-           "vg_get_sorted", "vg_get_grid", "vg_get_system_grid", "vg_get_launches",
+           "vg_get_radius", "vg_get_sorted", "vg_get_grid", "vg_get_system_grid", "vg_get_launches",
            "vg_get_kernel_ms", "vg_graph_capture", "vg_graph_launch", "vg_graph_sync",
-           "vg_sort_blocks_noalloc", "vg_last_error", "vg_destroy"]
+           "vg_sort_blocks_noalloc", "vg_last_error", "vg_destroy",
+           "vg_mlp_create", "vg_mlp_destroy", "vg_mlp_last_error", "vg_mlp_set_params",
+           "vg_mlp_get_params", "vg_mlp_features", "vg_mlp_labels", "vg_mlp_dataset",
+           "vg_mlp_loss_grad", "vg_mlp_train", "vg_mlp_infer", "vg_mlp_predict"]
+MLP_NPARAM = 1985
 
 
 class VgConfig(ctypes.Structure):
@@ -76,7 +80,8 @@ def load(path: str = LIB_PATH):
         "vg_get_counts": (I, [P, ctypes.POINTER(L), ctypes.POINTER(L)]),
         "vg_get_cells": (I, [P, P, P, P, P, P, P, P, I]),
         "vg_get_faces": (I, [P, P, P, P, P, I]),
-        "vg_get_work": (I, [P, P, P, P, P, P, P, I]),
+        "vg_get_work": (I, [P, P, P, P, P, P, P, P, I]),
+        "vg_get_radius": (I, [P, P, I]),
         "vg_get_kernel_ms": (I, [P, ctypes.POINTER(D), ctypes.POINTER(L)]),
         "vg_get_sorted": (I, [P, ctypes.POINTER(L), P, P, I]),
         "vg_get_grid": (I, [P, P]),
@@ -84,6 +89,18 @@ def load(path: str = LIB_PATH):
         "vg_get_launches": (I, [P, ctypes.POINTER(L)]),
         "vg_sort_blocks_noalloc": (I, [I, P, P, P, P, L, P, P, P, P, ctypes.c_char_p, I]),
         "vg_last_error": (ctypes.c_char_p, [P]),
+        "vg_mlp_create": (I, [ctypes.POINTER(P), P]),
+        "vg_mlp_destroy": (None, [P]),
+        "vg_mlp_last_error": (ctypes.c_char_p, [P]),
+        "vg_mlp_set_params": (I, [P, P]),
+        "vg_mlp_get_params": (I, [P, P]),
+        "vg_mlp_features": (I, [P, P, I]),
+        "vg_mlp_labels": (I, [P, P, I]),
+        "vg_mlp_dataset": (I, [P, P, P, ctypes.POINTER(L)]),
+        "vg_mlp_loss_grad": (I, [P, P, P, L, ctypes.c_float, ctypes.POINTER(D), P]),
+        "vg_mlp_train": (I, [P, P, P, L, ctypes.c_float, ctypes.c_float, I, P]),
+        "vg_mlp_infer": (I, [P, P, L, P]),
+        "vg_mlp_predict": (I, [P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
         "vg_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -233,11 +250,16 @@ def vg_get_faces(ctx, face_off=None, nbr_id=None, nbr_img=None, face_order=None)
 
 
 def vg_get_work(ctx, n_tested=None, n_vtests=None, n_cuts=None, n_newv=None, n_retest=None,
-                fallback=None):
-    arrs = [n_tested, n_vtests, n_cuts, n_newv, n_retest, fallback]
+                fallback=None, n_prefetch=None):
+    arrs = [n_tested, n_vtests, n_cuts, n_newv, n_retest, fallback, n_prefetch]
     dev = {(_ptr(a)[1]) for a in arrs if a is not None}
     on_dev = dev.pop() if dev else 0
     _check(ctx, load().vg_get_work(ctx, *[_ptr(a)[0] for a in arrs], on_dev))
+
+
+def vg_get_radius(ctx, rmax):
+    p, dev = _ptr(rmax)
+    _check(ctx, load().vg_get_radius(ctx, p, dev))
 
 
 def vg_get_sorted(ctx, block_start=None, order=None):
@@ -295,9 +317,102 @@ def vg_sort_blocks_noalloc(dim, lo, hi, periodic, nblocks, pos, block_start, ord
         raise VgError(code, buf.value.decode())
 
 
+def vg_last_error(ctx) -> str:
+    return load().vg_last_error(ctx).decode()
+
+
+def vg_mlp_last_error(m) -> str:
+    return load().vg_mlp_last_error(m).decode()
+
+
 def vg_destroy(ctx):
     if ctx:
         load().vg_destroy(ctx)
+
+
+# ---- learned candidate count ------------------------------------------------------
+
+def _mcheck(m, code):
+    if code != VG_OK:
+        msg = _lib.vg_mlp_last_error(m).decode() if m else ""
+        raise VgError(code, msg)
+
+
+def _dev_ptr(x, what):
+    p, dev = _ptr(x)
+    if not dev:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    return p
+
+
+def vg_mlp_create(stream=None):
+    h = ctypes.c_void_p()
+    st = None
+    if stream is not None:
+        st = stream if isinstance(stream, int) else stream.cuda_stream
+    code = load().vg_mlp_create(ctypes.byref(h), st)
+    if code != VG_OK:
+        raise VgError(code, "vg_mlp_create failed")
+    return h
+
+
+def vg_mlp_destroy(m):
+    if m:
+        load().vg_mlp_destroy(m)
+
+
+def vg_mlp_set_params(m, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.shape != (MLP_NPARAM,):
+        raise ValueError(f"params must hold {MLP_NPARAM} floats")
+    _mcheck(m, load().vg_mlp_set_params(m, p.ctypes.data))
+
+
+def vg_mlp_get_params(m):
+    p = np.zeros(MLP_NPARAM, np.float32)
+    _mcheck(m, load().vg_mlp_get_params(m, p.ctypes.data))
+    return p
+
+
+def vg_mlp_features(ctx, X):
+    p, dev = _ptr(X)
+    _check(ctx, load().vg_mlp_features(ctx, p, dev))
+
+
+def vg_mlp_labels(ctx, kstar):
+    p, dev = _ptr(kstar)
+    _check(ctx, load().vg_mlp_labels(ctx, p, dev))
+
+
+def vg_mlp_dataset(ctx, X, t):
+    """Training rows into device tensors X (>= blocks x 27) and t (>= blocks);
+    returns the number of rows."""
+    m = ctypes.c_int64()
+    _check(ctx, load().vg_mlp_dataset(ctx, _dev_ptr(X, "X"), _dev_ptr(t, "t"), ctypes.byref(m)))
+    return m.value
+
+
+def vg_mlp_loss_grad(m, X, t, M, u):
+    loss = ctypes.c_double()
+    g = np.zeros(MLP_NPARAM, np.float32)
+    _mcheck(m, load().vg_mlp_loss_grad(m, _dev_ptr(X, "X"), _dev_ptr(t, "t"), int(M), float(u),
+                                       ctypes.byref(loss), g.ctypes.data))
+    return loss.value, g
+
+
+def vg_mlp_train(m, X, t, M, u, lr, steps):
+    losses = np.zeros(max(int(steps), 1), np.float32)
+    _mcheck(m, load().vg_mlp_train(m, _dev_ptr(X, "X"), _dev_ptr(t, "t"), int(M), float(u), float(lr),
+                                   int(steps), losses.ctypes.data))
+    return losses[:int(steps)]
+
+
+def vg_mlp_infer(m, X, M, y):
+    _mcheck(m, load().vg_mlp_infer(m, _dev_ptr(X, "X"), int(M), _dev_ptr(y, "y")))
+
+
+def vg_mlp_predict(ctx, m, alpha=1.0, kmin=8.0, kmax=1024.0):
+    _check(ctx, load().vg_mlp_predict(ctx, m, float(alpha), float(kmin), float(kmax)))
 
 
 # ---- convenience: one call from host arrays to host results -------------------
@@ -328,10 +443,15 @@ def _fetch(ctx, n, d, work) -> dict:
     vg_get_faces(ctx, fo, ids, img, order_)
     out.update({"face_off": fo, "nbr_id": ids[:nface], "nbr_img": img[:nface, :d],
                 "face_order": order_[:nface]})
+    rfin = np.zeros(n, np.float32)
+    vg_get_radius(ctx, rfin)
+    out["rmax"] = rfin
     if work:
-        w = {k: np.zeros(n, np.int32) for k in ("n_tested", "n_vtests", "n_cuts", "n_newv", "n_retest")}
+        w = {k: np.zeros(n, np.int32)
+             for k in ("n_tested", "n_vtests", "n_cuts", "n_newv", "n_retest", "n_prefetch")}
         fb = np.zeros(n, np.uint8)
-        vg_get_work(ctx, w["n_tested"], w["n_vtests"], w["n_cuts"], w["n_newv"], w["n_retest"], fb)
+        vg_get_work(ctx, w["n_tested"], w["n_vtests"], w["n_cuts"], w["n_newv"], w["n_retest"], fb,
+                    w["n_prefetch"])
         w["fallback"] = fb
         out["work"] = w
     return out
