@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Store st
     const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1) << gbase);
     S_t &S = reinterpret_cast<S_t *>(smem_raw)[warp * GPW + gid];
     const int total = cells ? (tier == 1 ? *o.retry_count : (tier == 2 ? *o.retry2_count : ncells)) : st.n;
+    const float tol32f = (float)pp.tol32;
     if (gl == 0) S.sys_id = -1;
     __syncwarp(gmask);
     const Sys &SY = sys_ref<BATCH>(st, S.sysc);
@@ -388,7 +389,7 @@ __global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Store st
                     // ---------------------------------------- cut by q.r = c
                     if (pp.collect && gl == 0) { S.cnt[0]++; S.cnt[1] += nvert; }
                     T tau;
-                    if constexpr (F32) tau = (float)pp.tol32 * sqrtf(r2 * cq);
+                    if constexpr (F32) tau = tol32f * sqrtf(r2 * cq);
                     else tau = (T)(tau_rel_s * sqrt((double)cq));
                     unsigned outm = 0, nearm = 0, onm = 0;
 #pragma unroll
@@ -602,8 +603,8 @@ __global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Store st
             const bool anybad = __any_sync(gmask, bad) || !(area > 0.0);
             if (F32 && pass == 0 && !degen && !anybad) {
                 // FP32 vertex error ~ 3e-7 R relative to the thickness 2A/P
-                const double thick = area / (double)per;
-                if (!(thick * 10.0 > sqrt((double)r2))) {
+                const float thick = (float)area / (float)per;
+                if (!(thick * 10.f > sqrtf((float)r2))) {
                     degen = true;
                     __syncwarp(gmask);
                     continue;
@@ -637,7 +638,8 @@ __global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Store st
                 }
                 if (gl == 0) {
                     o.vol[out_i] = 0.5 * area;
-                    o.rfin[out_i] = (float)sqrt((double)r2);
+                    if constexpr (F32) o.rfin[out_i] = sqrtf(r2);
+                    else o.rfin[out_i] = (float)sqrt(r2);
                     o.area[out_i] = (double)per;
                     const T inv = (T)1 / ((T)3 * (T)area);
                     o.cen[(long long)out_i * 3 + 0] = (double)rx + (double)(cxs * inv);

@@ -378,6 +378,8 @@ __global__ void __launch_bounds__(128, VG_MINB)
     const Grid &g = SY.g;
     const int total = cells ? (tier == 1 ? *o.retry_count : (tier == 2 ? *o.retry2_count : ncells)) : st.n;
     const int chunk = pp.chunk > 0 ? pp.chunk : 1;
+    // FP32 band factor, converted once (FP64 work is scarce on this part)
+    const float tol32f = (float)pp.tol32;
 
     for (int iter = 0; iter < (1 << 30); iter++) {
         int base = 0;
@@ -858,7 +860,7 @@ __global__ void __launch_bounds__(128, VG_MINB)
                 // ================================= cut by the plane q.r = c
                 if (pp.collect && lane == 0) { S.cnt[0]++; S.cnt[1] += ntri; }
                 T tau;
-                if constexpr (F32) tau = (float)pp.tol32 * sqrtf(r2 * qq);
+                if constexpr (F32) tau = tol32f * sqrtf(r2 * qq);
                 else tau = (T)(pp.tau_rel * g.s * sqrt((double)qq));
                 unsigned outm = 0, nearm = 0, onm = 0;
 #pragma unroll
@@ -1268,8 +1270,8 @@ __global__ void __launch_bounds__(128, VG_MINB)
                 bool anybad = __any_sync(FULL, bad);
                 if (F32 && pass == 0 && !degen && !anybad) {
                     // FP32 vertex error ~ 3e-7 R relative to the thickness 3V/A
-                    const double thick = vol / (2.0 * (double)area);
-                    if (!(thick * 10.0 > sqrt((double)r2))) {
+                    const float thick = (float)vol / (2.f * (float)area);
+                    if (!(thick * 10.f > sqrtf((float)r2))) {
                         degen = true;
                         __syncwarp();
                         continue;
@@ -1326,7 +1328,8 @@ __global__ void __launch_bounds__(128, VG_MINB)
                     if (lane == 0) {
                         const double v6 = vol;
                         o.vol[out_i] = v6 * (1.0 / 6.0);
-                        o.rfin[out_i] = (float)sqrt((double)r2);
+                        if constexpr (F32) o.rfin[out_i] = sqrtf(r2);
+                        else o.rfin[out_i] = (float)sqrt(r2);
                         o.area[out_i] = (double)area;
                         // centroid = sum det (u0 + a + b) / (4 sum det)
                         const T inv = v6 != 0.0 ? (T)1 / ((T)4 * (T)v6) : (T)0;
