@@ -97,7 +97,7 @@ typedef struct {
     int use_mlp;       /* VG_PREFETCH: 1 = take the per-block candidate count
                           written by vg_mlp_predict() after the last insert */
     int chunk;         /* cells taken per work-queue ticket; <= 0: default */
-    int warps_per_cta; /* <= 0: default */
+    int warps_per_cta; /* 3D cells per CTA (one warp each), 1..4; <= 0: 4 */
     int collect_stats; /* 1 = fill the per-cell work counters */
     int time_kernels;  /* 1 = record CUDA events around the cell kernels on the
                           context's stream (read with vg_get_kernel_ms) */
@@ -171,6 +171,17 @@ vg_status vg_insert(vg_ctx *ctx, int64_t n, const double *pos, const double *rad
 
 /* Computes all cells with the given configuration (NULL: defaults). */
 vg_status vg_compute(vg_ctx *ctx, const vg_config *cfg);
+
+/*
+ * Computes only the cells of the m input indices in `cells` (host or device
+ * int32 per on_device), e.g. a sample for timing a configuration.  The
+ * per-cell arrays of the listed cells then equal those of vg_compute();
+ * those of other cells are unspecified, and vg_get_faces / vg_get_counts
+ * return VG_ERR_STATE until the next full compute.  VG_ERR_ARG for an index
+ * outside [0, n).
+ */
+vg_status vg_compute_subset(vg_ctx *ctx, const vg_config *cfg, const int32_t *cells, int64_t m,
+                            int on_device);
 
 /*
  * CUDA graph of one whole step (the paper has no counterpart; it replaces

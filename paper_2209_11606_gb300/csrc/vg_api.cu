@@ -244,6 +244,7 @@ vg_status prepare_insert(vg_ctx *c, const std::vector<long long> &counts, const 
     release_graph(c);
     c->inserted = 0;
     c->kblock_valid = 0;
+    c->subset = 0;
     c->computed = 0;
     const int d = c->dim;
     vg_status ls = layout_systems(c, counts);
@@ -349,13 +350,15 @@ vg_status check_config(vg_ctx *c, const vg_config &cfg) {
     if (cfg.precision != VG_FP64 && cfg.precision != VG_FP32_RETEST) return fail(c, VG_ERR_ARG, "precision");
     if (cfg.order != VG_WALK && cfg.order != VG_PREFETCH) return fail(c, VG_ERR_ARG, "order");
     if (!(cfg.tol32 > 0) || !(cfg.tau_rel > 0) || !(cfg.merge_rel > 0)) return fail(c, VG_ERR_ARG, "tolerances");
+    if (cfg.warps_per_cta > 4) return fail(c, VG_ERR_ARG, "warps_per_cta above 4 (CTAs of at most 128 threads)");
     if (cfg.use_mlp && !c->kblock_valid) return fail(c, VG_ERR_STATE, "use_mlp without vg_mlp_predict after the insert");
     return VG_OK;
 }
 
 // The three cell launches (tier 0 over all cells, then the large-cell
 // tiers over the cells the previous tier handed on), enqueued on `s`.
-cudaError_t enqueue_cells(vg_ctx *c, const vg_config &cfg, cudaStream_t s) {
+cudaError_t enqueue_cells(vg_ctx *c, const vg_config &cfg, cudaStream_t s, const int *subset = nullptr,
+                          int nsubset = 0) {
     Store st;
     st.p32 = c->d_p32; st.p64 = c->d_p64; st.sid = c->d_sid; st.sblk = c->d_sblk; st.bstart = c->d_bstart;
     st.ssys = c->d_ssys; st.sys = c->d_sys; st.sys0 = c->sys[0]; st.nsys = (int)c->sys.size();
@@ -382,8 +385,8 @@ cudaError_t enqueue_cells(vg_ctx *c, const vg_config &cfg, cudaStream_t s) {
     if ((e = cudaMemsetAsync(c->d_capcount, 0, sizeof(int), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->d_capcount2, 0, sizeof(int), s)) != cudaSuccess) return e;
     auto launch = c->dim == 3 ? launch_cells3 : launch_cells2;
-    const int nc = (int)c->n;
-    if ((e = launch(st, o, pp, off, cfg.precision, c->d_ticket, c->sm_count, cfg.warps_per_cta, nullptr, nc, 0, s)))
+    const int nc = subset ? nsubset : (int)c->n;
+    if ((e = launch(st, o, pp, off, cfg.precision, c->d_ticket, c->sm_count, cfg.warps_per_cta, subset, nc, 0, s)))
         return e;
     if ((e = launch(st, o, pp, off, cfg.precision, c->d_ticket + 1, c->sm_count, 0, c->d_caplist, 0, 1, s))) return e;
     return launch(st, o, pp, off, cfg.precision, c->d_ticket + 2, c->sm_count, 0, c->d_caplist2, 0, 2, s);
@@ -565,6 +568,56 @@ vg_status vg_compute(vg_ctx *c, const vg_config *cfg_in) {
     c->launches += g_launch_count - l0;
     if (e != cudaSuccess) return cuda_fail(c, e, "compact_faces");
     c->computed = 1;
+    c->subset = 0;
+    return VG_OK;
+}
+
+vg_status vg_compute_subset(vg_ctx *c, const vg_config *cfg_in, const int32_t *cells, int64_t m, int on_device) {
+    if (!c) return VG_ERR_ARG;
+    if (!c->inserted) return fail(c, VG_ERR_STATE, "vg_compute_subset before vg_insert");
+    vg_config cfg;
+    if (cfg_in) cfg = *cfg_in; else vg_config_default(&cfg);
+    vg_status s = check_config(c, cfg);
+    if (s != VG_OK) return s;
+    if (m < 0 || m > c->n || (m > 0 && !cells)) return fail(c, VG_ERR_ARG, "bad cell list");
+    if (c->graph_unchecked && (s = graph_check(c)) != VG_OK) return s;
+    release_graph(c);
+    const long long n = c->n;
+    const long long l0 = g_launch_count;
+    const long long want = std::max<long long>(1024, n * 24);
+    if (c->fcap < want) {
+        VG_CUDA(ensure(c, c->d_faces, want));
+        c->fcap = want;
+    }
+    VG_CUDA(ensure(c, c->d_rank, n));
+    VG_CUDA(ensure(c, c->d_subset, m));
+    VG_CUDA(ensure(c, c->d_subset_in, m));
+    const int32_t *in = cells;
+    if (!on_device && m > 0) {
+        VG_CUDA(cudaMemcpyAsync(c->d_subset_in, cells, sizeof(int) * m, cudaMemcpyHostToDevice, c->stream));
+        in = c->d_subset_in;
+    }
+    cudaError_t e = map_cells(c->d_sid, n, in, m, c->d_rank, c->d_subset, c->d_err + 2, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "map_cells");
+    int bad = 0;
+    VG_CUDA(cudaMemcpyAsync(&bad, c->d_err + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    VG_CUDA(cudaStreamSynchronize(c->stream));
+    if (bad) return fail(c, VG_ERR_ARG, std::to_string(bad) + " cell indices outside [0, n)");
+    const bool timed = cfg.time_kernels && c->nev < vg_ctx::NEV;
+    if (timed) {
+        for (int k = 0; k < 2; k++)
+            if (!c->ev[2 * c->nev + k]) VG_CUDA(cudaEventCreate(&c->ev[2 * c->nev + k]));
+        VG_CUDA(cudaEventRecord(c->ev[2 * c->nev], c->stream));
+    }
+    e = enqueue_cells(c, cfg, c->stream, c->d_subset, (int)m);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cell kernels");
+    if (timed) {
+        VG_CUDA(cudaEventRecord(c->ev[2 * c->nev + 1], c->stream));
+        c->nev++;
+    }
+    c->launches += g_launch_count - l0;
+    c->computed = 1;
+    c->subset = 1;
     return VG_OK;
 }
 
@@ -681,6 +734,7 @@ vg_status vg_graph_launch(vg_ctx *c) {
     c->launches += c->graph_kernels;
     c->inserted = 1;
     c->computed = 1;
+    c->subset = 0;
     c->graph_unchecked = 1;
     return VG_OK;
 }
@@ -701,6 +755,7 @@ vg_status vg_get_counts(vg_ctx *c, int64_t *n_cells, int64_t *n_faces) {
         if (gs != VG_OK) return gs;
     }
     if (!c->computed) return fail(c, VG_ERR_STATE, "no computed cells");
+    if (c->subset) return fail(c, VG_ERR_STATE, "faces exist after a full compute only");
     if (n_cells) *n_cells = c->n;
     if (n_faces) {
         long long t = 0;
@@ -748,6 +803,7 @@ vg_status vg_get_faces(vg_ctx *c, int64_t *face_off, int32_t *nbr_id, int8_t *nb
         if (gs != VG_OK) return gs;
     }
     if (!c->computed) return fail(c, VG_ERR_STATE, "no computed cells");
+    if (c->subset) return fail(c, VG_ERR_STATE, "faces exist after a full compute only");
     const long long n = c->n;
     long long t = 0;
     VG_CUDA(cudaMemcpyAsync(&t, c->d_face_off + n, sizeof t, cudaMemcpyDeviceToHost, c->stream));
@@ -854,6 +910,7 @@ void vg_destroy(vg_ctx *c) {
     release(c->d_off_code); release(c->d_off_lb); release(c->d_kblock); release(c->d_w_newv);
     release(c->d_w_pref); release(c->d_rfin);
     release(c->d_kstar); release(c->d_kmax); release(c->d_feat);
+    release(c->d_rank); release(c->d_subset); release(c->d_subset_in);
     release(c->d_sys_init);
     release_graph(c);
     for (int k = 0; k < 2; k++)

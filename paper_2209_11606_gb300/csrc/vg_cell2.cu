@@ -602,9 +602,11 @@ __global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Store st
             edges = __reduce_add_sync(gmask, edges);
             const bool anybad = __any_sync(gmask, bad) || !(area > 0.0);
             if (F32 && pass == 0 && !degen && !anybad) {
-                // FP32 vertex error ~ 3e-7 R relative to the thickness 2A/P
+                // FP32 vertex error ~ 3e-7 max(R, h) (h: the block side that
+                // bounds the stored FP32 offsets) relative to the thickness 2A/P
                 const float thick = (float)area / (float)per;
-                if (!(thick * 10.f > sqrtf((float)r2))) {
+                const float scale = fmaxf(sqrtf((float)r2), fmaxf(g.hf[0], g.hf[1]));
+                if (!(thick * 10.f > scale)) {
                     degen = true;
                     __syncwarp(gmask);
                     continue;

@@ -1269,9 +1269,11 @@ __global__ void __launch_bounds__(128, VG_MINB)
                 const int osum = __reduce_add_sync(FULL, order_sum);
                 bool anybad = __any_sync(FULL, bad);
                 if (F32 && pass == 0 && !degen && !anybad) {
-                    // FP32 vertex error ~ 3e-7 R relative to the thickness 3V/A
+                    // FP32 vertex error ~ 3e-7 max(R, h) (h: the block side that
+                    // bounds the stored FP32 offsets) relative to the thickness 3V/A
                     const float thick = (float)vol / (2.f * (float)area);
-                    if (!(thick * 10.f > sqrtf((float)r2))) {
+                    const float scale = fmaxf(sqrtf((float)r2), fmaxf(g.hf[0], fmaxf(g.hf[1], g.hf[2])));
+                    if (!(thick * 10.f > scale)) {
                         degen = true;
                         __syncwarp();
                         continue;

@@ -130,6 +130,11 @@ cudaError_t launch_cells2(const Store &s, const Out &o, const Params &p, const O
                           int precision, unsigned *ticket, int sm_count, int warps_per_cta,
                           const int *cells, int ncells, int tier, cudaStream_t st);
 
+// Sorted positions of the input indices cells[0..m) (via the inverse of
+// sid); out-of-range indices are counted in *bad and mapped to 0.
+cudaError_t map_cells(const int *sid, long long n, const int *cells, long long m, int *rank, int *out, int *bad,
+                      cudaStream_t st);
+
 cudaError_t compact_faces(long long n, const int *nf, const unsigned char *status,
                           const long long *fptr, const int2 *faces, long long fcap, long long *face_off,
                           int *nbr_id, signed char *nbr_img, unsigned char *face_order,
@@ -203,6 +208,10 @@ struct vg_ctx {
     float *d_off_lb = nullptr;
 
     long long launches = 0;   // kernels launched by this context
+
+    // vg_compute_subset: sorted position of every input index, the mapped list
+    int *d_rank = nullptr, *d_subset = nullptr, *d_subset_in = nullptr;
+    int subset = 0;           // the last compute covered a subset of the cells
 
     // CUDA graph of one whole step (sort -> cells -> faces), vg_graph_capture()
     cudaStream_t gstream = nullptr;       // capture stream (non-blocking)

@@ -273,6 +273,44 @@ cudaError_t sort_particles(const Sys *sys, int nsys, int dim, long long total_bl
     return cudaGetLastError();
 }
 
+// ---- cell lists -----------------------------------------------------------------
+
+namespace {
+__global__ void k_rank(const int *__restrict__ sid, long long n, int *__restrict__ rank) {
+    const long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (u < n) rank[sid[u]] = (int)u;
+}
+
+__global__ void k_map(const int *__restrict__ cells, long long m, long long n, const int *__restrict__ rank,
+                      int *__restrict__ out, int *__restrict__ bad) {
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    const int i = cells[k];
+    if (i < 0 || i >= n) {
+        atomicAdd(bad, 1);
+        out[k] = 0;
+    } else {
+        out[k] = rank[i];
+    }
+}
+}  // namespace
+
+cudaError_t map_cells(const int *sid, long long n, const int *cells, long long m, int *rank, int *out, int *bad,
+                      cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    const int T = 256;
+    if (n > 0) {
+        ++g_launch_count;
+        k_rank<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(sid, n, rank);
+    }
+    if (m > 0) {
+        ++g_launch_count;
+        k_map<<<(unsigned)((m + T - 1) / T), T, 0, st>>>(cells, m, n, rank, out, bad);
+    }
+    return cudaGetLastError();
+}
+
 // ---- CSR compaction of faces ---------------------------------------------------
 
 namespace {

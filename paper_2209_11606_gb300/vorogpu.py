@@ -25,7 +25,7 @@ VG_WALK, VG_PREFETCH = 0, 1
 VG_CELL_OK, VG_CELL_EMPTY, VG_CELL_CAP, VG_CELL_DUP, VG_CELL_LIMIT = 0, 1, 2, 3, 4
 
 EXPORTS = ["vg_config_default", "vg_create", "vg_batch_create", "vg_insert", "vg_batch_insert",
-           "vg_compute", "vg_get_counts", "vg_get_cells", "vg_get_faces", "vg_get_work",
+           "vg_compute", "vg_compute_subset", "vg_get_counts", "vg_get_cells", "vg_get_faces", "vg_get_work",
            "vg_get_radius", "vg_get_sorted", "vg_get_grid", "vg_get_system_grid", "vg_get_launches",
            "vg_get_kernel_ms", "vg_graph_capture", "vg_graph_launch", "vg_graph_sync",
            "vg_sort_blocks_noalloc", "vg_last_error", "vg_destroy",
@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH):
         "vg_insert": (I, [P, L, P, P, I]),
         "vg_batch_insert": (I, [P, P, P, P, I]),
         "vg_compute": (I, [P, ctypes.POINTER(VgConfig)]),
+        "vg_compute_subset": (I, [P, ctypes.POINTER(VgConfig), P, L, I]),
         "vg_graph_capture": (I, [P, P, P, P, ctypes.POINTER(VgConfig)]),
         "vg_graph_launch": (I, [P]),
         "vg_graph_sync": (I, [P]),
@@ -203,6 +204,16 @@ def vg_insert(ctx, pos, radii=None):
 
 def vg_compute(ctx, cfg: VgConfig | None = None):
     _check(ctx, load().vg_compute(ctx, None if cfg is None else ctypes.byref(cfg)))
+
+
+def vg_compute_subset(ctx, cells, cfg: VgConfig | None = None):
+    """Computes the cells whose input indices are listed (int32 numpy array
+    or CUDA tensor)."""
+    if isinstance(cells, np.ndarray):
+        cells = np.ascontiguousarray(cells, dtype=np.int32)
+    p, dev = _ptr(cells)
+    _check(ctx, load().vg_compute_subset(ctx, None if cfg is None else ctypes.byref(cfg), p,
+                                         int(cells.shape[0]), dev))
 
 
 def vg_graph_capture(ctx, counts, pos, radii=None, cfg: VgConfig | None = None):
