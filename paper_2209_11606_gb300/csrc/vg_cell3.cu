@@ -93,6 +93,7 @@ struct Src {
     int nwin;          // walk: blocks in the current window
     int limit, fell_back;
     int last;          // walk: the current window is the last one
+    int nbatch;        // candidate batches loaded for this cell
     float rho2;        // prefetch radius^2 (0: none)
     int rg[3];         // prefetch reach in blocks per axis
 };
@@ -107,6 +108,7 @@ struct Smem {
     unsigned stri[32 * VPL];      // staging for compaction and statistics
     T sx[32 * VPL], sy[32 * VPL], sz[32 * VPL];
     float skap[32 * VPL];
+    float4 v4[32 * VPL];                    // FP32 form: the cell's vertices (x, y, z, kappa); free slots 0
     unsigned long long E[MAXP][MAXP / 64];  // removed directed edges of one cut
     union {
         FT ftab[32][MAXP];             // face walk tables, one row per face of a round
@@ -138,6 +140,27 @@ __device__ __forceinline__ int imgc(int img, int a) { return (int)(signed char)(
 __device__ __forceinline__ int pack_img(int mx, int my, int mz) {
     return (mx & 0xff) | ((my & 0xff) << 8) | ((mz & 0xff) << 16);
 }
+// Whether the plane q.r = c may cut the cell whose vertices are mirrored in
+// v4: some vertex lies beyond -band (band = tau * kappa, the classification's
+// FP32 band), widened by 1 % to cover rounding.  A candidate without such a
+// vertex removes nothing now, and nothing after later cuts either (the cell
+// only shrinks), so one lane can drop it alone instead of the whole warp
+// classifying it; every kept candidate still goes through the exact test.
+// A free slot holds (0, 0, 0, 0): it keeps a candidate only if c <= 0 (a
+// radical plane that the particle itself lies beyond), which is harmless.
+template <int CAP>
+__device__ __forceinline__ bool may_cut(const float4 *v4, float qx, float qy, float qz, float c, float tau) {
+    const float lim = -1.01f * tau;
+    bool m = false;
+#pragma unroll 8
+    for (int t = 0; t < CAP; t++) {
+        const float4 v = v4[t];
+        const float d = fmaf(v.x, qx, fmaf(v.y, qy, fmaf(v.z, qz, -c)));
+        m |= d >= lim * v.w;
+    }
+    return m;
+}
+
 __device__ __forceinline__ int floordiv(int a, int b) {
     int q = a / b;
     if ((a % b != 0) && ((a < 0) != (b < 0))) q--;
@@ -483,6 +506,12 @@ __global__ void __launch_bounds__(128, VG_MINB)
                     vy[0] = sy ? hi[1] : lo[1];
                     vz[0] = sz ? hi[2] : lo[2];
                 }
+                if constexpr (F32) {
+#pragma unroll
+                    for (int s = 0; s < VPL; s++)
+                        S.v4[s * 32 + lane] = tri[s] != TRI_EMPTY ? make_float4(vx[s], vy[s], vz[s], kap[s])
+                                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
             }
             int ntri = 8;        // vertices
             unsigned rows = 1;   // register slots (rows of 32) that hold any vertex
@@ -519,6 +548,7 @@ __global__ void __launch_bounds__(128, VG_MINB)
             src.limit = 0;
             src.fell_back = 0;
             src.last = 0;
+            src.nbatch = 0;
             if constexpr (F32) {
                 if (pp.order == VG_PREFETCH && st.n < (1 << 27)) {
                     float kt = (float)(pp.prefetch_k > 0 ? pp.prefetch_k : 72);
@@ -700,6 +730,9 @@ __global__ void __launch_bounds__(128, VG_MINB)
                         }
                         const int idx = u + lane;
                         const bool in = idx < count;
+                        // the first batch meets the initial box: nothing to drop yet
+                        const int nb0 = src.nbatch;
+                        const bool filt = nb0 > 0;
                         bool ok = false;
                         if (in) {
                             const int slot = S.x.pf.slot[idx];
@@ -710,8 +743,15 @@ __global__ void __launch_bounds__(128, VG_MINB)
                             cimg = r.y;
                             crj = st.radical ? (T)__ldg(&st.p32[r.x]).w : (T)0;
                             ok = (T)q4.w < stop;
+                            if constexpr (F32) {
+                                if (filt && ok && q4.w >= 1e-30f) {
+                                    const float cc = st.radical ? 0.5f * (q4.w + rp32 * rp32 - crj * crj) : 0.5f * q4.w;
+                                    ok = may_cut<CAP>(S.v4, q4.x, q4.y, q4.z, cc, tol32f * sqrtf(r2 * q4.w));
+                                }
+                            }
                         }
                         want = __ballot_sync(FULL, ok);
+                        src.nbatch = nb0 + 1;  // every lane writes the same value
                         // bucketed: once the last entry's bucket starts beyond the
                         // bound, every later entry lies beyond it too
                         const int last = min(count - u, 32) - 1;
@@ -727,6 +767,8 @@ __global__ void __launch_bounds__(128, VG_MINB)
                     if (vp < vtot) {
                         // a batch of the current window's particles
                         const int v = vp + lane;
+                        const int nb0 = src.nbatch;
+                        const bool filt = nb0 > 0;
                         bool ok = false;
                         if (v < vtot) {
                             int lo = 0, hi = src.nwin - 1;  // last block with vstart <= v
@@ -752,10 +794,17 @@ __global__ void __launch_bounds__(128, VG_MINB)
                             }
                             if (ox == 0 && oy == 0 && oz == 0 && j == i) ok = false;
                             ok = ok && cqq < stop;
+                            if constexpr (F32) {
+                                if (filt && ok && cqq >= 1e-30f) {
+                                    const float cc = st.radical ? 0.5f * (cqq + rp32 * rp32 - crj * crj) : 0.5f * cqq;
+                                    ok = may_cut<CAP>(S.v4, cqx, cqy, cqz, cc, tol32f * sqrtf(r2 * cqq));
+                                }
+                            }
                             cref = j;
                             cimg = mc & 0xffffff;
                         }
                         want = __ballot_sync(FULL, ok);
+                        src.nbatch = nb0 + 1;  // every lane writes the same value
                         src.vp = vp + 32;
                         continue;
                     }
@@ -1031,6 +1080,9 @@ __global__ void __launch_bounds__(128, VG_MINB)
                         if constexpr (F32) q2 *= 1.f + 4e-6f * kap[s];  // allowance for FP32 error
                         rr = rr > q2 ? rr : q2;
                     }
+                    if constexpr (F32)
+                        S.v4[s * 32 + lane] = tri[s] != TRI_EMPTY ? make_float4(vx[s], vy[s], vz[s], kap[s])
+                                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
                     if (__any_sync(FULL, tri[s] != TRI_EMPTY)) rows |= 1u << s;
                 }
 #pragma unroll
@@ -1396,7 +1448,7 @@ cudaError_t launch_t(const Store &s, const Out &o, const Params &p, const Offset
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int grid = sm_count * per_sm;
-    if (tier > 0) grid = sm_count;
+    if (tier == 2) grid = sm_count;
     if ((e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
     ++g_launch_count;
     kfn<<<grid, warps * 32, smem, st>>>(s, o, p, off, ticket, cells, ncells, tier);
@@ -1411,7 +1463,10 @@ cudaError_t launch_cells3(const Store &s, const Out &o, const Params &p, const O
     const int w = warps_per_cta > 0 ? warps_per_cta : 4;
     // the rare large cells (tiers 1, 2) always take the batched form
     if (tier == 2) return launch_t<double, 16, 256, true>(s, o, p, off, ticket, sm_count, 1, cells, ncells, tier, st);
-    if (tier == 1) return launch_t<double, 4, 128, true>(s, o, p, off, ticket, sm_count, 2, cells, ncells, tier, st);
+    if (tier == 1)
+        return precision == VG_FP64
+                   ? launch_t<double, 4, 128, true>(s, o, p, off, ticket, sm_count, 2, cells, ncells, tier, st)
+                   : launch_t<float, 4, 128, true>(s, o, p, off, ticket, sm_count, 2, cells, ncells, tier, st);
     const bool batch = s.nsys > 1;
     if (precision == VG_FP64)
         return batch ? launch_t<double, 2, 64, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st)
