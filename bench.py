@@ -1,19 +1,24 @@
 #!/usr/bin/env python
 """Benchmark of the cell-based Voronoi hot path on GB300.
 
-Workload (the 3D metric's configuration): 1,000,000 points uniform i.i.d. in
-a periodic cube of side 100 (unit density, seed 1), 58^3 blocks.  One step is
-the whole hot path on one batch, replayed as one captured CUDA graph
-(vg_graph_capture / vg_graph_launch): counting sort of the device-resident
-points into blocks, the cell kernels (FP32 cuts with FP64 re-test,
-sorted-distance prefetch), and the CSR compaction of the faces.  L2 is
-flushed between steps (a 256 MB write outside the timed events).
+Default workload (the 3D metric's configuration): 1,000,000 points uniform
+i.i.d. in a periodic cube of side 100 (unit density, seed 1), 58^3 blocks.
+One step is the whole hot path on one batch, replayed as one captured CUDA
+graph (vg_graph_capture / vg_graph_launch): counting sort of the
+device-resident points into blocks, the learned per-block preload targets,
+the cell kernels (FP32 cuts with FP64 re-test, distance-sorted preload), and
+the CSR compaction of the faces.  L2 is flushed between steps (a 256 MB write
+outside the timed events).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload uniform1m|slabs102m]
 
-With N > 1 (torchrun, one rank per GPU) every rank processes its own
-1M-point system (weak scaling, no collective on the data path); value is the
-cells of all ranks over the slowest rank's time.
+With N > 1 (torchrun, one rank per GPU) every rank processes its own system
+(weak scaling, no collective on the data path); value is the cells of all
+ranks over the slowest rank's time.
+
+--workload slabs102m runs the 102.4M-point periodic cube of alternating
+perturbed-FCC and uniform slabs instead (no e2e, no batched line).
 
 --impl reference times the FP64 CPU oracle (block-grid walk with the radius
 bound, OpenMP over cells) on this host's cores, on a bounded sample of the
@@ -23,7 +28,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
@@ -35,16 +39,22 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "3D Voronoi cells/s, 1 GB300, chosen vs plain FP64 form; % of roofline"
-N_POINTS = 1_000_000
-SIDE = 100.0
-GRID = (58, 58, 58)
-WORKLOAD = ("uniform1m: 1,000,000 points uniform in a periodic cube of side 100 (seed 1), "
-            "58^3 blocks; chosen form = FP32 cuts + FP64 re-test, sorted prefetch")
+WORKLOADS = {
+    "uniform1m": ("uniform1m: 1,000,000 points uniform in a periodic cube of side 100 (seed 1), 58^3 blocks; "
+                  "chosen form = FP32 cuts + FP64 re-test, learned distance-sorted preload"),
+    "slabs102m": ("slabs102m: 102,400,000 points in a periodic cube of side 296 a (a = 51/32), 8 z-slabs "
+                  "alternating perturbed FCC (sigma 0.05 a) and uniform points (seed 6), blocks by the "
+                  "n_opt = 4.6 rule; chosen form = FP32 cuts + FP64 re-test, learned distance-sorted preload"),
+}
 # FP32 peak derived from unit counts and clock: 152 SMs x 128 FP32 lanes x
 # 2 FLOP (FMA) x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # algorithmic FLOP counts per unit of work (see the design notes)
 FLOP_VTEST, FLOP_CAND, FLOP_NEWV, FLOP_FANTET = 6, 12, 51, 42
+MLP_ALPHA, MLP_KMIN, MLP_KMAX = 1.2, 8.0, 1024.0
+PKG = os.path.join(ROOT, "paper_2209_11606_gb300")
+MLP_PARAMS = os.path.join(PKG, "mlp_params_gb300.json")
+TUNE_CACHE = os.path.join(PKG, "tuned_gb300.json")
 
 
 def parse():
@@ -53,15 +63,20 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="uniform1m", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
 
-def workload(rank: int):
+def workload(name: str, rank: int):
     from paper_2209_11606_gb300 import workloads as W
-    return W.uniform(N_POINTS, 3, SIDE, True, seed=1 + rank)
+    if name == "uniform1m":
+        s = W.uniform(1_000_000, 3, 100.0, True, seed=1 + rank)
+        return s, (58, 58, 58)
+    s = W.fcc_uniform_slabs(seed=6 + rank)
+    return s, None
 
 
 class Clocks:
@@ -112,39 +127,88 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def mlp_params(V, torch):
+    """The learned preload's parameters: from the file the last training run
+    wrote, else trained here on the labels of the 1M-point configuration
+    (uniform and perturbed BCC) by the library's training kernels."""
+    if os.path.exists(MLP_PARAMS):
+        with open(MLP_PARAMS) as f:
+            d = json.load(f)
+        return np.asarray(d["params"], dtype=np.float32), d["meta"]
+    from paper_2209_11606_gb300 import predictor as P, workloads as W
+    t0 = time.perf_counter()
+    rows = []
+    for name in ("uniform1m", "bcc1m"):
+        s = W.workload(name)
+        rows.append(P.rows_for_system(s, torch, s.meta["grid"]))
+    X = torch.cat([r[0] for r in rows])
+    t = torch.cat([r[1] for r in rows])
+    params, losses = P.train(X, t, torch, seed=0, steps=1500, lr=3e-3, u=4.0)
+    meta = {"trained_on": "k* labels of uniform1m and bcc1m (FP32 form)", "rows": int(X.shape[0]),
+            "steps": 1500, "lr": 3e-3, "u": 4.0, "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+            "seconds": time.perf_counter() - t0}
+    try:
+        with open(MLP_PARAMS, "w") as f:
+            json.dump({"meta": meta, "params": [float(x) for x in params]}, f)
+    except OSError:
+        pass
+    return params, meta
+
+
+def graph_steps(V, torch, ctx, stream, flush, steps):
+    """Times `steps` graph replays, L2 flushed before each; returns per-step ms."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.fill_(k & 0xff)
+        evs[k][0].record(stream)
+        V.vg_graph_launch(ctx)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    V.vg_graph_sync(ctx)
+    return [a.elapsed_time(b) for a, b in evs]
+
+
 def batched_run(V, torch, stream, flush, steps: int = 5, seed: int = 5):
     """The 256-system batched workload: one container, one graph replay per
-    step (one sort over all systems' blocks, one persistent cell launch)."""
-    from paper_2209_11606_gb300 import workloads as W
+    step (one sort over all systems' blocks, one persistent cell launch),
+    with N_opt per distribution class and the launch parameters from the
+    autotuner (cached per class)."""
+    from paper_2209_11606_gb300 import autotune as A, workloads as W
     systems = W.batched_systems(256, 1000, 200_000, seed=seed)
-    descs = [V.vg_system(x.lo, x.hi, x.periodic) for x in systems]
+    t0 = time.perf_counter()
+    cache = A.Cache(TUNE_CACHE)
+    key = "batched256-seed%d" % seed
+    tb = cache.get(key)
+    if tb is None:
+        tb = A.tune_batch(systems, torch, cache)
+        tb = {"n_opt": tb["n_opt"], "launch": tb["launch"], "classes": tb["classes"]}
+        cache.put(key, tb)
+    tune_s = time.perf_counter() - t0
+    descs = [V.vg_system(x.lo, x.hi, x.periodic, n_opt=v) for x, v in zip(systems, tb["n_opt"])]
     counts = [x.n for x in systems]
     pos = torch.from_numpy(np.concatenate([x.pos for x in systems])).cuda()
     ctx = V.vg_batch_create(3, descs, stream=stream)
     try:
-        cfg = V.vg_config_default()
+        cfg = A.config_from(tb["launch"])
         V.vg_graph_capture(ctx, counts, pos, None, cfg)
         for _ in range(3):
             V.vg_graph_launch(ctx)
         V.vg_graph_sync(ctx)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(steps)]
-        torch.cuda.synchronize()
-        for k in range(steps):
-            flush.fill_(k & 0xff)
-            evs[k][0].record(stream)
-            V.vg_graph_launch(ctx)
-            evs[k][1].record(stream)
-        torch.cuda.synchronize()
-        V.vg_graph_sync(ctx)
-        ms = [a.elapsed_time(b) for a, b in evs]
+        ms = graph_steps(V, torch, ctx, stream, flush, steps)
         n = int(sum(counts))
-        kinds = {}
+        mix = {}
         for x in systems:
-            kinds[x.tag] = kinds.get(x.tag, 0) + 1
+            mix[x.tag] = mix.get(x.tag, 0) + 1
+        per_class = {}
+        for c, v in zip(tb["classes"], tb["n_opt"]):
+            per_class[c] = v
         return {"value": n * steps / (sum(ms) / 1000.0), "unit": "cells/s", "steps": steps,
                 "ms_per_step": sum(ms) / steps, "cells_per_step": n, "systems": len(systems),
-                "mix": kinds, "form": "FP32 cuts + FP64 re-test, sorted prefetch, one graph replay",
+                "mix": mix, "n_opt_by_class": per_class,
+                "launch": {k: tb["launch"][k] for k in ("order", "warps_per_cta", "chunk")},
+                "tuning_seconds": tune_s,
+                "form": "FP32 cuts + FP64 re-test, autotuned N_opt and launch, one graph replay",
                 "workload": "256 3D systems, sizes log-uniform in [1000, 200000], uniform / perturbed "
                             "FCC (sigma 0.05 a) / 50 Gaussian blobs (sigma 0.02 side), random "
                             f"periodicity (seed {seed})"}
@@ -152,19 +216,20 @@ def batched_run(V, torch, stream, flush, steps: int = 5, seed: int = 5):
         V.vg_destroy(ctx)
 
 
-def cpu_baseline(s, cells: int, seed: int = 0):
+def cpu_baseline(s, grid, cells: int, seed: int = 0):
     """Times the FP64 oracle on a sample of `cells` cells of system s."""
     import oracle
     rng = np.random.default_rng(seed)
     sample = np.sort(rng.choice(s.n, size=min(cells, s.n), replace=False))
     oracle.build()
     threads = os.cpu_count() or 1
+    if grid is None:
+        grid = oracle.grid_size(s.n, s.lo, s.hi, 4.6)
     t0 = time.perf_counter()
-    oracle.compute(s.pos, s.lo, s.hi, s.periodic, method="grid", nblocks=GRID, cells=sample,
-                   threads=threads)
+    oracle.compute(s.pos, s.lo, s.hi, s.periodic, method="grid", nblocks=grid, cells=sample, threads=threads)
     dt = time.perf_counter() - t0
     return {"value": len(sample) / dt, "unit": "cells/s", "cores": threads, "kind": "oracle",
-            "sample": f"{len(sample)} random cells of the 1M-point workload (FP64 block-grid "
+            "sample": f"{len(sample)} random cells of the {s.n}-point workload (FP64 block-grid "
                       f"walk with the radius bound, OpenMP dynamic over cells)",
             "seconds": dt}
 
@@ -172,14 +237,14 @@ def cpu_baseline(s, cells: int, seed: int = 0):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    s = workload(0)
+    s, grid = workload(args.workload, 0)
     per_step = 100_000
     for _ in range(args.warmup):
-        cpu_baseline(s, 20_000, seed=99)
+        cpu_baseline(s, grid, 20_000, seed=99)
     total, cells = 0.0, 0
     res = None
     for k in range(args.steps):
-        res = cpu_baseline(s, per_step, seed=k)
+        res = cpu_baseline(s, grid, per_step, seed=k)
         total += res["seconds"]
         cells += per_step
     v = cells / total
@@ -187,10 +252,9 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD.replace("chosen form = FP32 cuts + FP64 re-test, sorted prefetch",
-                                                    "FP64 CPU oracle")},
+            "config": {"workload": WORKLOADS[args.workload].split(";")[0] + "; FP64 CPU oracle"},
             "cpu_baseline": {"value": v, "unit": "cells/s", "kind": "oracle", "cores": res["cores"],
-                             "sample": f"{per_step} random cells per step of the 1M-point workload"},
+                             "sample": f"{per_step} random cells per step of the {s.n}-point workload"},
             "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -215,29 +279,30 @@ def main():
 
     from paper_2209_11606_gb300 import build as B
     B.build()
-    from paper_2209_11606_gb300 import vorogpu as V
+    from paper_2209_11606_gb300 import predictor as P, vorogpu as V
 
-    s = workload(rank)
+    big = args.workload == "slabs102m"
+    s, grid = workload(args.workload, rank)
     n = s.n
     stream = torch.cuda.current_stream()
     pos_d = torch.from_numpy(s.pos).cuda()
-    ctx = V.vg_create(3, s.lo, s.hi, s.periodic, GRID, stream=stream)
-    cfg = V.vg_config_default()
-    cfg.precision = V.VG_FP32_RETEST
-    cfg.order = V.VG_PREFETCH
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    params, mlp_meta = mlp_params(V, torch)
+    mlp = P.predictor(params)
+    ctx = V.vg_create(3, s.lo, s.hi, s.periodic, grid, stream=stream)
+    V.vg_set_predictor(ctx, mlp, MLP_ALPHA, MLP_KMIN, MLP_KMAX)
+    cfg = V.vg_config_default()
+    cfg.precision, cfg.order, cfg.use_mlp = V.VG_FP32_RETEST, V.VG_PREFETCH, 1
 
-    def step():
+    # warm-up through the eager calls, then the step as one graph: sort ->
+    # learned preload targets -> cells -> faces, the cell kernels timed by
+    # event nodes inside the graph
+    for _ in range(max(args.warmup, 3)):
         V.vg_insert(ctx, pos_d)
         V.vg_compute(ctx, cfg)
-
-    for _ in range(max(args.warmup, 3)):
-        step()
     torch.cuda.synchronize()
-    # the step as one graph: sort -> cells -> faces, cell kernels timed by
-    # event nodes inside the graph
     gcfg = V.vg_config_default()
-    gcfg.precision, gcfg.order, gcfg.time_kernels = cfg.precision, cfg.order, 1
+    gcfg.precision, gcfg.order, gcfg.use_mlp, gcfg.time_kernels = cfg.precision, cfg.order, 1, 1
     V.vg_graph_capture(ctx, [n], pos_d, None, gcfg)
     for _ in range(max(args.warmup, 3)):
         V.vg_graph_launch(ctx)
@@ -246,24 +311,15 @@ def main():
     # ---- timed region: K steps, L2 flushed between them ----------------------
     V.vg_get_kernel_ms(ctx)  # reset
     l0 = V.vg_get_launches(ctx)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     time.sleep(0.3)
-    for k in range(args.steps):
-        flush.fill_(k & 0xff)
-        evs[k][0].record(stream)
-        V.vg_graph_launch(ctx)
-        evs[k][1].record(stream)
-    torch.cuda.synchronize()
+    step_ms = graph_steps(V, torch, ctx, stream, flush, args.steps)
     clk = clocks.stop()
-    V.vg_graph_sync(ctx)  # input flags and face capacity of the replays
     launches = V.vg_get_launches(ctx) - l0
-    step_ms = [a.elapsed_time(b) for a, b in evs]
     kern_ms, kern_n = V.vg_get_kernel_ms(ctx)
     t_total = sum(step_ms) / 1000.0
     if dist:
@@ -275,21 +331,26 @@ def main():
 
     if rank != 0:
         V.vg_destroy(ctx)
+        V.vg_mlp_destroy(mlp)
         if dist:
             dist.destroy_process_group()
         return
 
     # ---- work counters -> algorithmic FLOPs of the cell kernels ----------------
-    cfg.collect_stats = 1
-    step()
-    cfg.collect_stats = 0
-    w = {k: np.zeros(n, np.int32) for k in ("t", "v", "c", "nv", "r")}
-    fb = np.zeros(n, np.uint8)
-    V.vg_get_work(ctx, w["t"], w["v"], w["c"], w["nv"], w["r"], fb)
+    def work(c):
+        c.collect_stats = 1
+        V.vg_insert(ctx, pos_d)
+        V.vg_compute(ctx, c)
+        c.collect_stats = 0
+        w = {k: np.zeros(n, np.int32) for k in ("t", "v", "c", "nv", "r", "p")}
+        fb = np.zeros(n, np.uint8)
+        V.vg_get_work(ctx, w["t"], w["v"], w["c"], w["nv"], w["r"], fb, w["p"])
+        return w, fb
+
+    w, fb = work(cfg)
     ne = np.zeros(n, np.int32)
     nf = np.zeros(n, np.int32)
-    st = np.zeros(n, np.uint8)
-    V.vg_get_cells(ctx, ne=ne, nf=nf, status=st)
+    V.vg_get_cells(ctx, ne=ne, nf=nf)
     fan = 2 * ne.astype(np.int64) - 2 * nf.astype(np.int64)
     flop = (FLOP_VTEST * w["v"].astype(np.int64).sum() + FLOP_CAND * w["t"].astype(np.int64).sum() +
             FLOP_NEWV * w["nv"].astype(np.int64).sum() + FLOP_FANTET * fan.sum())
@@ -297,47 +358,49 @@ def main():
     achieved = flop / (kern_avg_ms / 1000.0) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-            "kernel": "k_cells3<float> (cell kernel phase)", "kernel_ms": kern_avg_ms,
+            "kernel": "k_cells3<float,2,64> (cell kernel phase, all tiers)", "kernel_ms": kern_avg_ms,
             "flop_per_cell": flop / n,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    c_fixed = V.vg_config_default()
+    w_fixed, fb_fixed = work(c_fixed)
+    learned = {"fallback_rate": float(fb.mean()), "preload_per_cell": float(w["p"].mean()),
+               "fixed_k_fallback_rate": float(fb_fixed.mean()),
+               "fixed_k_preload_per_cell": float(w_fixed["p"].mean()),
+               "alpha": MLP_ALPHA, "trained": mlp_meta}
 
-    # ---- the plain FP64 form on the same input (the metric's comparison) -------
-    cfg64 = V.vg_config_default()
-    cfg64.precision = V.VG_FP64
-    cfg64.order = V.VG_WALK
-    V.vg_insert(ctx, pos_d)
-    V.vg_compute(ctx, cfg64)
-    torch.cuda.synchronize()
-    reps = 3
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    tot64 = 0.0
-    for k in range(reps):
-        flush.fill_(k)
-        e0.record(stream)
-        V.vg_insert(ctx, pos_d)
-        V.vg_compute(ctx, cfg64)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        tot64 += e0.elapsed_time(e1) / 1000.0
-    plain64 = n * reps / tot64
+    # ---- the same step in other forms (graph replays) ---------------------------
+    def form_rate(order, use_mlp, precision=V.VG_FP32_RETEST, reps=5):
+        c2 = V.vg_config_default()
+        c2.precision, c2.order, c2.use_mlp = precision, order, use_mlp
+        V.vg_graph_capture(ctx, [n], pos_d, None, c2)
+        V.vg_graph_launch(ctx)
+        V.vg_graph_sync(ctx)
+        ms = graph_steps(V, torch, ctx, stream, flush, reps)
+        return n * reps / (sum(ms) / 1000.0)
+
+    forms = {"fp32_prefetch_fixed_k72": form_rate(V.VG_PREFETCH, 0),
+             "fp32_walk": form_rate(V.VG_WALK, 0)}
+    plain64 = form_rate(V.VG_WALK, 0, V.VG_FP64, reps=1 if big else 3)
 
     # ---- end to end through the public API, host buffers -----------------------
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not big:
         pos_h = torch.from_numpy(s.pos).pin_memory().numpy()
         outs = {"vol": np.float64, "area": np.float64, "nv": np.int32, "ne": np.int32,
                 "nf": np.int32, "status": np.uint8}
         host = {k: torch.empty(n, dtype=getattr(torch, np.dtype(t).name)).pin_memory().numpy()
                 for k, t in outs.items()}
         cen = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+        V.vg_insert(ctx, pos_d)
+        V.vg_compute(ctx, cfg)
         _, nface = V.vg_get_counts(ctx)
         fo = torch.empty(n + 1, dtype=torch.int64).pin_memory().numpy()
         cap = int(nface * 1.2) + 1024
         ids = torch.empty(cap, dtype=torch.int32).pin_memory().numpy()
         img = torch.empty((cap, 3), dtype=torch.int8).pin_memory().numpy()
         fod = torch.empty(cap, dtype=torch.uint8).pin_memory().numpy()
-        d2h = 0
         reps = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(reps):
             V.vg_insert(ctx, pos_h)
@@ -354,20 +417,25 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells_per_step": n * world,
+            "config": {"workload": WORKLOADS[args.workload], "cells_per_step": n * world,
                        "l2": "flushed between steps (256 MB write outside the timed events)",
                        "parallelism": f"replicas{world}"},
+            "step": "one CUDA graph replay: counting sort, learned preload targets, cell kernels "
+                    "(3 capacity tiers), face CSR",
             "roofline": roof,
-            "step": "one CUDA graph replay: counting sort, cell kernels (3 capacity tiers), face CSR",
             "plain_fp64": {"value": plain64, "unit": "cells/s",
-                           "form": "FP64 everywhere, block walk (Sec. 2.1.3)"},
+                           "form": "FP64 everywhere, block walk (Sec. 2.1.3), graph replay"},
+            "chosen_vs_plain": value / world / plain64,
+            "forms": forms, "learned_preload": learned,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-            "fallback_rate": float(fb.mean()), "retest_per_cell": float(w["r"].mean())}
-    if not args.no_batched:
+            "retest_per_cell": float(w["r"].mean())}
+    if not args.no_batched and not big:
         line["batched"] = batched_run(V, torch, stream, flush)
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(s, 100_000).items() if k != "seconds"}
+        line["cpu_baseline"] = {k: v for k, v in
+                                cpu_baseline(s, grid, 100_000 if big else n).items() if k != "seconds"}
     V.vg_destroy(ctx)
+    V.vg_mlp_destroy(mlp)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -366,6 +366,16 @@ vg_status vg_mlp_infer(vg_mlp *mlp, const float *X, int64_t M, float *y);
 vg_status vg_mlp_predict(vg_ctx *ctx, vg_mlp *mlp, float alpha, float kmin, float kmax);
 
 /*
+ * Attaches a predictor to a container (NULL detaches): every later sort
+ * (vg_insert, vg_batch_insert, graph replays) is followed by the prediction
+ * of vg_mlp_predict(), so use_mlp = 1 needs no separate call and a captured
+ * graph runs sort -> predict -> cells -> faces.  The container does not own
+ * the predictor, which must outlive its use; attach again after training it
+ * further.
+ */
+vg_status vg_set_predictor(vg_ctx *ctx, vg_mlp *mlp, float alpha, float kmin, float kmax);
+
+/*
  * Counting sort into blocks that allocates no device memory.  The paper has
  * no counterpart: it is a variant of the sort inside vg_insert() for callers
  * that must not allocate at call time -- for example a plugin whose host

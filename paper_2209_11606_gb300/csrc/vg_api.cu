@@ -281,6 +281,15 @@ vg_status prepare_insert(vg_ctx *c, const std::vector<long long> &counts, const 
         if (radii) VG_CUDA(ensure(c, c->d_rad, n));
     }
     VG_CUDA(ensure(c, c->d_count, c->total_blk));
+    if (c->pred) {
+        if (!c->d_kblock || c->cap_kblock < c->total_blk) {
+            if (c->d_kblock) cudaFree(c->d_kblock);
+            c->d_kblock = nullptr;
+            c->cap_kblock = 0;
+            VG_CUDA(cudaMalloc((void **)&c->d_kblock, sizeof(float) * std::max<long long>(1, c->total_blk)));
+            c->cap_kblock = c->total_blk;
+        }
+    }
     VG_CUDA(ensure(c, c->d_bstart, c->total_blk + 1));
     const size_t need_scan = std::max(scan_tmp_bytes_i32(c->total_blk + 1),
                                       (((size_t)n * sizeof(int) + 255) & ~(size_t)255) + scan_tmp_bytes_i64(n + 1));
@@ -317,6 +326,10 @@ cudaError_t enqueue_sort(vg_ctx *c, const double *dpos, const double *drad, cuda
         e = sort_particles(c->d_sys, nsys, c->dim, c->total_blk, c->n, dpos, drad, c->d_key, c->d_slot, c->d_count,
                            c->d_bstart, c->d_tmp, c->d_p32, c->d_p64, c->d_sid, c->d_sblk, c->d_ssys, c->d_err,
                            c->d_scan, s);
+    // the learned preload targets follow the block counts
+    if (e == cudaSuccess && c->pred)
+        e = launch_predict(mlp_weights(c->pred), c->d_sys, nsys, c->d_bstart, c->total_blk, c->pred_alpha,
+                           c->pred_kmin, c->pred_kmax, c->d_kblock, s);
     return e;
 }
 
@@ -343,6 +356,7 @@ vg_status insert_all(vg_ctx *c, const std::vector<long long> &counts, const doub
     if (e != cudaSuccess) return cuda_fail(c, e, "sort_particles");
     if ((s = read_input_flags(c)) != VG_OK) return s;
     c->inserted = 1;
+    if (c->pred) c->kblock_valid = 1;
     return VG_OK;
 }
 
@@ -736,6 +750,7 @@ vg_status vg_graph_launch(vg_ctx *c) {
     c->computed = 1;
     c->subset = 0;
     c->graph_unchecked = 1;
+    if (c->pred) c->kblock_valid = 1;
     return VG_OK;
 }
 

@@ -130,6 +130,11 @@ cudaError_t launch_cells2(const Store &s, const Out &o, const Params &p, const O
                           int precision, unsigned *ticket, int sm_count, int warps_per_cta,
                           const int *cells, int ncells, int tier, cudaStream_t st);
 
+// Per-block preload targets from the predictor's FP16 weights (vg_mlp.cu).
+cudaError_t launch_predict(const void *weights, const Sys *sys, int nsys, const int *bstart, long long nblk,
+                           float alpha, float kmin, float kmax, float *kblock, cudaStream_t st);
+const void *mlp_weights(const vg_mlp *m);
+
 // Sorted positions of the input indices cells[0..m) (via the inverse of
 // sid); out-of-range indices are counted in *bad and mapped to 0.
 cudaError_t map_cells(const int *sid, long long n, const int *cells, long long m, int *rank, int *out, int *bad,
@@ -227,6 +232,8 @@ struct vg_ctx {
     vg_config g_cfg{};
 
     // learned preload targets, one per block (valid until the next insert)
+    vg_mlp *pred = nullptr;   // predictor run after every sort (vg_set_predictor)
+    float pred_alpha = 1.f, pred_kmin = 8.f, pred_kmax = 1024.f;
     float *d_kblock = nullptr;
     long long cap_kblock = 0;
     int kblock_valid = 0;

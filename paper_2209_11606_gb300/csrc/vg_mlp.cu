@@ -373,6 +373,18 @@ __global__ void k_predict(const MlpInf *__restrict__ W, const Sys *sys, int nsys
 unsigned nblocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
+
+cudaError_t launch_predict(const void *weights, const Sys *sys, int nsys, const int *bstart, long long nblk,
+                           float alpha, float kmin, float kmax, float *kblock, cudaStream_t st) {
+    if (nblk <= 0) return cudaSuccess;
+    ++g_launch_count;
+    k_predict<<<nblocks_for(nblk, 128), 128, 0, st>>>((const MlpInf *)weights, sys, nsys, bstart, nblk, alpha, kmin,
+                                                      kmax, kblock);
+    return cudaGetLastError();
+}
+
+const void *mlp_weights(const vg_mlp *m);
+
 }  // namespace vg
 
 using namespace vg;
@@ -386,6 +398,8 @@ struct vg_mlp {
     long long step = 0;
     std::string err;
 };
+
+const void *vg::mlp_weights(const vg_mlp *m) { return m ? (const void *)m->d_inf : nullptr; }
 
 namespace {
 
@@ -700,12 +714,22 @@ vg_status vg_mlp_predict(vg_ctx *c, vg_mlp *m, float alpha, float kmin, float km
     C_CUDA(grow(c->d_kblock, c->cap_kblock, B));
     // the predictor's weights are written on its own stream
     C_CUDA(cudaStreamSynchronize(m->stream));
-    ++g_launch_count;
-    k_predict<<<nblocks_for(B, 128), 128, 0, c->stream>>>(m->d_inf, c->d_sys, (int)c->sys.size(), c->d_bstart, B,
-                                                          alpha, kmin, kmax, c->d_kblock);
-    C_CUDA(cudaGetLastError());
+    C_CUDA(launch_predict(m->d_inf, c->d_sys, (int)c->sys.size(), c->d_bstart, B, alpha, kmin, kmax, c->d_kblock,
+                          c->stream));
     c->launches += 1;
     c->kblock_valid = 1;
+    return VG_OK;
+}
+
+vg_status vg_set_predictor(vg_ctx *c, vg_mlp *m, float alpha, float kmin, float kmax) {
+    if (!c) return VG_ERR_ARG;
+    if (m && (!(alpha > 0.f) || !(kmin > 0.f) || !(kmax >= kmin))) return cfail(c, VG_ERR_ARG, "alpha, kmin, kmax");
+    // the predictor's weights are written on its own stream
+    if (m) C_CUDA(cudaStreamSynchronize(m->stream));
+    c->pred = m;
+    c->pred_alpha = alpha;
+    c->pred_kmin = kmin;
+    c->pred_kmax = kmax;
     return VG_OK;
 }
 

@@ -31,7 +31,7 @@ EXPORTS = ["vg_config_default", "vg_create", "vg_batch_create", "vg_insert", "vg
            "vg_sort_blocks_noalloc", "vg_last_error", "vg_destroy",
            "vg_mlp_create", "vg_mlp_destroy", "vg_mlp_last_error", "vg_mlp_set_params",
            "vg_mlp_get_params", "vg_mlp_features", "vg_mlp_labels", "vg_mlp_dataset",
-           "vg_mlp_loss_grad", "vg_mlp_train", "vg_mlp_infer", "vg_mlp_predict"]
+           "vg_mlp_loss_grad", "vg_mlp_train", "vg_mlp_infer", "vg_mlp_predict", "vg_set_predictor"]
 MLP_NPARAM = 1985
 
 
@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH):
         "vg_mlp_train": (I, [P, P, P, L, ctypes.c_float, ctypes.c_float, I, P]),
         "vg_mlp_infer": (I, [P, P, L, P]),
         "vg_mlp_predict": (I, [P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+        "vg_set_predictor": (I, [P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
         "vg_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -424,6 +425,10 @@ def vg_mlp_infer(m, X, M, y):
 
 def vg_mlp_predict(ctx, m, alpha=1.0, kmin=8.0, kmax=1024.0):
     _check(ctx, load().vg_mlp_predict(ctx, m, float(alpha), float(kmin), float(kmax)))
+
+
+def vg_set_predictor(ctx, m, alpha=1.0, kmin=8.0, kmax=1024.0):
+    _check(ctx, load().vg_set_predictor(ctx, m, float(alpha), float(kmin), float(kmax)))
 
 
 # ---- convenience: one call from host arrays to host results -------------------

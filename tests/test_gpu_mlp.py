@@ -247,3 +247,37 @@ def test_use_mlp_needs_a_prediction_after_insert():
     finally:
         v.vg_mlp_destroy(m)
         v.vg_destroy(ctx)
+
+
+def test_attached_predictor_runs_inside_the_graph():
+    import torch
+    v = V()
+    s = W.uniform(20000, 3, 20000 ** (1 / 3), True, seed=107)
+    nb = (15, 15, 15)
+    ctx = v.vg_create(3, s.lo, s.hi, s.periodic, nb)
+    m = v.vg_mlp_create()
+    try:
+        v.vg_mlp_set_params(m, OM.init_params(15).astype(np.float32))
+        pos = torch.from_numpy(s.pos).cuda()
+        # eager: explicit prediction after the insert
+        v.vg_insert(ctx, pos)
+        v.vg_mlp_predict(ctx, m, 1.3, 8.0, 512.0)
+        cfg = v.vg_config_default()
+        cfg.use_mlp = 1
+        cfg.collect_stats = 1
+        v.vg_compute(ctx, cfg)
+        eager = v._fetch(ctx, s.n, 3, True)
+        # attached: the graph runs sort -> predict -> cells -> faces
+        v.vg_set_predictor(ctx, m, 1.3, 8.0, 512.0)
+        v.vg_graph_capture(ctx, [s.n], pos, None, cfg)
+        v.vg_graph_launch(ctx)
+        got = v._fetch(ctx, s.n, 3, True)
+        assert np.array_equal(got["work"]["n_prefetch"], eager["work"]["n_prefetch"])
+        for k in ("vol", "area", "nf", "nbr_id", "face_off"):
+            assert np.array_equal(got[k], eager[k]), k
+        ref = oracle.compute(s.pos, s.lo, s.hi, s.periodic, nblocks=nb)
+        rep = compare(got, ref, 1e-5)
+        assert rep["topology_ok"] and rep["values_ok"], rep
+    finally:
+        v.vg_destroy(ctx)
+        v.vg_mlp_destroy(m)
