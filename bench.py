@@ -51,6 +51,10 @@ WORKLOADS = {
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # algorithmic FLOP counts per unit of work (see the design notes)
 FLOP_VTEST, FLOP_CAND, FLOP_NEWV, FLOP_FANTET = 6, 12, 51, 42
+# DRAM bytes (read + write) of one k_cells3<float,2,64> launch over the 1M
+# uniform cells, from the ncu capture summarised in
+# profiles/k_cells3_fp32_uniform1m_ncu.md (null for other workloads)
+CELL_KERNEL_DRAM_BYTES_UNIFORM1M = 149.632e6 + 261.173e6
 MLP_ALPHA, MLP_KMIN, MLP_KMAX = 1.2, 8.0, 1024.0
 PKG = os.path.join(ROOT, "paper_2209_11606_gb300")
 MLP_PARAMS = os.path.join(PKG, "mlp_params_gb300.json")
@@ -357,7 +361,9 @@ def main():
     kern_avg_ms = kern_ms / max(kern_n, 1)
     achieved = flop / (kern_avg_ms / 1000.0) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+            "frac": achieved / FP32_PEAK_TFLOPS,
+            "traffic": None if big else CELL_KERNEL_DRAM_BYTES_UNIFORM1M,
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
             "kernel": "k_cells3<float,2,64> (cell kernel phase, all tiers)", "kernel_ms": kern_avg_ms,
             "flop_per_cell": flop / n,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
