@@ -11,14 +11,15 @@ the CSR compaction of the faces.  L2 is flushed between steps (a 256 MB write
 outside the timed events).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload uniform1m|slabs102m]
+                    [--workload uniform1m|slabs102m|radical2m|hex10m]
 
 With N > 1 (torchrun, one rank per GPU) every rank processes its own system
 (weak scaling, no collective on the data path); value is the cells of all
 ranks over the slowest rank's time.
 
---workload slabs102m runs the 102.4M-point periodic cube of alternating
-perturbed-FCC and uniform slabs instead (no e2e, no batched line).
+--workload selects another configuration (no e2e and no batched line there):
+slabs102m, the 102.4M-point periodic cube of alternating perturbed-FCC and
+uniform slabs; radical2m, 2M radical (power) cells; hex10m, 10M 2D cells.
 
 --impl reference times the FP64 CPU oracle (block-grid walk with the radius
 bound, OpenMP over cells) on this host's cores, on a bounded sample of the
@@ -45,7 +46,14 @@ WORKLOADS = {
     "slabs102m": ("slabs102m: 102,400,000 points in a periodic cube of side 296 a (a = 51/32), 8 z-slabs "
                   "alternating perturbed FCC (sigma 0.05 a) and uniform points (seed 6), blocks by the "
                   "n_opt = 4.6 rule; chosen form = FP32 cuts + FP64 re-test, learned distance-sorted preload"),
+    "radical2m": ("radical2m: 2,000,000 points uniform in a periodic cube (unit density, seed 4), radii "
+                  "log-normal (sigma 0.3) scaled to packing fraction 0.4, blocks by the n_opt = 4.6 rule; "
+                  "chosen form = FP32 cuts + FP64 re-test, distance-sorted preload (fixed target 72)"),
+    "hex10m": ("hex10m: 2D, 10,000,314 points of a perturbed hexagonal lattice (2943 x 3398, sigma 0.05 of the "
+               "column spacing, seed 3) in the periodic unit square, blocks by the n_opt = 3.4 rule; "
+               "chosen form = FP32 cuts + FP64 re-test, block walk"),
 }
+METRIC_2D = "2D Voronoi cells/s, 1 GB300, chosen vs plain FP64 form; % of roofline"
 # FP32 peak derived from unit counts and clock: 152 SMs x 128 FP32 lanes x
 # 2 FLOP (FMA) x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -55,7 +63,7 @@ FLOP_VTEST, FLOP_CAND, FLOP_NEWV, FLOP_FANTET = 6, 12, 51, 42
 # uniform cells, from the ncu capture summarised in
 # profiles/k_cells3_fp32_uniform1m_ncu.md (null for other workloads)
 CELL_KERNEL_DRAM_BYTES_UNIFORM1M = 149.632e6 + 261.173e6
-MLP_ALPHA, MLP_KMIN, MLP_KMAX = 1.2, 8.0, 1024.0
+MLP_ALPHA, MLP_KMIN, MLP_KMAX = 1.5, 24.0, 1024.0
 PKG = os.path.join(ROOT, "paper_2209_11606_gb300")
 MLP_PARAMS = os.path.join(PKG, "mlp_params_gb300.json")
 TUNE_CACHE = os.path.join(PKG, "tuned_gb300.json")
@@ -75,12 +83,16 @@ def parse():
 
 
 def workload(name: str, rank: int):
+    """(system, block grid or None for the n_opt rule, chosen order, learned preload)."""
     from paper_2209_11606_gb300 import workloads as W
     if name == "uniform1m":
-        s = W.uniform(1_000_000, 3, 100.0, True, seed=1 + rank)
-        return s, (58, 58, 58)
-    s = W.fcc_uniform_slabs(seed=6 + rank)
-    return s, None
+        return W.uniform(1_000_000, 3, 100.0, True, seed=1 + rank), (58, 58, 58), "prefetch", True
+    if name == "slabs102m":
+        return W.fcc_uniform_slabs(seed=6 + rank), None, "prefetch", True
+    if name == "radical2m":
+        return W.radical_uniform(2_000_000, 0.4, 0.3, seed=4 + rank), None, "prefetch", False
+    s = W.hexagonal(2943, 3398, (1.0, 1.0), 0.05, seed=3 + rank)
+    return s, None, "walk", False
 
 
 class Clocks:
@@ -228,9 +240,10 @@ def cpu_baseline(s, grid, cells: int, seed: int = 0):
     oracle.build()
     threads = os.cpu_count() or 1
     if grid is None:
-        grid = oracle.grid_size(s.n, s.lo, s.hi, 4.6)
+        grid = oracle.grid_size(s.n, s.lo, s.hi, 4.6 if s.dim == 3 else 3.4)
     t0 = time.perf_counter()
-    oracle.compute(s.pos, s.lo, s.hi, s.periodic, method="grid", nblocks=grid, cells=sample, threads=threads)
+    oracle.compute(s.pos, s.lo, s.hi, s.periodic, radii=s.radii, method="grid", nblocks=grid, cells=sample,
+                   threads=threads)
     dt = time.perf_counter() - t0
     return {"value": len(sample) / dt, "unit": "cells/s", "cores": threads, "kind": "oracle",
             "sample": f"{len(sample)} random cells of the {s.n}-point workload (FP64 block-grid "
@@ -241,7 +254,7 @@ def cpu_baseline(s, grid, cells: int, seed: int = 0):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    s, grid = workload(args.workload, 0)
+    s, grid, _, _ = workload(args.workload, 0)
     per_step = 100_000
     for _ in range(args.warmup):
         cpu_baseline(s, grid, 20_000, seed=99)
@@ -252,9 +265,9 @@ def run_reference(args, rank, world):
         total += res["seconds"]
         cells += per_step
     v = cells / total
-    line = {"metric": METRIC, "value": v, "unit": "cells/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+    line = {"metric": METRIC if s.dim == 3 else METRIC_2D, "value": v, "unit": "cells/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": WORKLOADS[args.workload].split(";")[0] + "; FP64 CPU oracle"},
             "cpu_baseline": {"value": v, "unit": "cells/s", "kind": "oracle", "cores": res["cores"],
@@ -286,28 +299,31 @@ def main():
     from paper_2209_11606_gb300 import predictor as P, vorogpu as V
 
     big = args.workload == "slabs102m"
-    s, grid = workload(args.workload, rank)
-    n = s.n
+    s, grid, chosen_order, learned_on = workload(args.workload, rank)
+    n, dim = s.n, s.dim
+    order_code = V.VG_PREFETCH if chosen_order == "prefetch" else V.VG_WALK
     stream = torch.cuda.current_stream()
     pos_d = torch.from_numpy(s.pos).cuda()
+    rad_d = None if s.radii is None else torch.from_numpy(s.radii).cuda()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     params, mlp_meta = mlp_params(V, torch)
     mlp = P.predictor(params)
-    ctx = V.vg_create(3, s.lo, s.hi, s.periodic, grid, stream=stream)
-    V.vg_set_predictor(ctx, mlp, MLP_ALPHA, MLP_KMIN, MLP_KMAX)
+    ctx = V.vg_create(dim, s.lo, s.hi, s.periodic, grid, stream=stream)
+    if learned_on:
+        V.vg_set_predictor(ctx, mlp, MLP_ALPHA, MLP_KMIN, MLP_KMAX)
     cfg = V.vg_config_default()
-    cfg.precision, cfg.order, cfg.use_mlp = V.VG_FP32_RETEST, V.VG_PREFETCH, 1
+    cfg.precision, cfg.order, cfg.use_mlp = V.VG_FP32_RETEST, order_code, int(learned_on)
 
     # warm-up through the eager calls, then the step as one graph: sort ->
     # learned preload targets -> cells -> faces, the cell kernels timed by
     # event nodes inside the graph
     for _ in range(max(args.warmup, 3)):
-        V.vg_insert(ctx, pos_d)
+        V.vg_insert(ctx, pos_d, rad_d)
         V.vg_compute(ctx, cfg)
     torch.cuda.synchronize()
     gcfg = V.vg_config_default()
-    gcfg.precision, gcfg.order, gcfg.use_mlp, gcfg.time_kernels = cfg.precision, cfg.order, 1, 1
-    V.vg_graph_capture(ctx, [n], pos_d, None, gcfg)
+    gcfg.precision, gcfg.order, gcfg.use_mlp, gcfg.time_kernels = cfg.precision, cfg.order, cfg.use_mlp, 1
+    V.vg_graph_capture(ctx, [n], pos_d, rad_d, gcfg)
     for _ in range(max(args.warmup, 3)):
         V.vg_graph_launch(ctx)
     V.vg_graph_sync(ctx)
@@ -343,7 +359,7 @@ def main():
     # ---- work counters -> algorithmic FLOPs of the cell kernels ----------------
     def work(c):
         c.collect_stats = 1
-        V.vg_insert(ctx, pos_d)
+        V.vg_insert(ctx, pos_d, rad_d)
         V.vg_compute(ctx, c)
         c.collect_stats = 0
         w = {k: np.zeros(n, np.int32) for k in ("t", "v", "c", "nv", "r", "p")}
@@ -355,49 +371,58 @@ def main():
     ne = np.zeros(n, np.int32)
     nf = np.zeros(n, np.int32)
     V.vg_get_cells(ctx, ne=ne, nf=nf)
-    fan = 2 * ne.astype(np.int64) - 2 * nf.astype(np.int64)
-    flop = (FLOP_VTEST * w["v"].astype(np.int64).sum() + FLOP_CAND * w["t"].astype(np.int64).sum() +
-            FLOP_NEWV * w["nv"].astype(np.int64).sum() + FLOP_FANTET * fan.sum())
+    if dim == 3:
+        fan = 2 * ne.astype(np.int64) - 2 * nf.astype(np.int64)
+        flop = (FLOP_VTEST * w["v"].astype(np.int64).sum() + FLOP_CAND * w["t"].astype(np.int64).sum() +
+                FLOP_NEWV * w["nv"].astype(np.int64).sum() + FLOP_FANTET * fan.sum())
+    else:
+        # 2D: 4 per vertex test, 8 per candidate, 12 per new vertex, 6 per shoelace term
+        flop = (4 * w["v"].astype(np.int64).sum() + 8 * w["t"].astype(np.int64).sum() +
+                12 * w["nv"].astype(np.int64).sum() + 6 * ne.astype(np.int64).sum())
     kern_avg_ms = kern_ms / max(kern_n, 1)
     achieved = flop / (kern_avg_ms / 1000.0) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP32_PEAK_TFLOPS,
-            "traffic": None if big else CELL_KERNEL_DRAM_BYTES_UNIFORM1M,
+            "traffic": CELL_KERNEL_DRAM_BYTES_UNIFORM1M if args.workload == "uniform1m" else None,
             "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-            "kernel": "k_cells3<float,2,64> (cell kernel phase, all tiers)", "kernel_ms": kern_avg_ms,
+            "kernel": ("k_cells3<float,2,64>" if dim == 3 else "k_cells2<float,8,32>") + " (cell kernel phase, all tiers)",
+            "kernel_ms": kern_avg_ms,
             "flop_per_cell": flop / n,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
-    c_fixed = V.vg_config_default()
-    w_fixed, fb_fixed = work(c_fixed)
-    learned = {"fallback_rate": float(fb.mean()), "preload_per_cell": float(w["p"].mean()),
-               "fixed_k_fallback_rate": float(fb_fixed.mean()),
-               "fixed_k_preload_per_cell": float(w_fixed["p"].mean()),
-               "alpha": MLP_ALPHA, "trained": mlp_meta}
+    learned = None
+    if learned_on:
+        c_fixed = V.vg_config_default()
+        w_fixed, fb_fixed = work(c_fixed)
+        learned = {"fallback_rate": float(fb.mean()), "preload_per_cell": float(w["p"].mean()),
+                   "fixed_k_fallback_rate": float(fb_fixed.mean()),
+                   "fixed_k_preload_per_cell": float(w_fixed["p"].mean()),
+                   "alpha": MLP_ALPHA, "trained": mlp_meta}
 
     # ---- the same step in other forms (graph replays) ---------------------------
     def form_rate(order, use_mlp, precision=V.VG_FP32_RETEST, reps=5):
         c2 = V.vg_config_default()
         c2.precision, c2.order, c2.use_mlp = precision, order, use_mlp
-        V.vg_graph_capture(ctx, [n], pos_d, None, c2)
+        V.vg_graph_capture(ctx, [n], pos_d, rad_d, c2)
         V.vg_graph_launch(ctx)
         V.vg_graph_sync(ctx)
         ms = graph_steps(V, torch, ctx, stream, flush, reps)
         return n * reps / (sum(ms) / 1000.0)
 
-    forms = {"fp32_prefetch_fixed_k72": form_rate(V.VG_PREFETCH, 0),
-             "fp32_walk": form_rate(V.VG_WALK, 0)}
+    forms = {"fp32_walk": form_rate(V.VG_WALK, 0)}
+    if dim == 3 and (learned_on or chosen_order != "prefetch"):
+        forms["fp32_prefetch_fixed_k72"] = form_rate(V.VG_PREFETCH, 0)
     plain64 = form_rate(V.VG_WALK, 0, V.VG_FP64, reps=1 if big else 3)
 
     # ---- end to end through the public API, host buffers -----------------------
     e2e = None
-    if not args.no_e2e and not big:
+    if not args.no_e2e and args.workload == "uniform1m":
         pos_h = torch.from_numpy(s.pos).pin_memory().numpy()
         outs = {"vol": np.float64, "area": np.float64, "nv": np.int32, "ne": np.int32,
                 "nf": np.int32, "status": np.uint8}
         host = {k: torch.empty(n, dtype=getattr(torch, np.dtype(t).name)).pin_memory().numpy()
                 for k, t in outs.items()}
         cen = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
-        V.vg_insert(ctx, pos_d)
+        V.vg_insert(ctx, pos_d, rad_d)
         V.vg_compute(ctx, cfg)
         _, nface = V.vg_get_counts(ctx)
         fo = torch.empty(n + 1, dtype=torch.int64).pin_memory().numpy()
@@ -420,7 +445,8 @@ def main():
         e2e = {"value": n * reps / dt, "unit": "cells/s", "h2d_bytes_per_step": int(n * 3 * 8),
                "d2h_bytes_per_step": int(d2h)}
 
-    line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+    line = {"metric": METRIC if dim == 3 else METRIC_2D, "value": value, "unit": "cells/s", "n_gpus": world,
+            "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "cells_per_step": n * world,
@@ -435,11 +461,12 @@ def main():
             "forms": forms, "learned_preload": learned,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "retest_per_cell": float(w["r"].mean())}
-    if not args.no_batched and not big:
+    if not args.no_batched and args.workload == "uniform1m":
         line["batched"] = batched_run(V, torch, stream, flush)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = {k: v for k, v in
-                                cpu_baseline(s, grid, 100_000 if big else n).items() if k != "seconds"}
+                                cpu_baseline(s, grid, n if args.workload == "uniform1m" else 100_000).items()
+                                if k != "seconds"}
     V.vg_destroy(ctx)
     V.vg_mlp_destroy(mlp)
     print(json.dumps(line), flush=True)
