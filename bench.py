@@ -48,7 +48,7 @@ WORKLOADS = {
                   "n_opt = 4.6 rule; chosen form = FP32 cuts + FP64 re-test, learned distance-sorted preload"),
     "radical2m": ("radical2m: 2,000,000 points uniform in a periodic cube (unit density, seed 4), radii "
                   "log-normal (sigma 0.3) scaled to packing fraction 0.4, blocks by the n_opt = 4.6 rule; "
-                  "chosen form = FP32 cuts + FP64 re-test, distance-sorted preload (fixed target 72)"),
+                  "chosen form = FP32 cuts + FP64 re-test, block walk"),
     "hex10m": ("hex10m: 2D, 10,000,314 points of a perturbed hexagonal lattice (2943 x 3398, sigma 0.05 of the "
                "column spacing, seed 3) in the periodic unit square, blocks by the n_opt = 3.4 rule; "
                "chosen form = FP32 cuts + FP64 re-test, block walk"),
@@ -90,7 +90,7 @@ def workload(name: str, rank: int):
     if name == "slabs102m":
         return W.fcc_uniform_slabs(seed=6 + rank), None, "prefetch", True
     if name == "radical2m":
-        return W.radical_uniform(2_000_000, 0.4, 0.3, seed=4 + rank), None, "prefetch", False
+        return W.radical_uniform(2_000_000, 0.4, 0.3, seed=4 + rank), None, "walk", False
     s = W.hexagonal(2943, 3398, (1.0, 1.0), 0.05, seed=3 + rank)
     return s, None, "walk", False
 
@@ -408,7 +408,9 @@ def main():
         ms = graph_steps(V, torch, ctx, stream, flush, reps)
         return n * reps / (sum(ms) / 1000.0)
 
-    forms = {"fp32_walk": form_rate(V.VG_WALK, 0)}
+    forms = {}
+    if learned_on or chosen_order != "walk":
+        forms["fp32_walk"] = form_rate(V.VG_WALK, 0)
     if dim == 3 and (learned_on or chosen_order != "prefetch"):
         forms["fp32_prefetch_fixed_k72"] = form_rate(V.VG_PREFETCH, 0)
     plain64 = form_rate(V.VG_WALK, 0, V.VG_FP64, reps=1 if big else 3)
