@@ -57,6 +57,14 @@ constexpr int MAX_SHELL_EXTRA = 4;
 #ifndef VG_MINB
 #define VG_MINB 4
 #endif
+#ifndef VG_MAXT
+#define VG_MAXT 128
+#endif
+#ifdef VG_MAXREG
+#define VG_BOUNDS __maxnreg__(VG_MAXREG)
+#else
+#define VG_BOUNDS __launch_bounds__(VG_MAXT, VG_MINB)
+#endif
 
 template <typename T> struct V4T;
 template <> struct V4T<float> { using t = float4; };
@@ -129,6 +137,9 @@ struct Smem {
     } x;
     FT sfirst[32];             // a triangle of each face of a round
     int elist[32 * VPL];       // boundary edges (x | y << 8) of one cut
+    typename V4T<T>::t cbq[32];  // the current candidate batch: q and |q|^2, one per lane
+    int2 cbr[32];                //   sorted index and packed image
+    T cbrj[32];                  //   radius (radical)
     CellC cc;
     Src src;
     int cnt[6];  // work counters
@@ -380,7 +391,7 @@ __device__ __forceinline__ bool resolve(const Grid &g, long long base, const int
 // ---- the kernel ------------------------------------------------------------------
 
 template <typename T, int VPL, int MAXP, bool BATCH>
-__global__ void __launch_bounds__(128, VG_MINB)
+__global__ void VG_BOUNDS
     k_cells3(const __grid_constant__ Store st, const __grid_constant__ Out o,
              const __grid_constant__ Params pp, const __grid_constant__ Offsets off, unsigned *ticket,
              const int *cells, int ncells, int tier) {
@@ -712,8 +723,6 @@ __global__ void __launch_bounds__(128, VG_MINB)
                 }
             }
             unsigned want = 0;
-            T cqx = 0, cqy = 0, cqz = 0, cqq = 0, crj = 0;
-            int cref = 0, cimg = 0;
             T stop = stop2();
 
             for (int guard = 0; guard < (1 << 30); guard++) {
@@ -734,14 +743,17 @@ __global__ void __launch_bounds__(128, VG_MINB)
                         const int nb0 = src.nbatch;
                         const bool filt = nb0 > 0;
                         bool ok = false;
+                        T cqq = 0;
+                        __syncwarp();  // the previous batch has been read
                         if (in) {
                             const int slot = S.x.pf.slot[idx];
                             const float4 q4 = S.x.pf.q[slot];
                             const int2 r = S.x.pf.r[slot];
-                            cqx = (T)q4.x; cqy = (T)q4.y; cqz = (T)q4.z; cqq = (T)q4.w;
-                            cref = r.x;
-                            cimg = r.y;
-                            crj = st.radical ? (T)__ldg(&st.p32[r.x]).w : (T)0;
+                            cqq = (T)q4.w;
+                            const T crj = st.radical ? (T)__ldg(&st.p32[r.x]).w : (T)0;
+                            S.cbq[lane] = mk4<T>((T)q4.x, (T)q4.y, (T)q4.z, (T)q4.w);
+                            S.cbr[lane] = r;
+                            S.cbrj[lane] = crj;
                             ok = (T)q4.w < stop;
                             if constexpr (F32) {
                                 if (filt && ok && q4.w >= 1e-30f) {
@@ -751,11 +763,12 @@ __global__ void __launch_bounds__(128, VG_MINB)
                             }
                         }
                         want = __ballot_sync(FULL, ok);
+                        __syncwarp();
                         src.nbatch = nb0 + 1;  // every lane writes the same value
                         // bucketed: once the last entry's bucket starts beyond the
                         // bound, every later entry lies beyond it too
                         const int last = min(count - u, 32) - 1;
-                        const float qlast = __shfl_sync(FULL, (float)cqq, last);
+                        const float qlast = __shfl_sync(FULL, (float)cqq, last);  // this batch's lane value
                         const float t = fminf(qlast / src.rho2, 1.f);
                         const int bl = min(NBIN - 1, (int)((float)NBIN * t * sqrtf(t)));
                         const float f = (float)bl / (float)NBIN;
@@ -770,7 +783,9 @@ __global__ void __launch_bounds__(128, VG_MINB)
                         const int nb0 = src.nbatch;
                         const bool filt = nb0 > 0;
                         bool ok = false;
+                        __syncwarp();  // the previous batch has been read
                         if (v < vtot) {
+                            T cqx = 0, cqy = 0, cqz = 0, cqq = 0, crj = 0;
                             int lo = 0, hi = src.nwin - 1;  // last block with vstart <= v
                             while (lo < hi) {
                                 const int mid = (lo + hi + 1) >> 1;
@@ -800,10 +815,12 @@ __global__ void __launch_bounds__(128, VG_MINB)
                                     ok = may_cut<CAP>(S.v4, cqx, cqy, cqz, cc, tol32f * sqrtf(r2 * cqq));
                                 }
                             }
-                            cref = j;
-                            cimg = mc & 0xffffff;
+                            S.cbq[lane] = mk4<T>(cqx, cqy, cqz, cqq);
+                            S.cbr[lane] = make_int2(j, mc & 0xffffff);
+                            S.cbrj[lane] = crj;
                         }
                         want = __ballot_sync(FULL, ok);
+                        __syncwarp();
                         src.nbatch = nb0 + 1;  // every lane writes the same value
                         src.vp = vp + 32;
                         continue;
@@ -892,14 +909,15 @@ __global__ void __launch_bounds__(128, VG_MINB)
                 if (want == 0) break;
                 const int srcl = __ffs(want) - 1;
                 want &= want - 1;
-                const T qx = __shfl_sync(FULL, cqx, srcl), qy = __shfl_sync(FULL, cqy, srcl);
-                const T qz = __shfl_sync(FULL, cqz, srcl), qq = __shfl_sync(FULL, cqq, srcl);
-                const int ref = __shfl_sync(FULL, cref, srcl), img = __shfl_sync(FULL, cimg, srcl);
+                const auto cq4 = S.cbq[srcl];
+                const int2 cr = S.cbr[srcl];
+                const T qx = cq4.x, qy = cq4.y, qz = cq4.z, qq = cq4.w;
+                const int ref = cr.x, img = cr.y;
                 if (qq >= stop) continue;
                 if (qq < (T)1e-30) { flags |= 8; continue; }
                 T c;
                 if (st.radical) {
-                    const T rj = __shfl_sync(FULL, crj, srcl);
+                    const T rj = S.cbrj[srcl];
                     if constexpr (F32) c = 0.5f * (qq + rp32 * rp32 - rj * rj);
                     else c = 0.5 * (qq + S.cc.rp * S.cc.rp - rj * rj);
                 } else {
@@ -1460,7 +1478,7 @@ cudaError_t launch_t(const Store &s, const Out &o, const Params &p, const Offset
 cudaError_t launch_cells3(const Store &s, const Out &o, const Params &p, const Offsets &off, int precision,
                           unsigned *ticket, int sm_count, int warps_per_cta, const int *cells, int ncells, int tier,
                           cudaStream_t st) {
-    const int w = warps_per_cta > 0 ? warps_per_cta : 4;
+    const int w = warps_per_cta > 0 ? min(warps_per_cta, VG_MAXT / 32) : VG_MAXT / 32;
     // the rare large cells (tiers 1, 2) always take the batched form
     if (tier == 2) return launch_t<double, 16, 256, true>(s, o, p, off, ticket, sm_count, 1, cells, ncells, tier, st);
     if (tier == 1)
