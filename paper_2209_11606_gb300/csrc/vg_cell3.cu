@@ -60,6 +60,11 @@ constexpr int MAX_SHELL_EXTRA = 4;
 #ifndef VG_MAXT
 #define VG_MAXT 128
 #endif
+// tier-0 lanes per cell and vertex slots per lane (G * VPL = 64)
+#ifndef VG_T0_G
+#define VG_T0_G 32
+#endif
+#define VG_T0_VPL (64 / VG_T0_G)
 #ifdef VG_MAXREG
 #define VG_BOUNDS __maxnreg__(VG_MAXREG)
 #else
@@ -106,26 +111,26 @@ struct Src {
     int rg[3];         // prefetch reach in blocks per axis
 };
 
-template <typename T, int VPL, int MAXP>
+template <typename T, int VPL, int MAXP, int G>
 struct Smem {
     // slot indices in the face walk tables: a byte up to 256 vertices
-    using FT = typename std::conditional<(32 * VPL > 256), unsigned short, unsigned char>::type;
+    using FT = typename std::conditional<(G * VPL > 256), unsigned short, unsigned char>::type;
     typename V4T<T>::t pl[MAXP];  // plane normal (x,y,z) and constant (w), cell frame
     int pref[MAXP];               // neighbour's sorted index, or wall code -1..-6
     int pimg[MAXP];               // packed image shift of the neighbour
-    unsigned stri[32 * VPL];      // staging for compaction and statistics
-    T sx[32 * VPL], sy[32 * VPL], sz[32 * VPL];
-    float skap[32 * VPL];
-    float4 v4[32 * VPL];                    // FP32 form: the cell's vertices (x, y, z, kappa); free slots 0
+    unsigned stri[G * VPL];       // staging for compaction and statistics
+    T sx[G * VPL], sy[G * VPL], sz[G * VPL];
+    float skap[G * VPL];
+    float4 v4[G * VPL];                     // FP32 form: the cell's vertices (x, y, z, kappa); free slots 0
     unsigned long long E[MAXP][MAXP / 64];  // removed directed edges of one cut
     union {
-        FT ftab[32][MAXP];             // face walk tables, one row per face of a round
+        FT ftab[G][MAXP];              // face walk tables, one row per face of a round
         struct {
             int start[NRUN], j0[NRUN], oxb[NRUN], oyz[NRUN];
         } run;                         // prefetch gather: runs of contiguous blocks
         struct {
-            int vstart[32], j0[32], o[32], m[32];
-        } win;                         // walk: a window of up to 32 blocks
+            int vstart[G], j0[G], o[G], m[G];
+        } win;                         // walk: a window of up to G blocks
     } w;
     union {
         struct {
@@ -133,13 +138,13 @@ struct Smem {
             int2 r[KMAX];    // sorted index and packed image
             int slot[KMAX];  // sorted order of the slots
         } pf;
-        double dpos[32 * VPL][3];  // FP64 vertices (degenerate cells)
+        double dpos[G * VPL][3];   // FP64 vertices (degenerate cells)
     } x;
-    FT sfirst[32];             // a triangle of each face of a round
-    int elist[32 * VPL];       // boundary edges (x | y << 8) of one cut
-    typename V4T<T>::t cbq[32];  // the current candidate batch: q and |q|^2, one per lane
-    int2 cbr[32];                //   sorted index and packed image
-    T cbrj[32];                  //   radius (radical)
+    FT sfirst[G];              // a triangle of each face of a round
+    int elist[G * VPL];        // boundary edges (x | y << 8) of one cut
+    typename V4T<T>::t cbq[G];   // the current candidate batch: q and |q|^2, one per lane
+    int2 cbr[G];                 //   sorted index and packed image
+    T cbrj[G];                   //   radius (radical)
     CellC cc;
     Src src;
     int cnt[6];  // work counters
@@ -184,54 +189,67 @@ __device__ __forceinline__ unsigned mk_tri(int a, int b, int c) {
     return (unsigned)a | ((unsigned)b << 8) | ((unsigned)c << 16);
 }
 
-__device__ __forceinline__ int warp_excl_scan(int v, int lane, int &total) {
+// Group primitives: a cell is handled by G consecutive lanes (G = 32: one
+// warp per cell; G = 16: two cells per warp).  gmask holds the group's lanes;
+// lane indices below are relative to the group.
+template <int G>
+__device__ __forceinline__ unsigned gballot(unsigned gmask, int gbase, bool p) {
+    const unsigned b = __ballot_sync(gmask, p);
+    if constexpr (G == 32) return b;
+    else return (b >> gbase) & ((1u << G) - 1);
+}
+template <int G>
+__device__ __forceinline__ int gexcl_scan(unsigned gmask, int v, int gl, int &total) {
     int x = v;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        int y = __shfl_up_sync(FULL, x, d);
-        if (lane >= d) x += y;
+    for (int d = 1; d < G; d <<= 1) {
+        int y = __shfl_up_sync(gmask, x, d, G);
+        if (gl >= d) x += y;
     }
-    total = __shfl_sync(FULL, x, 31);
+    total = __shfl_sync(gmask, x, G - 1, G);
     return x - v;
 }
-__device__ __forceinline__ double warp_sum_d(double v) {
+template <int G>
+__device__ __forceinline__ double gsum(unsigned gmask, double v) {
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
+    for (int d = G / 2; d > 0; d >>= 1) v += __shfl_xor_sync(gmask, v, d, G);
     return v;
 }
-__device__ __forceinline__ float warp_sum_t(float v) {
+template <int G>
+__device__ __forceinline__ float gsum(unsigned gmask, float v) {
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
+    for (int d = G / 2; d > 0; d >>= 1) v += __shfl_xor_sync(gmask, v, d, G);
     return v;
 }
-__device__ __forceinline__ double warp_sum_t(double v) { return warp_sum_d(v); }
-__device__ __forceinline__ double warp_max_t(double v) {
+template <int G>
+__device__ __forceinline__ double gmax(unsigned gmask, double v) {
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, d));
+    for (int d = G / 2; d > 0; d >>= 1) v = fmax(v, __shfl_xor_sync(gmask, v, d, G));
     return v;
 }
-__device__ __forceinline__ float warp_max_t(float v) {
+template <int G>
+__device__ __forceinline__ float gmax(unsigned gmask, float v) {
     // non-negative floats order like their bit patterns
-    return __int_as_float((int)__reduce_max_sync(FULL, (unsigned)__float_as_int(v)));
+    return __int_as_float((int)__reduce_max_sync(gmask, (unsigned)__float_as_int(v)));
 }
-__device__ __forceinline__ unsigned long long warp_or64(unsigned long long v) {
-    unsigned lo = __reduce_or_sync(FULL, (unsigned)v);
-    unsigned hi = __reduce_or_sync(FULL, (unsigned)(v >> 32));
+__device__ __forceinline__ unsigned long long gor64(unsigned gmask, unsigned long long v) {
+    unsigned lo = __reduce_or_sync(gmask, (unsigned)v);
+    unsigned hi = __reduce_or_sync(gmask, (unsigned)(v >> 32));
     return ((unsigned long long)hi << 32) | lo;
 }
 
-// Bitonic sort of 32*E keys held E per lane (element g = lane*E + e).
-template <int E>
-__device__ __forceinline__ void bitonic(unsigned long long (&k)[E], int lane) {
+// Bitonic sort of G*E keys held E per lane of a group (element g = gl*E + e).
+template <int E, int G>
+__device__ __forceinline__ void bitonic(unsigned long long (&k)[E], int gl, unsigned gmask) {
 #pragma unroll
-    for (int size = 2; size <= 32 * E; size <<= 1) {
+    for (int size = 2; size <= G * E; size <<= 1) {
 #pragma unroll
         for (int j = size >> 1; j > 0; j >>= 1) {
             if (j < E) {
 #pragma unroll
                 for (int e = 0; e < E; e++) {
                     if ((e & j) == 0) {
-                        int gi = lane * E + e;
+                        int gi = gl * E + e;
                         bool up = (gi & size) == 0;
                         unsigned long long a = k[e], b = k[e ^ j];
                         bool sw = up ? (a > b) : (a < b);
@@ -242,9 +260,9 @@ __device__ __forceinline__ void bitonic(unsigned long long (&k)[E], int lane) {
                 int lm = j / E;
 #pragma unroll
                 for (int e = 0; e < E; e++) {
-                    int gi = lane * E + e;
+                    int gi = gl * E + e;
                     bool up = (gi & size) == 0;
-                    unsigned long long ot = __shfl_xor_sync(FULL, k[e], lm);
+                    unsigned long long ot = __shfl_xor_sync(gmask, k[e], lm, G);
                     bool lower = (gi & j) == 0;
                     bool keep_min = (lower == up);
                     unsigned long long mn = k[e] < ot ? k[e] : ot, mx = k[e] < ot ? ot : k[e];
@@ -390,24 +408,27 @@ __device__ __forceinline__ bool resolve(const Grid &g, long long base, const int
 
 // ---- the kernel ------------------------------------------------------------------
 
-template <typename T, int VPL, int MAXP, bool BATCH>
+template <typename T, int VPL, int MAXP, bool BATCH, int G>
 __global__ void VG_BOUNDS
     k_cells3(const __grid_constant__ Store st, const __grid_constant__ Out o,
              const __grid_constant__ Params pp, const __grid_constant__ Offsets off, unsigned *ticket,
              const int *cells, int ncells, int tier) {
     constexpr bool F32 = sizeof(T) == 4;
-    constexpr int CAP = 32 * VPL;
+    constexpr int CAP = G * VPL;
     constexpr int NW = MAXP / 64;
-    constexpr int R = MAXP / 32;
-    using S_t = Smem<T, VPL, MAXP>;
+    constexpr int R = MAXP / G;
+    using S_t = Smem<T, VPL, MAXP, G>;
     extern __shared__ __align__(32) unsigned char smem_raw[];
+    // G lanes per cell: gl is the lane within the cell's group
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    S_t &S = reinterpret_cast<S_t *>(smem_raw)[warp];
+    const int gl = lane % G, gbase = lane - gl;
+    const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1) << gbase);
+    S_t &S = reinterpret_cast<S_t *>(smem_raw)[warp * (32 / G) + lane / G];
     Src &src = S.src;
     // the edge matrix starts clear; every cut leaves it clear
-    for (int u = lane; u < MAXP * NW; u += 32) (&S.E[0][0])[u] = 0ull;
-    if (lane == 0) S.sys_id = -1;
-    __syncwarp();
+    for (int u = gl; u < MAXP * NW; u += G) (&S.E[0][0])[u] = 0ull;
+    if (gl == 0) S.sys_id = -1;
+    __syncwarp(gmask);
     const Sys &SY = sys_ref<BATCH>(st, S.sysc);
     const Grid &g = SY.g;
     const int total = cells ? (tier == 1 ? *o.retry_count : (tier == 2 ? *o.retry2_count : ncells)) : st.n;
@@ -417,8 +438,8 @@ __global__ void VG_BOUNDS
 
     for (int iter = 0; iter < (1 << 30); iter++) {
         int base = 0;
-        if (lane == 0) base = (int)atomicAdd(ticket, (unsigned)chunk);
-        base = __shfl_sync(FULL, base, 0);
+        if (gl == 0) base = (int)atomicAdd(ticket, (unsigned)chunk);
+        base = __shfl_sync(gmask, base, 0, G);
         if (base >= total) break;
         const int wend = min(base + chunk, total);
         for (int w = base; w < wend; w++) {
@@ -428,12 +449,12 @@ __global__ void VG_BOUNDS
                 // the cell's system descriptor, kept while consecutive cells share it
                 const int sidx = __ldg(&st.ssys[i]);
                 if (sidx != S.sys_id) {
-                    __syncwarp();
+                    __syncwarp(gmask);
                     const int *src32 = reinterpret_cast<const int *>(&st.sys[sidx]);
                     int *dst32 = reinterpret_cast<int *>(&S.sysc);
-                    for (int u = lane; u < (int)(sizeof(Sys) / 4); u += 32) dst32[u] = __ldg(&src32[u]);
-                    if (lane == 0) S.sys_id = sidx;
-                    __syncwarp();
+                    for (int u = gl; u < (int)(sizeof(Sys) / 4); u += G) dst32[u] = __ldg(&src32[u]);
+                    if (gl == 0) S.sys_id = sidx;
+                    __syncwarp(gmask);
                 }
             }
             const int kh = __ldg(&st.sblk[i]);
@@ -442,7 +463,7 @@ __global__ void VG_BOUNDS
             {
                 const float4 p32 = __ldg(&st.p32[i]);
                 o0 = p32.x; o1 = p32.y; o2 = p32.z; rp32 = p32.w;
-                if (lane == 0) {
+                if (gl == 0) {
                     const D4 p64 = st.p64[i];
                     S.cc.i = i;
                     S.cc.self_id = __ldg(&st.sid[i]);
@@ -453,14 +474,14 @@ __global__ void VG_BOUNDS
                     S.cc.rp = p64.w;
                     S.cc.rmax = st.radical ? (BATCH ? S.sysc.rmax : st.sys[0].rmax) : 0.0;
                 }
-                if (pp.collect && lane < 6) S.cnt[lane] = 0;
+                if (pp.collect && gl < 6) S.cnt[gl] = 0;
             }
             // ------------------------------------- initial cell, Eqs. (1)-(2)
             unsigned tri[VPL];
             T vx[VPL], vy[VPL], vz[VPL];
             float kap[VPL];
             {
-                __syncwarp();
+                __syncwarp(gmask);
                 T lo[3], hi[3];
                 const float oo[3] = {o0, o1, o2};
 #pragma unroll
@@ -476,8 +497,8 @@ __global__ void VG_BOUNDS
                         hi[a] = g.hi[a] - S.cc.p[a];
                     }
                 }
-                if (lane < 6) {
-                    const int a = lane >> 1, side = lane & 1;
+                if (gl < 6) {
+                    const int a = gl >> 1, side = gl & 1;
                     T n[3] = {0, 0, 0};
                     T c;
                     int ref, img;
@@ -498,9 +519,9 @@ __global__ void VG_BOUNDS
                         ref = -(1 + 2 * a + side);
                         img = 0;
                     }
-                    S.pl[lane] = mk4<T>(n[0], n[1], n[2], c);
-                    S.pref[lane] = ref;
-                    S.pimg[lane] = img;
+                    S.pl[gl] = mk4<T>(n[0], n[1], n[2], c);
+                    S.pref[gl] = ref;
+                    S.pimg[gl] = img;
                 }
 #pragma unroll
                 for (int s = 0; s < VPL; s++) {
@@ -508,8 +529,8 @@ __global__ void VG_BOUNDS
                     vx[s] = vy[s] = vz[s] = (T)0;
                     kap[s] = 1.f;
                 }
-                if (lane < 8) {
-                    const int sx = lane & 1, sy = (lane >> 1) & 1, sz = (lane >> 2) & 1;
+                if (gl < 8) {
+                    const int sx = gl & 1, sy = (gl >> 1) & 1, sz = (gl >> 2) & 1;
                     const int minus = (1 - sx) + (1 - sy) + (1 - sz);
                     const int A = sx, B = 2 + sy, C = 4 + sz;
                     tri[0] = (minus & 1) ? mk_tri(A, C, B) : mk_tri(A, B, C);
@@ -520,16 +541,16 @@ __global__ void VG_BOUNDS
                 if constexpr (F32) {
 #pragma unroll
                     for (int s = 0; s < VPL; s++)
-                        S.v4[s * 32 + lane] = tri[s] != TRI_EMPTY ? make_float4(vx[s], vy[s], vz[s], kap[s])
+                        S.v4[s * G + gl] = tri[s] != TRI_EMPTY ? make_float4(vx[s], vy[s], vz[s], kap[s])
                                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
             int ntri = 8;        // vertices
-            unsigned rows = 1;   // register slots (rows of 32) that hold any vertex
+            unsigned rows = 1;   // register slots (rows of G lanes) that hold any vertex
             unsigned long long live[NW];
 #pragma unroll
             for (int w2 = 0; w2 < NW; w2++) live[w2] = w2 == 0 ? 0x3full : 0ull;
-            T r2 = warp_max_t(lane < 8 ? vx[0] * vx[0] + vy[0] * vy[0] + vz[0] * vz[0] : (T)0);
+            T r2 = gmax<G>(gmask, gl < 8 ? vx[0] * vx[0] + vy[0] * vy[0] + vz[0] * vz[0] : (T)0);
             // bit 0 degenerate, 1 capacity/consistency failure, 2 empty, 3 duplicate point
             int flags = 0;
 
@@ -566,15 +587,15 @@ __global__ void VG_BOUNDS
                     if (pp.kblock) kt = fmaxf(8.f, __ldg(&pp.kblock[kh]));
                     // local density from the 27 surrounding blocks
                     int n27 = 0, v27 = 0;
-                    if (lane < 27) {
+                    for (int q = gl; q < 27; q += G) {
                         int kk, mx, my, mz;
-                        if (resolve(g, SY.blk_base, S.cc.b, lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1, kk, mx, my, mz)) {
-                            n27 = __ldg(&st.bstart[kk + 1]) - __ldg(&st.bstart[kk]);
-                            v27 = 1;
+                        if (resolve(g, SY.blk_base, S.cc.b, q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1, kk, mx, my, mz)) {
+                            n27 += __ldg(&st.bstart[kk + 1]) - __ldg(&st.bstart[kk]);
+                            v27 += 1;
                         }
                     }
-                    n27 = __reduce_add_sync(FULL, n27);
-                    v27 = __reduce_add_sync(FULL, v27);
+                    n27 = __reduce_add_sync(gmask, n27);
+                    v27 = __reduce_add_sync(gmask, v27);
                     const float dens = (float)max(n27, 1) / ((float)max(v27, 1) * g.hf[0] * g.hf[1] * g.hf[2]);
                     float rho = cbrtf(3.f * kt / (4.f * 3.14159265f * dens));
                     int count = 0;
@@ -589,12 +610,12 @@ __global__ void VG_BOUNDS
                         count = 0;
                         if (rg0 > RGMAX || rg1 > RGMAX || rg2 > RGMAX) { give_up = true; break; }
                         // 1. runs of contiguous blocks: rows along x (fixed oy, oz)
-                        //    split where the x image shift changes; one row per lane
+                        //    split where the x image shift changes; one row per gl
                         const int wy = 2 * rg1 + 1, nrows = wy * (2 * rg2 + 1);
                         const int bx = S.cc.b[0];
                         int nrun = 0, npart = 0;
-                        for (int r0 = 0; r0 < nrows; r0 += 32) {
-                            const int r = r0 + lane;
+                        for (int r0 = 0; r0 < nrows; r0 += G) {
+                            const int r = r0 + gl;
                             int oy = 0, oz = 0, krow = 0, ox = 0, oxhi = -1;
                             bool rowok = false;
                             if (r < nrows) {
@@ -628,7 +649,7 @@ __global__ void VG_BOUNDS
                                         xb = bx + oxhi;
                                     }
                                 }
-                                const unsigned hb = __ballot_sync(FULL, have);
+                                const unsigned hb = gballot<G>(gmask, gbase, have);
                                 if (!hb) break;
                                 int len = 0, j0r = 0;
                                 if (have) {
@@ -636,8 +657,8 @@ __global__ void VG_BOUNDS
                                     len = __ldg(&st.bstart[krow + xb + 1]) - j0r;
                                 }
                                 int ltot;
-                                const int lex = warp_excl_scan(len, lane, ltot);
-                                const int slot = nrun + __popc(hb & ((1u << lane) - 1));
+                                const int lex = gexcl_scan<G>(gmask, len, gl, ltot);
+                                const int slot = nrun + __popc(hb & ((1u << gl) - 1));
                                 if (have && slot < NRUN) {
                                     S.w.run.start[slot] = npart + lex;
                                     S.w.run.j0[slot] = j0r;
@@ -651,10 +672,10 @@ __global__ void VG_BOUNDS
                             }
                         }
                         if (nrun > NRUN) { give_up = true; break; }
-                        __syncwarp();
-                        // 2. all particles of all runs, 32 at a time
-                        for (int v0 = 0; v0 < npart; v0 += 32) {
-                            const int v = v0 + lane;
+                        __syncwarp(gmask);
+                        // 2. all particles of all runs, G at a time
+                        for (int v0 = 0; v0 < npart; v0 += G) {
+                            const int v = v0 + gl;
                             bool keep = false;
                             float qx = 0.f, qy = 0.f, qz = 0.f, qq = 0.f;
                             int j = 0, img = 0;
@@ -677,15 +698,15 @@ __global__ void VG_BOUNDS
                                     img = pack_img(mx, my, mz);
                                 }
                             }
-                            const unsigned bal = __ballot_sync(FULL, keep);
-                            const int pos = count + __popc(bal & ((1u << lane) - 1));
+                            const unsigned bal = gballot<G>(gmask, gbase, keep);
+                            const int pos = count + __popc(bal & ((1u << gl) - 1));
                             if (keep && pos < KMAX) {
                                 S.x.pf.q[pos] = make_float4(qx, qy, qz, qq);
                                 S.x.pf.r[pos] = make_int2(j, img);
                             }
                             count += __popc(bal);
                         }
-                        __syncwarp();
+                        __syncwarp(gmask);
                         if (count <= KMAX) break;
                         rho *= 0.8f * cbrtf((float)KMAX / (float)count);
                     }
@@ -694,10 +715,10 @@ __global__ void VG_BOUNDS
                         // rho (about equal counts); inside a bucket the gather order,
                         // which is deterministic, is kept
                         const float irho2 = 1.f / rho2;
-                        int bin[KMAX / 32];
+                        int bin[KMAX / G];
 #pragma unroll
-                        for (int e2 = 0; e2 < KMAX / 32; e2++) {
-                            const int slot = e2 * 32 + lane;
+                        for (int e2 = 0; e2 < KMAX / G; e2++) {
+                            const int slot = e2 * G + gl;
                             bin[e2] = NBIN;
                             if (slot < count) {
                                 const float t = fminf(S.x.pf.q[slot].w * irho2, 1.f);
@@ -707,19 +728,19 @@ __global__ void VG_BOUNDS
                         int pos0 = 0;
                         for (int b = 0; b < NBIN; b++) {
 #pragma unroll
-                            for (int e2 = 0; e2 < KMAX / 32; e2++) {
-                                const unsigned m = __ballot_sync(FULL, bin[e2] == b);
-                                if (bin[e2] == b) S.x.pf.slot[pos0 + __popc(m & ((1u << lane) - 1))] = e2 * 32 + lane;
+                            for (int e2 = 0; e2 < KMAX / G; e2++) {
+                                const unsigned m = gballot<G>(gmask, gbase, bin[e2] == b);
+                                if (bin[e2] == b) S.x.pf.slot[pos0 + __popc(m & ((1u << gl) - 1))] = e2 * G + gl;
                                 pos0 += __popc(m);
                             }
                         }
                         src.mode = 0;
                         src.count = count;
-                        if (pp.collect && lane == 0) S.cnt[5] = count;
+                        if (pp.collect && gl == 0) S.cnt[5] = count;
                         src.rho2 = rho2;
                         src.rg[0] = rg0; src.rg[1] = rg1; src.rg[2] = rg2;
                     }
-                    __syncwarp();
+                    __syncwarp(gmask);
                 }
             }
             unsigned want = 0;
@@ -737,23 +758,23 @@ __global__ void VG_BOUNDS
                             else { src.mode = 1; src.fell_back = 1; }
                             continue;
                         }
-                        const int idx = u + lane;
+                        const int idx = u + gl;
                         const bool in = idx < count;
                         // the first batch meets the initial box: nothing to drop yet
                         const int nb0 = src.nbatch;
                         const bool filt = nb0 > 0;
                         bool ok = false;
                         T cqq = 0;
-                        __syncwarp();  // the previous batch has been read
+                        __syncwarp(gmask);  // the previous batch has been read
                         if (in) {
                             const int slot = S.x.pf.slot[idx];
                             const float4 q4 = S.x.pf.q[slot];
                             const int2 r = S.x.pf.r[slot];
                             cqq = (T)q4.w;
                             const T crj = st.radical ? (T)__ldg(&st.p32[r.x]).w : (T)0;
-                            S.cbq[lane] = mk4<T>((T)q4.x, (T)q4.y, (T)q4.z, (T)q4.w);
-                            S.cbr[lane] = r;
-                            S.cbrj[lane] = crj;
+                            S.cbq[gl] = mk4<T>((T)q4.x, (T)q4.y, (T)q4.z, (T)q4.w);
+                            S.cbr[gl] = r;
+                            S.cbrj[gl] = crj;
                             ok = (T)q4.w < stop;
                             if constexpr (F32) {
                                 if (filt && ok && q4.w >= 1e-30f) {
@@ -762,28 +783,28 @@ __global__ void VG_BOUNDS
                                 }
                             }
                         }
-                        want = __ballot_sync(FULL, ok);
-                        __syncwarp();
-                        src.nbatch = nb0 + 1;  // every lane writes the same value
+                        want = gballot<G>(gmask, gbase, ok);
+                        __syncwarp(gmask);
+                        src.nbatch = nb0 + 1;  // every gl writes the same value
                         // bucketed: once the last entry's bucket starts beyond the
                         // bound, every later entry lies beyond it too
-                        const int last = min(count - u, 32) - 1;
-                        const float qlast = __shfl_sync(FULL, (float)cqq, last);  // this batch's lane value
+                        const int last = min(count - u, G) - 1;
+                        const float qlast = __shfl_sync(gmask, (float)cqq, last, G);  // this batch's gl value
                         const float t = fminf(qlast / src.rho2, 1.f);
                         const int bl = min(NBIN - 1, (int)((float)NBIN * t * sqrtf(t)));
                         const float f = (float)bl / (float)NBIN;
                         const float lb2 = src.rho2 * cbrtf(f * f) * 0.9999f;  // margin for rounding
-                        src.u = ((T)lb2 >= stop) ? count : u + 32;
+                        src.u = ((T)lb2 >= stop) ? count : u + G;
                         continue;
                     }
                     const int vp = src.vp, vtot = src.vtot;
                     if (vp < vtot) {
                         // a batch of the current window's particles
-                        const int v = vp + lane;
+                        const int v = vp + gl;
                         const int nb0 = src.nbatch;
                         const bool filt = nb0 > 0;
                         bool ok = false;
-                        __syncwarp();  // the previous batch has been read
+                        __syncwarp(gmask);  // the previous batch has been read
                         if (v < vtot) {
                             T cqx = 0, cqy = 0, cqz = 0, cqq = 0, crj = 0;
                             int lo = 0, hi = src.nwin - 1;  // last block with vstart <= v
@@ -815,17 +836,17 @@ __global__ void VG_BOUNDS
                                     ok = may_cut<CAP>(S.v4, cqx, cqy, cqz, cc, tol32f * sqrtf(r2 * cqq));
                                 }
                             }
-                            S.cbq[lane] = mk4<T>(cqx, cqy, cqz, cqq);
-                            S.cbr[lane] = make_int2(j, mc & 0xffffff);
-                            S.cbrj[lane] = crj;
+                            S.cbq[gl] = mk4<T>(cqx, cqy, cqz, cqq);
+                            S.cbr[gl] = make_int2(j, mc & 0xffffff);
+                            S.cbrj[gl] = crj;
                         }
-                        want = __ballot_sync(FULL, ok);
-                        __syncwarp();
-                        src.nbatch = nb0 + 1;  // every lane writes the same value
-                        src.vp = vp + 32;
+                        want = gballot<G>(gmask, gbase, ok);
+                        __syncwarp(gmask);
+                        src.nbatch = nb0 + 1;  // every gl writes the same value
+                        src.vp = vp + G;
                         continue;
                     }
-                    // a new window: up to 32 blocks set up in parallel
+                    // a new window: up to G blocks set up in parallel
                     if (src.last) { src.mode = 3; continue; }
                     int ox = 0, oy = 0, oz = 0;
                     bool cand = false;
@@ -833,7 +854,7 @@ __global__ void VG_BOUNDS
                         const int e = src.e;
                         const int ocount = SY.off_count, obase = SY.off_base;
                         if (e >= ocount) { src.mode = 2; continue; }
-                        const int ei = e + lane;
+                        const int ei = e + gl;
                         bool beyond = true;
                         if (ei < ocount) {
                             const float lb = __ldg(&off.lb[obase + ei]);
@@ -843,11 +864,11 @@ __global__ void VG_BOUNDS
                         }
                         // the list is sorted by its bound: entries past the first
                         // one beyond the stop radius are all beyond it
-                        const unsigned bb = __ballot_sync(FULL, beyond);
-                        const int first = bb ? __ffs(bb) - 1 : 32;
-                        cand = lane < first;
-                        if (first < 32 && e + first < ocount) src.last = 1;
-                        src.e = e + 32;
+                        const unsigned bb = gballot<G>(gmask, gbase, beyond);
+                        const int first = bb ? __ffs(bb) - 1 : G;
+                        cand = gl < first;
+                        if (first < G && e + first < ocount) src.last = 1;
+                        src.e = e + G;
                     } else {
                         const int shell = src.shell;
                         const float hmin = fminf(g.hf[0], fminf(g.hf[1], g.hf[2]));
@@ -857,7 +878,7 @@ __global__ void VG_BOUNDS
                         if (shell > maxs) { src.limit = 1; src.mode = 3; continue; }
                         const int wd = 2 * shell + 1, sidx = src.sidx;
                         if (sidx >= wd * wd * wd) { src.shell = shell + 1; src.sidx = 0; continue; }
-                        const int si = sidx + lane;
+                        const int si = sidx + gl;
                         if (si < wd * wd * wd) {
                             ox = si % wd - shell;
                             oy = (si / wd) % wd - shell;
@@ -870,7 +891,7 @@ __global__ void VG_BOUNDS
                             cand = max(abs(ox), max(abs(oy), abs(oz))) == shell &&
                                    !(lbx * lbx + lby * lby + lbz * lbz < lbmax * lbmax);
                         }
-                        src.sidx = sidx + 32;
+                        src.sidx = sidx + G;
                     }
                     int kk = 0, mx = 0, my = 0, mz = 0, len = 0, j0b = 0, inpref = 0;
                     if (cand) {
@@ -891,11 +912,11 @@ __global__ void VG_BOUNDS
                                      block_gap2(g, o0, o1, o2, ox, oy, oz) < rho2;
                         }
                     }
-                    const unsigned cb = __ballot_sync(FULL, cand);
+                    const unsigned cb = gballot<G>(gmask, gbase, cand);
                     int ltot;
-                    const int lex = warp_excl_scan(cand ? len : 0, lane, ltot);
+                    const int lex = gexcl_scan<G>(gmask, cand ? len : 0, gl, ltot);
                     if (cand) {
-                        const int slot = __popc(cb & ((1u << lane) - 1));
+                        const int slot = __popc(cb & ((1u << gl) - 1));
                         S.w.win.vstart[slot] = lex;
                         S.w.win.j0[slot] = j0b;
                         S.w.win.o[slot] = pack_img(ox, oy, oz) | (inpref << 24);
@@ -904,7 +925,7 @@ __global__ void VG_BOUNDS
                     src.nwin = __popc(cb);
                     src.vp = 0;
                     src.vtot = ltot;
-                    __syncwarp();
+                    __syncwarp(gmask);
                 }
                 if (want == 0) break;
                 const int srcl = __ffs(want) - 1;
@@ -925,7 +946,7 @@ __global__ void VG_BOUNDS
                 }
 
                 // ================================= cut by the plane q.r = c
-                if (pp.collect && lane == 0) { S.cnt[0]++; S.cnt[1] += ntri; }
+                if (pp.collect && gl == 0) { S.cnt[0]++; S.cnt[1] += ntri; }
                 T tau;
                 if constexpr (F32) tau = tol32f * sqrtf(r2 * qq);
                 else tau = (T)(pp.tau_rel * g.s * sqrt((double)qq));
@@ -946,8 +967,8 @@ __global__ void VG_BOUNDS
                     }
                 }
                 if constexpr (F32) {
-                    if (__any_sync(FULL, nearm)) {
-                        if (pp.collect && lane == 0) S.cnt[4]++;
+                    if (__any_sync(gmask, nearm)) {
+                        if (pp.collect && gl == 0) S.cnt[4]++;
 #pragma unroll
                         for (int s = 0; s < VPL; s++) {
                             if (nearm & (1u << s)) {
@@ -959,9 +980,9 @@ __global__ void VG_BOUNDS
                         }
                     }
                 }
-                if (!__any_sync(FULL, outm)) continue;
-                if (__any_sync(FULL, onm)) flags |= 1;
-                if (pp.collect && lane == 0) S.cnt[2]++;
+                if (!__any_sync(gmask, outm)) continue;
+                if (__any_sync(gmask, onm)) flags |= 1;
+                if (pp.collect && gl == 0) S.cnt[2]++;
                 int np = -1;
 #pragma unroll
                 for (int w2 = NW - 1; w2 >= 0; w2--)
@@ -977,7 +998,7 @@ __global__ void VG_BOUNDS
                         atomicOr(&S.E[cc][a >> 6], 1ull << (a & 63));
                     }
                 }
-                __syncwarp();
+                __syncwarp(gmask);
                 unsigned bnd[VPL];
                 int kc = 0, nc = 0;
 #pragma unroll
@@ -994,8 +1015,8 @@ __global__ void VG_BOUNDS
                         kc++;
                     }
                 }
-                __syncwarp();
-                // every lane has read the matrix: clear the rows this cut marked
+                __syncwarp(gmask);
+                // every gl has read the matrix: clear the rows this cut marked
 #pragma unroll
                 for (int s = 0; s < VPL; s++) {
                     if (outm & (1u << s)) {
@@ -1005,10 +1026,10 @@ __global__ void VG_BOUNDS
                     }
                 }
                 int tot2;
-                const int pk = warp_excl_scan(kc | (nc << 16), lane, tot2);
+                const int pk = gexcl_scan<G>(gmask, kc | (nc << 16), gl, tot2);
                 const int K = tot2 & 0xffff, N = tot2 >> 16;
                 const int tot = K + N;
-                if (pp.collect && lane == 0) S.cnt[3] += N;
+                if (pp.collect && gl == 0) S.cnt[3] += N;
                 const int rc = tot > CAP ? 3 : (tot == 0 ? 2 : 1);
                 if (rc != 1) {
                     flags |= rc == 2 ? 4 : 2;
@@ -1027,9 +1048,9 @@ __global__ void VG_BOUNDS
                         }
                     }
                 }
-                __syncwarp();
-                // new vertices, one per lane: planes x, y and the cutting plane
-                for (int q = lane; q < N; q += 32) {
+                __syncwarp(gmask);
+                // new vertices, one per gl: planes x, y and the cutting plane
+                for (int q = gl; q < N; q += G) {
                     const int xy = S.elist[q];
                     const int x = xy & 0xff, y = xy >> 8;
                     const auto P1 = S.pl[x];
@@ -1064,12 +1085,12 @@ __global__ void VG_BOUNDS
                     S.sx[q] = nx; S.sy[q] = ny; S.sz[q] = nz;
                     S.skap[q] = kp;
                 }
-                if (lane == 0) {
+                if (gl == 0) {
                     S.pl[np] = mk4<T>(qx, qy, qz, c);
                     S.pref[np] = ref;
                     S.pimg[np] = img;
                 }
-                __syncwarp();
+                __syncwarp(gmask);
                 // kept vertices stay in place; free slots take the new ones in order
                 ntri = tot;
                 unsigned long long lv[NW];
@@ -1081,8 +1102,8 @@ __global__ void VG_BOUNDS
 #pragma unroll
                 for (int s = 0; s < VPL; s++) {
                     const bool fr = tri[s] == TRI_EMPTY;
-                    const unsigned fm = __ballot_sync(FULL, fr);
-                    const int rank = rank0 + __popc(fm & ((1u << lane) - 1));
+                    const unsigned fm = gballot<G>(gmask, gbase, fr);
+                    const int rank = rank0 + __popc(fm & ((1u << gl) - 1));
                     rank0 += __popc(fm);
                     if (fr && rank < N) {
                         tri[s] = S.stri[rank];
@@ -1099,14 +1120,14 @@ __global__ void VG_BOUNDS
                         rr = rr > q2 ? rr : q2;
                     }
                     if constexpr (F32)
-                        S.v4[s * 32 + lane] = tri[s] != TRI_EMPTY ? make_float4(vx[s], vy[s], vz[s], kap[s])
+                        S.v4[s * G + gl] = tri[s] != TRI_EMPTY ? make_float4(vx[s], vy[s], vz[s], kap[s])
                                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (__any_sync(FULL, tri[s] != TRI_EMPTY)) rows |= 1u << s;
+                    if (__any_sync(gmask, tri[s] != TRI_EMPTY)) rows |= 1u << s;
                 }
 #pragma unroll
-                for (int w2 = 0; w2 < NW; w2++) live[w2] = warp_or64(lv[w2]);
-                r2 = warp_max_t(rr);
-                __syncwarp();
+                for (int w2 = 0; w2 < NW; w2++) live[w2] = gor64(gmask, lv[w2]);
+                r2 = gmax<G>(gmask, rr);
+                __syncwarp(gmask);
                 stop = stop2();
             }
 
@@ -1122,7 +1143,7 @@ __global__ void VG_BOUNDS
                 const int T_ = ntri;
 #pragma unroll
                 for (int s = 0; s < VPL; s++) {
-                    const int t = s * 32 + lane;
+                    const int t = s * G + gl;
                     S.stri[t] = tri[s]; S.sx[t] = vx[s]; S.sy[t] = vy[s]; S.sz[t] = vz[s];
                 }
                 // reference point for the fans: a vertex of the cell (a radical
@@ -1132,21 +1153,21 @@ __global__ void VG_BOUNDS
                 T rx = 0, ry = 0, rz = 0;
                 {
                     int rsl = 0;
-                    unsigned occ = __ballot_sync(FULL, tri[0] != TRI_EMPTY);
+                    unsigned occ = gballot<G>(gmask, gbase, tri[0] != TRI_EMPTY);
 #pragma unroll
                     for (int s = 1; s < VPL; s++) {
-                        const unsigned oc = __ballot_sync(FULL, tri[s] != TRI_EMPTY);
+                        const unsigned oc = gballot<G>(gmask, gbase, tri[s] != TRI_EMPTY);
                         if (!occ && oc) { occ = oc; rsl = s; }
                     }
                     const int rl = __ffs(occ) - 1;
-                    tref = rsl * 32 + rl;
+                    tref = rsl * G + rl;
                     T cxv = 0, cyv = 0, czv = 0;
 #pragma unroll
                     for (int s = 0; s < VPL; s++)
                         if (s == rsl) { cxv = vx[s]; cyv = vy[s]; czv = vz[s]; }
-                    rx = __shfl_sync(FULL, cxv, rl);
-                    ry = __shfl_sync(FULL, cyv, rl);
-                    rz = __shfl_sync(FULL, czv, rl);
+                    rx = __shfl_sync(gmask, cxv, rl, G);
+                    ry = __shfl_sync(gmask, cyv, rl, G);
+                    rz = __shfl_sync(gmask, czv, rl, G);
                 }
                 // pass 0 sums the FP32 vertices; a cell thin against its
                 // distance from the particle gets a pass from FP64 vertices
@@ -1154,7 +1175,7 @@ __global__ void VG_BOUNDS
                 if (degen) {
 #pragma unroll
                     for (int s = 0; s < VPL; s++) {
-                        const int t = s * 32 + lane;
+                        const int t = s * G + gl;
                         if (tri[s] != TRI_EMPTY) {
                             if constexpr (F32) {
                                 vertex64(&g, &st, &S.cc, S.pref, S.pimg, tri[s], S.x.dpos[t]);
@@ -1164,7 +1185,7 @@ __global__ void VG_BOUNDS
                         }
                     }
                 }
-                __syncwarp();
+                __syncwarp(gmask);
                 double dref[3];
                 if (degen) { dref[0] = S.x.dpos[tref][0]; dref[1] = S.x.dpos[tref][1]; dref[2] = S.x.dpos[tref][2]; }
                 else { dref[0] = (double)rx; dref[1] = (double)ry; dref[2] = (double)rz; }
@@ -1178,8 +1199,8 @@ __global__ void VG_BOUNDS
                 unsigned long long key[R];
 #pragma unroll
                 for (int r = 0; r < R; r++) key[r] = ~0ull;
-                for (int rnd = 0; rnd * 32 < F; rnd++) {
-                    const int f = rnd * 32 + lane;
+                for (int rnd = 0; rnd * G < F; rnd++) {
+                    const int f = rnd * G + gl;
                     // plane of face f: the f-th set bit of the live mask
                     int a = -1;
                     if (f < F) {
@@ -1199,7 +1220,7 @@ __global__ void VG_BOUNDS
                     // every vertex enters itself in the walk tables of its faces
 #pragma unroll
                     for (int s = 0; s < VPL; s++) {
-                        const int t = s * 32 + lane;
+                        const int t = s * G + gl;
                         if (tri[s] != TRI_EMPTY) {
                             const unsigned tr = tri[s];
                             const int pp3[3] = {tri_a(tr), tri_b(tr), tri_c(tr)};
@@ -1213,15 +1234,15 @@ __global__ void VG_BOUNDS
                                     if (pl_ >= lo64 + 64) rk += __popcll(live[w2]);
                                     else if (pl_ > lo64) rk += __popcll(live[w2] & ((1ull << (pl_ - lo64)) - 1));
                                 }
-                                if ((rk >> 5) == rnd) {
-                                    S.w.ftab[rk & 31][xx] = (typename S_t::FT)t;
-                                    S.sfirst[rk & 31] = (typename S_t::FT)t;
+                                if (rk / G == rnd) {
+                                    S.w.ftab[rk % G][xx] = (typename S_t::FT)t;
+                                    S.sfirst[rk % G] = (typename S_t::FT)t;
                                 }
                             }
                         }
                     }
-                    __syncwarp();
-                    const int t0 = a >= 0 ? (int)S.sfirst[lane] : -1;
+                    __syncwarp(gmask);
+                    const int t0 = a >= 0 ? (int)S.sfirst[gl] : -1;
                     if (a >= 0) {
                         int steps = 0, cur = t0;
                         bool closed = false;
@@ -1236,7 +1257,7 @@ __global__ void VG_BOUNDS
                                 const int p0 = tri_a(tr), p1 = tri_b(tr), p2 = tri_c(tr);
                                 const int yy = p0 == a ? p2 : (p1 == a ? p0 : (p2 == a ? p1 : -1));
                                 if (yy < 0) { bad = true; break; }
-                                const int nx = S.w.ftab[lane][yy];
+                                const int nx = S.w.ftab[gl][yy];
                                 if (nx >= CAP || S.stri[nx] == TRI_EMPTY) { bad = true; break; }
                                 if (nx == t0) { steps++; closed = true; break; }
                                 if (cur != t0) {
@@ -1273,7 +1294,7 @@ __global__ void VG_BOUNDS
                                 const int p0 = tri_a(tr), p1 = tri_b(tr), p2 = tri_c(tr);
                                 const int yy = p0 == a ? p2 : (p1 == a ? p0 : (p2 == a ? p1 : -1));
                                 if (yy < 0) { bad = true; break; }
-                                const int nx = S.w.ftab[lane][yy];
+                                const int nx = S.w.ftab[gl][yy];
                                 if (nx >= CAP || S.stri[nx] == TRI_EMPTY) { bad = true; break; }
                                 if (nx == t0) { steps++; closed = true; break; }
                                 const double A[3] = {S.x.dpos[cur][0] - dref[0], S.x.dpos[cur][1] - dref[1],
@@ -1330,14 +1351,14 @@ __global__ void VG_BOUNDS
                                 if (r == rnd) key[r] = k;
                         }
                     }
-                    __syncwarp();
+                    __syncwarp(gmask);
                 }
-                vol = warp_sum_d(vol);
-                cx = warp_sum_t(cx); cy = warp_sum_t(cy); cz = warp_sum_t(cz);
-                area = warp_sum_t(area);
-                const int nfk = __reduce_add_sync(FULL, faces_kept);
-                const int osum = __reduce_add_sync(FULL, order_sum);
-                bool anybad = __any_sync(FULL, bad);
+                vol = gsum<G>(gmask, vol);
+                cx = gsum<G>(gmask, cx); cy = gsum<G>(gmask, cy); cz = gsum<G>(gmask, cz);
+                area = gsum<G>(gmask, area);
+                const int nfk = __reduce_add_sync(gmask, faces_kept);
+                const int osum = __reduce_add_sync(gmask, order_sum);
+                bool anybad = __any_sync(gmask, bad);
                 if (F32 && pass == 0 && !degen && !anybad) {
                     // FP32 vertex error ~ 3e-7 max(R, h) (h: the block side that
                     // bounds the stored FP32 offsets) relative to the thickness 3V/A
@@ -1345,7 +1366,7 @@ __global__ void VG_BOUNDS
                     const float scale = fmaxf(sqrtf((float)r2), fmaxf(g.hf[0], fmaxf(g.hf[1], g.hf[2])));
                     if (!(thick * 10.f > scale)) {
                         degen = true;
-                        __syncwarp();
+                        __syncwarp(gmask);
                         continue;
                     }
                 }
@@ -1356,7 +1377,7 @@ __global__ void VG_BOUNDS
                     int cntv = 0;
 #pragma unroll
                     for (int s = 0; s < VPL; s++) {
-                        const int t = s * 32 + lane;
+                        const int t = s * G + gl;
                         if (tri[s] != TRI_EMPTY) {
                             bool first = true;
                             for (int q = 0; q < t && first; q++) {
@@ -1368,7 +1389,7 @@ __global__ void VG_BOUNDS
                             cntv += first;
                         }
                     }
-                    nv = __reduce_add_sync(FULL, cntv);
+                    nv = __reduce_add_sync(gmask, cntv);
                 } else {
                     nv = T_;
                     if (nfk != T_ / 2 + 2) anybad = true;  // Euler with degree-3 vertices
@@ -1376,15 +1397,15 @@ __global__ void VG_BOUNDS
                 if (anybad) {
                     fail = true;  // inconsistent topology: the FP64 big-cell tier redoes it
                 } else {
-                    bitonic<R>(key, lane);
+                    bitonic<R, G>(key, gl, gmask);
                     long long fbase = 0;
-                    if (lane == 0) fbase = (long long)atomicAdd(o.fcount, (unsigned long long)nfk);
-                    fbase = __shfl_sync(FULL, fbase, 0);
+                    if (gl == 0) fbase = (long long)atomicAdd(o.fcount, (unsigned long long)nfk);
+                    fbase = __shfl_sync(gmask, fbase, 0, G);
                     const bool overflow = fbase + nfk > o.fcap;
                     if (!overflow) {
 #pragma unroll
                         for (int r = 0; r < R; r++) {
-                            const int gpos = lane * R + r;
+                            const int gpos = gl * R + r;
                             if (gpos < nfk) {
                                 const unsigned long long k = key[r];
                                 int2 ent;
@@ -1397,7 +1418,7 @@ __global__ void VG_BOUNDS
                             }
                         }
                     }
-                    if (lane == 0) {
+                    if (gl == 0) {
                         const double v6 = vol;
                         o.vol[out_i] = v6 * (1.0 / 6.0);
                         if constexpr (F32) o.rfin[out_i] = sqrtf(r2);
@@ -1415,10 +1436,10 @@ __global__ void VG_BOUNDS
                         o.fptr[out_i] = fbase;
                     }
                 }
-                __syncwarp();
+                __syncwarp(gmask);
                 break;
                 }  // pass
-            } else if (!fail && lane == 0) {
+            } else if (!fail && gl == 0) {
                 o.vol[out_i] = 0;
                 o.area[out_i] = 0;
                 o.rfin[out_i] = 0.f;
@@ -1427,7 +1448,7 @@ __global__ void VG_BOUNDS
                 o.status[out_i] = (unsigned char)status;
                 o.fptr[out_i] = 0;
             }
-            if (fail && lane == 0) {
+            if (fail && gl == 0) {
                 if (tier == 0) {
                     const int slot = atomicAdd(o.retry_count, 1);
                     o.retry[slot] = i;
@@ -1440,7 +1461,7 @@ __global__ void VG_BOUNDS
                 o.vol[out_i] = 0; o.area[out_i] = 0; o.rfin[out_i] = 0.f;
                 o.fptr[out_i] = 0;
             }
-            if (pp.collect && lane == 0) {
+            if (pp.collect && gl == 0) {
                 o.w_tested[out_i] = S.cnt[0];
                 o.w_vtests[out_i] = S.cnt[1];
                 o.w_cuts[out_i] = S.cnt[2];
@@ -1449,16 +1470,16 @@ __global__ void VG_BOUNDS
                 o.w_fallback[out_i] = (unsigned char)src.fell_back;
                 o.w_pref[out_i] = S.cnt[5];
             }
-            __syncwarp();
+            __syncwarp(gmask);
         }
     }
 }
 
-template <typename T, int VPL, int MAXP, bool BATCH>
+template <typename T, int VPL, int MAXP, bool BATCH, int G>
 cudaError_t launch_t(const Store &s, const Out &o, const Params &p, const Offsets &off, unsigned *ticket,
                      int sm_count, int warps, const int *cells, int ncells, int tier, cudaStream_t st) {
-    const size_t smem = sizeof(Smem<T, VPL, MAXP>) * warps;
-    auto kfn = k_cells3<T, VPL, MAXP, BATCH>;
+    const size_t smem = sizeof(Smem<T, VPL, MAXP, G>) * warps * (32 / G);
+    auto kfn = k_cells3<T, VPL, MAXP, BATCH, G>;
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -1475,22 +1496,25 @@ cudaError_t launch_t(const Store &s, const Out &o, const Params &p, const Offset
 
 }  // namespace
 
+// Tier 0 (cells up to 64 vertices and 64 planes) runs two cells per warp
+// (16 lanes, 4 vertex slots per lane); the larger tiers one cell per warp.
 cudaError_t launch_cells3(const Store &s, const Out &o, const Params &p, const Offsets &off, int precision,
                           unsigned *ticket, int sm_count, int warps_per_cta, const int *cells, int ncells, int tier,
                           cudaStream_t st) {
     const int w = warps_per_cta > 0 ? min(warps_per_cta, VG_MAXT / 32) : VG_MAXT / 32;
     // the rare large cells (tiers 1, 2) always take the batched form
-    if (tier == 2) return launch_t<double, 16, 256, true>(s, o, p, off, ticket, sm_count, 1, cells, ncells, tier, st);
+    if (tier == 2)
+        return launch_t<double, 16, 256, true, 32>(s, o, p, off, ticket, sm_count, 1, cells, ncells, tier, st);
     if (tier == 1)
         return precision == VG_FP64
-                   ? launch_t<double, 4, 128, true>(s, o, p, off, ticket, sm_count, 2, cells, ncells, tier, st)
-                   : launch_t<float, 4, 128, true>(s, o, p, off, ticket, sm_count, 2, cells, ncells, tier, st);
+                   ? launch_t<double, 4, 128, true, 32>(s, o, p, off, ticket, sm_count, 2, cells, ncells, tier, st)
+                   : launch_t<float, 4, 128, true, 32>(s, o, p, off, ticket, sm_count, 2, cells, ncells, tier, st);
     const bool batch = s.nsys > 1;
     if (precision == VG_FP64)
-        return batch ? launch_t<double, 2, 64, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st)
-                     : launch_t<double, 2, 64, false>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
-    return batch ? launch_t<float, 2, 64, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st)
-                 : launch_t<float, 2, 64, false>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
+        return batch ? launch_t<double, VG_T0_VPL, 64, true, VG_T0_G>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st)
+                     : launch_t<double, VG_T0_VPL, 64, false, VG_T0_G>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
+    return batch ? launch_t<float, VG_T0_VPL, 64, true, VG_T0_G>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st)
+                 : launch_t<float, VG_T0_VPL, 64, false, VG_T0_G>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
 }
 
 }  // namespace vg
