@@ -1025,9 +1025,33 @@ __global__ void VG_BOUNDS
                         for (int w2 = 0; w2 < NW; w2++) { S.E[a][w2] = 0; S.E[b][w2] = 0; S.E[cc][w2] = 0; }
                     }
                 }
-                int tot2;
-                const int pk = gexcl_scan<G>(gmask, kc | (nc << 16), gl, tot2);
-                const int K = tot2 & 0xffff, N = tot2 >> 16;
+                int pk, K, N;
+                if constexpr (VPL <= 4) {
+                    // exclusive prefix by bit planes: independent ballots
+                    // instead of a chain of shuffles
+                    const unsigned lt = (1u << gl) - 1;
+                    int pkk = 0, pkn = 0;
+                    K = 0;
+                    N = 0;
+#pragma unroll
+                    for (int b = 0; (1 << b) <= VPL; b++) {
+                        const unsigned m = gballot<G>(gmask, gbase, (kc >> b) & 1);
+                        pkk += __popc(m & lt) << b;
+                        K += __popc(m) << b;
+                    }
+#pragma unroll
+                    for (int b = 0; (1 << b) <= 3 * VPL; b++) {
+                        const unsigned m = gballot<G>(gmask, gbase, (nc >> b) & 1);
+                        pkn += __popc(m & lt) << b;
+                        N += __popc(m) << b;
+                    }
+                    pk = pkk | (pkn << 16);
+                } else {
+                    int tot2;
+                    pk = gexcl_scan<G>(gmask, kc | (nc << 16), gl, tot2);
+                    K = tot2 & 0xffff;
+                    N = tot2 >> 16;
+                }
                 const int tot = K + N;
                 if (pp.collect && gl == 0) S.cnt[3] += N;
                 const int rc = tot > CAP ? 3 : (tot == 0 ? 2 : 1);
@@ -1397,7 +1421,16 @@ __global__ void VG_BOUNDS
                 if (anybad) {
                     fail = true;  // inconsistent topology: the FP64 big-cell tier redoes it
                 } else {
-                    bitonic<R, G>(key, gl, gmask);
+                    // one round of faces: one key per lane, a shorter network
+                    const bool one = F <= G;
+                    if (one) {
+                        unsigned long long k1[1] = {key[0]};
+                        bitonic<1, G>(k1, gl, gmask);
+                        key[0] = k1[0];
+                    } else {
+                        bitonic<R, G>(key, gl, gmask);
+                    }
+                    const int kstride = one ? 1 : R;
                     long long fbase = 0;
                     if (gl == 0) fbase = (long long)atomicAdd(o.fcount, (unsigned long long)nfk);
                     fbase = __shfl_sync(gmask, fbase, 0, G);
@@ -1405,8 +1438,8 @@ __global__ void VG_BOUNDS
                     if (!overflow) {
 #pragma unroll
                         for (int r = 0; r < R; r++) {
-                            const int gpos = gl * R + r;
-                            if (gpos < nfk) {
+                            const int gpos = gl * kstride + r;
+                            if (r < kstride && gpos < nfk) {
                                 const unsigned long long k = key[r];
                                 int2 ent;
                                 ent.x = (int)((long long)(k >> 32) - 8);
