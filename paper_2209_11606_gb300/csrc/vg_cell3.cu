@@ -725,13 +725,43 @@ __global__ void VG_BOUNDS
                                 bin[e2] = min(NBIN - 1, (int)((float)NBIN * t * sqrtf(t)));
                             }
                         }
-                        int pos0 = 0;
-                        for (int b = 0; b < NBIN; b++) {
+                        if constexpr (NBIN * (KMAX / G) == G) {
+                            // counting sort by bin, stable in (row, lane) order: the
+                            // count of every (bin, row) pair, one pair per lane, an
+                            // exclusive scan over them in (bin, row) order, and each
+                            // element's rank among its equals in its row
+                            int *hist = S.w.run.start;  // the run table is free again
+                            constexpr int ROWS = KMAX / G;
+                            hist[gl] = 0;  // G entries: one per (bin, row) pair
+                            __syncwarp(gmask);
+                            int rank[ROWS];
 #pragma unroll
-                            for (int e2 = 0; e2 < KMAX / G; e2++) {
-                                const unsigned m = gballot<G>(gmask, gbase, bin[e2] == b);
-                                if (bin[e2] == b) S.x.pf.slot[pos0 + __popc(m & ((1u << gl) - 1))] = e2 * G + gl;
-                                pos0 += __popc(m);
+                            for (int e2 = 0; e2 < ROWS; e2++) {
+                                const unsigned eq = __match_any_sync(gmask, bin[e2]);
+                                const unsigned eqg = G == 32 ? eq : (eq >> gbase);
+                                rank[e2] = __popc(eqg & ((1u << gl) - 1));
+                                // the lowest lane of each group of equals writes its count
+                                if (bin[e2] < NBIN && rank[e2] == 0) hist[bin[e2] * ROWS + e2] = __popc(eqg);
+                            }
+                            __syncwarp(gmask);
+                            const int mine = hist[gl];
+                            int htot;
+                            const int start = gexcl_scan<G>(gmask, mine, gl, htot);
+                            __syncwarp(gmask);
+                            hist[gl] = start;
+                            __syncwarp(gmask);
+#pragma unroll
+                            for (int e2 = 0; e2 < ROWS; e2++)
+                                if (bin[e2] < NBIN) S.x.pf.slot[hist[bin[e2] * ROWS + e2] + rank[e2]] = e2 * G + gl;
+                        } else {
+                            int pos0 = 0;
+                            for (int b = 0; b < NBIN; b++) {
+#pragma unroll
+                                for (int e2 = 0; e2 < KMAX / G; e2++) {
+                                    const unsigned m = gballot<G>(gmask, gbase, bin[e2] == b);
+                                    if (bin[e2] == b) S.x.pf.slot[pos0 + __popc(m & ((1u << gl) - 1))] = e2 * G + gl;
+                                    pos0 += __popc(m);
+                                }
                             }
                         }
                         src.mode = 0;
@@ -947,21 +977,31 @@ __global__ void VG_BOUNDS
 
                 // ================================= cut by the plane q.r = c
                 if (pp.collect && gl == 0) { S.cnt[0]++; S.cnt[1] += ntri; }
-                T tau;
-                if constexpr (F32) tau = tol32f * sqrtf(r2 * qq);
-                else tau = (T)(pp.tau_rel * g.s * sqrt((double)qq));
                 unsigned outm = 0, nearm = 0, onm = 0;
+                if constexpr (F32) {
+                    // |d| against the band tau * kappa, squared (no square root on
+                    // the critical path): out if d > band, near if |d| <= band
+                    const float t2 = tol32f * tol32f * r2 * qq;
 #pragma unroll
-                for (int s = 0; s < VPL; s++) {
-                    if ((rows >> s) & 1) {
-                        const T d = vx[s] * qx + vy[s] * qy + vz[s] * qz - c;
-                        T band = tau;
-                        if constexpr (F32) band = tau * kap[s];
-                        if (tri[s] != TRI_EMPTY) {
-                            if (d > band) outm |= 1u << s;
-                            else if (d >= -band) {
-                                if constexpr (F32) nearm |= 1u << s;
-                                else onm |= 1u << s;
+                    for (int s = 0; s < VPL; s++) {
+                        if ((rows >> s) & 1) {
+                            const float d = vx[s] * qx + vy[s] * qy + vz[s] * qz - c;
+                            const float b2 = t2 * (kap[s] * kap[s]);
+                            if (tri[s] != TRI_EMPTY) {
+                                if (d > 0.f && d * d > b2) outm |= 1u << s;
+                                else if (d * d <= b2) nearm |= 1u << s;
+                            }
+                        }
+                    }
+                } else {
+                    const T tau = (T)(pp.tau_rel * g.s * sqrt((double)qq));
+#pragma unroll
+                    for (int s = 0; s < VPL; s++) {
+                        if ((rows >> s) & 1) {
+                            const T d = vx[s] * qx + vy[s] * qy + vz[s] * qz - c;
+                            if (tri[s] != TRI_EMPTY) {
+                                if (d > tau) outm |= 1u << s;
+                                else if (d >= -tau) onm |= 1u << s;
                             }
                         }
                     }
