@@ -547,9 +547,29 @@ __global__ void VG_BOUNDS
             }
             int ntri = 8;        // vertices
             unsigned rows = 1;   // register slots (rows of G lanes) that hold any vertex
+            // planes in use: a counter hands out plane slots; the exact set of
+            // live planes (those some vertex still lies on) is rebuilt from the
+            // vertices only when the counter runs out and for the statistics
             unsigned long long live[NW];
 #pragma unroll
             for (int w2 = 0; w2 < NW; w2++) live[w2] = w2 == 0 ? 0x3full : 0ull;
+            int nplane = 6;
+            auto live_planes = [&]() {
+                unsigned long long lv[NW];
+#pragma unroll
+                for (int w2 = 0; w2 < NW; w2++) lv[w2] = 0;
+#pragma unroll
+                for (int s = 0; s < VPL; s++) {
+                    if (tri[s] != TRI_EMPTY) {
+                        const int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
+                        lv[a >> 6] |= 1ull << (a & 63);
+                        lv[b >> 6] |= 1ull << (b & 63);
+                        lv[cc >> 6] |= 1ull << (cc & 63);
+                    }
+                }
+#pragma unroll
+                for (int w2 = 0; w2 < NW; w2++) live[w2] = gor64(gmask, lv[w2]);
+            };
             T r2 = gmax<G>(gmask, gl < 8 ? vx[0] * vx[0] + vy[0] * vy[0] + vz[0] * vz[0] : (T)0);
             // bit 0 degenerate, 1 capacity/consistency failure, 2 empty, 3 duplicate point
             int flags = 0;
@@ -1024,9 +1044,14 @@ __global__ void VG_BOUNDS
                 if (__any_sync(gmask, onm)) flags |= 1;
                 if (pp.collect && gl == 0) S.cnt[2]++;
                 int np = -1;
+                if (nplane < MAXP) {
+                    np = nplane++;
+                } else {
+                    live_planes();
 #pragma unroll
-                for (int w2 = NW - 1; w2 >= 0; w2--)
-                    if (~live[w2]) np = w2 * 64 + __ffsll((long long)~live[w2]) - 1;
+                    for (int w2 = NW - 1; w2 >= 0; w2--)
+                        if (~live[w2]) np = w2 * 64 + __ffsll((long long)~live[w2]) - 1;
+                }
                 if (np < 0) { flags |= 2; break; }
                 // mark the directed edges of removed triangles
 #pragma unroll
@@ -1157,9 +1182,6 @@ __global__ void VG_BOUNDS
                 __syncwarp(gmask);
                 // kept vertices stay in place; free slots take the new ones in order
                 ntri = tot;
-                unsigned long long lv[NW];
-#pragma unroll
-                for (int w2 = 0; w2 < NW; w2++) lv[w2] = 0;
                 T rr = 0;
                 int rank0 = 0;
                 rows = 0;
@@ -1175,10 +1197,6 @@ __global__ void VG_BOUNDS
                         kap[s] = S.skap[rank];
                     }
                     if (tri[s] != TRI_EMPTY) {
-                        const int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
-                        lv[a >> 6] |= 1ull << (a & 63);
-                        lv[b >> 6] |= 1ull << (b & 63);
-                        lv[cc >> 6] |= 1ull << (cc & 63);
                         T q2 = vx[s] * vx[s] + vy[s] * vy[s] + vz[s] * vz[s];
                         if constexpr (F32) q2 *= 1.f + 4e-6f * kap[s];  // allowance for FP32 error
                         rr = rr > q2 ? rr : q2;
@@ -1188,14 +1206,13 @@ __global__ void VG_BOUNDS
                                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
                     if (__any_sync(gmask, tri[s] != TRI_EMPTY)) rows |= 1u << s;
                 }
-#pragma unroll
-                for (int w2 = 0; w2 < NW; w2++) live[w2] = gor64(gmask, lv[w2]);
                 r2 = gmax<G>(gmask, rr);
                 __syncwarp(gmask);
                 stop = stop2();
             }
 
             // ================================================= statistics
+            live_planes();
             bool degen = flags & 1;
             bool fail = flags & 2;
             int status = VG_CELL_OK;
