@@ -655,6 +655,7 @@ __global__ void VG_BOUNDS
                                     oxhi = hi;
                                 }
                             }
+#pragma unroll 1
                             for (int k = 0; k <= 2 * RGMAX; k++) {
                                 bool have = rowok && ox <= oxhi;
                                 int xa = 0, xb = 0, m0 = 0;
