@@ -238,6 +238,24 @@ __device__ __forceinline__ unsigned long long gor64(unsigned gmask, unsigned lon
     return ((unsigned long long)hi << 32) | lo;
 }
 
+// Bitonic sort of G keys, one per lane of a group, with the stage loops kept
+// rolled (the network runs once per cell; small code matters more).
+template <int G>
+__device__ __forceinline__ unsigned long long bitonic1(unsigned long long k, int gl, unsigned gmask) {
+#pragma unroll 1
+    for (int size = 2; size <= G; size <<= 1) {
+#pragma unroll 1
+        for (int j = size >> 1; j > 0; j >>= 1) {
+            const bool up = (gl & size) == 0;
+            const unsigned long long ot = __shfl_xor_sync(gmask, k, j, G);
+            const bool keep_min = ((gl & j) == 0) == up;
+            const unsigned long long mn = k < ot ? k : ot, mx = k < ot ? ot : k;
+            k = keep_min ? mn : mx;
+        }
+    }
+    return k;
+}
+
 // Bitonic sort of G*E keys held E per lane of a group (element g = gl*E + e).
 template <int E, int G>
 __device__ __forceinline__ void bitonic(unsigned long long (&k)[E], int gl, unsigned gmask) {
@@ -1482,9 +1500,7 @@ __global__ void VG_BOUNDS
                     // one round of faces: one key per lane, a shorter network
                     const bool one = F <= G;
                     if (one) {
-                        unsigned long long k1[1] = {key[0]};
-                        bitonic<1, G>(k1, gl, gmask);
-                        key[0] = k1[0];
+                        key[0] = bitonic1<G>(key[0], gl, gmask);
                     } else {
                         bitonic<R, G>(key, gl, gmask);
                     }
