@@ -1273,14 +1273,16 @@ __global__ void VG_BOUNDS
                 // distance from the particle gets a pass from FP64 vertices
                 for (int pass = 0; pass < 2; pass++) {
                 if (degen) {
-#pragma unroll
+                    // (vertices read back from the staging arrays: the loop stays rolled)
+#pragma unroll 1
                     for (int s = 0; s < VPL; s++) {
                         const int t = s * G + gl;
-                        if (tri[s] != TRI_EMPTY) {
+                        const unsigned tr = S.stri[t];
+                        if (tr != TRI_EMPTY) {
                             if constexpr (F32) {
-                                vertex64(&g, &st, &S.cc, S.pref, S.pimg, tri[s], S.x.dpos[t]);
+                                vertex64(&g, &st, &S.cc, S.pref, S.pimg, tr, S.x.dpos[t]);
                             } else {
-                                S.x.dpos[t][0] = vx[s]; S.x.dpos[t][1] = vy[s]; S.x.dpos[t][2] = vz[s];
+                                S.x.dpos[t][0] = S.sx[t]; S.x.dpos[t][1] = S.sy[t]; S.x.dpos[t][2] = S.sz[t];
                             }
                         }
                     }
@@ -1318,11 +1320,11 @@ __global__ void VG_BOUNDS
                         }
                     }
                     // every vertex enters itself in the walk tables of its faces
-#pragma unroll
+#pragma unroll 1
                     for (int s = 0; s < VPL; s++) {
                         const int t = s * G + gl;
-                        if (tri[s] != TRI_EMPTY) {
-                            const unsigned tr = tri[s];
+                        const unsigned tr = S.stri[t];
+                        if (tr != TRI_EMPTY) {
                             const int pp3[3] = {tri_a(tr), tri_b(tr), tri_c(tr)};
 #pragma unroll
                             for (int k3 = 0; k3 < 3; k3++) {
@@ -1475,10 +1477,10 @@ __global__ void VG_BOUNDS
                     // distinct vertices: a vertex counts if no earlier one coincides
                     const double eps = pp.merge_rel * g.s, eps2 = eps * eps;
                     int cntv = 0;
-#pragma unroll
+#pragma unroll 1
                     for (int s = 0; s < VPL; s++) {
                         const int t = s * G + gl;
-                        if (tri[s] != TRI_EMPTY) {
+                        if (S.stri[t] != TRI_EMPTY) {
                             bool first = true;
                             for (int q = 0; q < t && first; q++) {
                                 if (S.stri[q] == TRI_EMPTY) continue;
