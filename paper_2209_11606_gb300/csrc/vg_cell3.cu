@@ -640,6 +640,7 @@ __global__ void VG_BOUNDS
                     bool give_up = false;
                     float rho2 = 0.f;
                     int rg0 = 0, rg1 = 0, rg2 = 0;
+#pragma unroll 1
                     for (int attempt = 0; attempt < 6; attempt++) {
                         rho2 = rho * rho;
                         rg0 = (int)ceilf(rho / g.hf[0]);
@@ -652,6 +653,7 @@ __global__ void VG_BOUNDS
                         const int wy = 2 * rg1 + 1, nrows = wy * (2 * rg2 + 1);
                         const int bx = S.cc.b[0];
                         int nrun = 0, npart = 0;
+#pragma unroll 1
                         for (int r0 = 0; r0 < nrows; r0 += G) {
                             const int r = r0 + gl;
                             int oy = 0, oz = 0, krow = 0, ox = 0, oxhi = -1;
@@ -713,6 +715,7 @@ __global__ void VG_BOUNDS
                         if (nrun > NRUN) { give_up = true; break; }
                         __syncwarp(gmask);
                         // 2. all particles of all runs, G at a time
+#pragma unroll 1
                         for (int v0 = 0; v0 < npart; v0 += G) {
                             const int v = v0 + gl;
                             bool keep = false;
@@ -1301,6 +1304,7 @@ __global__ void VG_BOUNDS
                 unsigned long long key[R];
 #pragma unroll
                 for (int r = 0; r < R; r++) key[r] = ~0ull;
+#pragma unroll 1
                 for (int rnd = 0; rnd * G < F; rnd++) {
                     const int f = rnd * G + gl;
                     // plane of face f: the f-th set bit of the live mask
@@ -1354,6 +1358,7 @@ __global__ void VG_BOUNDS
                         if (!degen) {
                             const T u0x = S.sx[t0] - rx, u0y = S.sy[t0] - ry, u0z = S.sz[t0] - rz;
                             T fv = 0, fcx = 0, fcy = 0, fcz = 0, fax = 0, fay = 0, faz = 0;
+#pragma unroll 1
                             for (steps = 0; steps < CAP; steps++) {
                                 const unsigned tr = S.stri[cur];
                                 const int p0 = tri_a(tr), p1 = tri_b(tr), p2 = tri_c(tr);
@@ -1391,6 +1396,7 @@ __global__ void VG_BOUNDS
                             double px = fx, py = fy, pz = fz, per = 0, fv = 0, fcx = 0, fcy = 0, fcz = 0;
                             double fax = 0, fay = 0, faz = 0;
                             int distinct = 1;
+#pragma unroll 1
                             for (steps = 0; steps < CAP; steps++) {
                                 const unsigned tr = S.stri[cur];
                                 const int p0 = tri_a(tr), p1 = tri_b(tr), p2 = tri_c(tr);
