@@ -256,6 +256,32 @@ __device__ __forceinline__ unsigned long long bitonic1(unsigned long long k, int
     return k;
 }
 
+// Bitonic sort of 2G keys, two per lane (element g = 2 gl + e), stage loops
+// rolled.
+template <int G>
+__device__ __forceinline__ void bitonic2(unsigned long long &k0, unsigned long long &k1, int gl, unsigned gmask) {
+#pragma unroll 1
+    for (int size = 2; size <= 2 * G; size <<= 1) {
+#pragma unroll 1
+        for (int j = size >> 1; j > 0; j >>= 1) {
+            const int g0 = 2 * gl;
+            if (j == 1) {
+                const bool up = (g0 & size) == 0;
+                const bool sw = up ? (k0 > k1) : (k0 < k1);
+                if (sw) { const unsigned long long t = k0; k0 = k1; k1 = t; }
+            } else {
+                const int lm = j >> 1;
+                const unsigned long long o0 = __shfl_xor_sync(gmask, k0, lm, G);
+                const unsigned long long o1 = __shfl_xor_sync(gmask, k1, lm, G);
+                const bool up0 = (g0 & size) == 0, up1 = ((g0 + 1) & size) == 0;
+                const bool km0 = ((g0 & j) == 0) == up0, km1 = (((g0 + 1) & j) == 0) == up1;
+                k0 = km0 ? (k0 < o0 ? k0 : o0) : (k0 < o0 ? o0 : k0);
+                k1 = km1 ? (k1 < o1 ? k1 : o1) : (k1 < o1 ? o1 : k1);
+            }
+        }
+    }
+}
+
 // Bitonic sort of G*E keys held E per lane of a group (element g = gl*E + e).
 template <int E, int G>
 __device__ __forceinline__ void bitonic(unsigned long long (&k)[E], int gl, unsigned gmask) {
@@ -1509,6 +1535,8 @@ __global__ void VG_BOUNDS
                     const bool one = F <= G;
                     if (one) {
                         key[0] = bitonic1<G>(key[0], gl, gmask);
+                    } else if constexpr (R == 2) {
+                        bitonic2<G>(key[0], key[1], gl, gmask);
                     } else {
                         bitonic<R, G>(key, gl, gmask);
                     }
