@@ -65,6 +65,8 @@ constexpr int MAX_SHELL_EXTRA = 4;
 #define VG_T0_G 32
 #endif
 #define VG_T0_VPL (64 / VG_T0_G)
+// branch that almost never runs: keep its code out of the common path
+#define VG_RARE(c) __builtin_expect(!!(c), 0)
 #ifdef VG_MAXREG
 #define VG_BOUNDS __maxnreg__(VG_MAXREG)
 #else
@@ -1033,7 +1035,7 @@ __global__ void VG_BOUNDS
                 const T qx = cq4.x, qy = cq4.y, qz = cq4.z, qq = cq4.w;
                 const int ref = cr.x, img = cr.y;
                 if (qq >= stop) continue;
-                if (qq < (T)1e-30) { flags |= 8; continue; }
+                if (VG_RARE(qq < (T)1e-30)) { flags |= 8; continue; }
                 T c;
                 if (st.radical) {
                     const T rj = S.cbrj[srcl];
@@ -1044,7 +1046,7 @@ __global__ void VG_BOUNDS
                 }
 
                 // ================================= cut by the plane q.r = c
-                if (pp.collect && gl == 0) { S.cnt[0]++; S.cnt[1] += ntri; }
+                if (VG_RARE(pp.collect) && gl == 0) { S.cnt[0]++; S.cnt[1] += ntri; }
                 unsigned outm = 0, nearm = 0, onm = 0;
                 if constexpr (F32) {
                     // |d| against the band tau * kappa, squared (no square root on
@@ -1075,7 +1077,7 @@ __global__ void VG_BOUNDS
                     }
                 }
                 if constexpr (F32) {
-                    if (__any_sync(gmask, nearm)) {
+                    if (VG_RARE(__any_sync(gmask, nearm))) {
                         if (pp.collect && gl == 0) S.cnt[4]++;
 #pragma unroll
                         for (int s = 0; s < VPL; s++) {
@@ -1090,7 +1092,7 @@ __global__ void VG_BOUNDS
                 }
                 if (!__any_sync(gmask, outm)) continue;
                 if (__any_sync(gmask, onm)) flags |= 1;
-                if (pp.collect && gl == 0) S.cnt[2]++;
+                if (VG_RARE(pp.collect) && gl == 0) S.cnt[2]++;
                 int np = -1;
                 if (nplane < MAXP) {
                     np = nplane++;
@@ -1100,7 +1102,7 @@ __global__ void VG_BOUNDS
                     for (int w2 = NW - 1; w2 >= 0; w2--)
                         if (~live[w2]) np = w2 * 64 + __ffsll((long long)~live[w2]) - 1;
                 }
-                if (np < 0) { flags |= 2; break; }
+                if (VG_RARE(np < 0)) { flags |= 2; break; }
                 // mark the directed edges of removed triangles
 #pragma unroll
                 for (int s = 0; s < VPL; s++) {
@@ -1166,9 +1168,9 @@ __global__ void VG_BOUNDS
                     N = tot2 >> 16;
                 }
                 const int tot = K + N;
-                if (pp.collect && gl == 0) S.cnt[3] += N;
+                if (VG_RARE(pp.collect) && gl == 0) S.cnt[3] += N;
                 const int rc = tot > CAP ? 3 : (tot == 0 ? 2 : 1);
-                if (rc != 1) {
+                if (VG_RARE(rc != 1)) {
                     flags |= rc == 2 ? 4 : 2;
                     break;
                 }
@@ -1204,7 +1206,7 @@ __global__ void VG_BOUNDS
                         const float m123 = (P1.x * P1.x + P1.y * P1.y + P1.z * P1.z) *
                                            (P2.x * P2.x + P2.y * P2.y + P2.z * P2.z) * qq;
                         const float d2 = det * det;
-                        if (!(d2 * KAP_MAX2 >= m123)) {
+                        if (VG_RARE(!(d2 * KAP_MAX2 >= m123))) {
                             const float3 v = solve_new64(&g, &st, &S.cc, S.pref, S.pimg, x, y, ref, img);
                             nx = v.x; ny = v.y; nz = v.z;
                             solved = true;
