@@ -179,6 +179,35 @@ __device__ __forceinline__ bool may_cut(const float4 *v4, float qx, float qy, fl
     return m;
 }
 
+// prefetch bucket b holds the distances t * rho with t^(3/2) in [b, b+1) / NBIN:
+// its lower bound is t = (b / NBIN)^(2/3)
+__constant__ float bucket_t[NBIN] = {0.f, 0.25f, 0.396850263f, 0.520020956f,
+                                     0.629960525f, 0.731004435f, 0.825481812f, 0.914826428f};
+static_assert(NBIN == 8, "bucket_t holds NBIN = 8 bounds");
+
+// Hardware approximations (PTX rcp/sqrt/lg2/ex2 .approx, a few ulps) where
+// a value only needs a few ulps: the FP32 band is tol32 = 1e-5 (about 80
+// ulps) wide, and the prefetch radius and its bucket bounds are heuristics
+// or carry relative margins of 1e-4.
+__device__ __forceinline__ float rcp_a(float x) {
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt_a(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+// x^(1/3) = 2^(log2(x) / 3), x > 0
+__device__ __forceinline__ float cbrt_a(float x) {
+    float l, r;
+    asm("lg2.approx.f32 %0, %1;" : "=f"(l) : "f"(x));
+    l *= (1.f / 3.f);
+    asm("ex2.approx.f32 %0, %1;" : "=f"(r) : "f"(l));
+    return r;
+}
+
 __device__ __forceinline__ int floordiv(int a, int b) {
     int q = a / b;
     if ((a % b != 0) && ((a < 0) != (b < 0))) q--;
@@ -662,8 +691,8 @@ __global__ void VG_BOUNDS
                     }
                     n27 = __reduce_add_sync(gmask, n27);
                     v27 = __reduce_add_sync(gmask, v27);
-                    const float dens = (float)max(n27, 1) / ((float)max(v27, 1) * g.hf[0] * g.hf[1] * g.hf[2]);
-                    float rho = cbrtf(3.f * kt / (4.f * 3.14159265f * dens));
+                    const float dens = (float)max(n27, 1) * rcp_a((float)max(v27, 1) * g.hf[0] * g.hf[1] * g.hf[2]);
+                    float rho = cbrt_a(3.f * kt * rcp_a(4.f * 3.14159265f * dens));
                     int count = 0;
                     bool give_up = false;
                     float rho2 = 0.f;
@@ -671,9 +700,11 @@ __global__ void VG_BOUNDS
 #pragma unroll 1
                     for (int attempt = 0; attempt < 6; attempt++) {
                         rho2 = rho * rho;
-                        rg0 = (int)ceilf(rho / g.hf[0]);
-                        rg1 = (int)ceilf(rho / g.hf[1]);
-                        rg2 = (int)ceilf(rho / g.hf[2]);
+                        // block reach, rounded up with a margin over the approximate quotient
+                        const float rm = rho * 1.0001f;
+                        rg0 = (int)ceilf(rm * rcp_a(g.hf[0]));
+                        rg1 = (int)ceilf(rm * rcp_a(g.hf[1]));
+                        rg2 = (int)ceilf(rm * rcp_a(g.hf[2]));
                         count = 0;
                         if (rg0 > RGMAX || rg1 > RGMAX || rg2 > RGMAX) { give_up = true; break; }
                         // 1. runs of contiguous blocks: rows along x (fixed oy, oz)
@@ -778,13 +809,13 @@ __global__ void VG_BOUNDS
                         }
                         __syncwarp(gmask);
                         if (count <= KMAX) break;
-                        rho *= 0.8f * cbrtf((float)KMAX / (float)count);
+                        rho *= 0.8f * cbrt_a((float)KMAX * rcp_a((float)count));
                     }
                     if (!give_up && count <= KMAX) {
                         // order by radial bucket: NBIN shells of equal volume inside
                         // rho (about equal counts); inside a bucket the gather order,
                         // which is deterministic, is kept
-                        const float irho2 = 1.f / rho2;
+                        const float irho2 = rcp_a(rho2);
                         int bin[KMAX / G];
 #pragma unroll
                         for (int e2 = 0; e2 < KMAX / G; e2++) {
@@ -792,7 +823,7 @@ __global__ void VG_BOUNDS
                             bin[e2] = NBIN;
                             if (slot < count) {
                                 const float t = fminf(S.x.pf.q[slot].w * irho2, 1.f);
-                                bin[e2] = min(NBIN - 1, (int)((float)NBIN * t * sqrtf(t)));
+                                bin[e2] = min(NBIN - 1, (int)((float)NBIN * t * sqrt_a(t)));
                             }
                         }
                         if constexpr (NBIN * (KMAX / G) == G) {
@@ -879,7 +910,7 @@ __global__ void VG_BOUNDS
                             if constexpr (F32) {
                                 if (filt && ok && q4.w >= 1e-30f) {
                                     const float cc = st.radical ? 0.5f * (q4.w + rp32 * rp32 - crj * crj) : 0.5f * q4.w;
-                                    ok = may_cut<CAP>(S.v4, q4.x, q4.y, q4.z, cc, tol32f * sqrtf(r2 * q4.w));
+                                    ok = may_cut<CAP>(S.v4, q4.x, q4.y, q4.z, cc, tol32f * sqrt_a(r2 * q4.w));
                                 }
                             }
                         }
@@ -890,10 +921,10 @@ __global__ void VG_BOUNDS
                         // bound, every later entry lies beyond it too
                         const int last = min(count - u, G) - 1;
                         const float qlast = __shfl_sync(gmask, (float)cqq, last, G);  // this batch's gl value
-                        const float t = fminf(qlast / src.rho2, 1.f);
-                        const int bl = min(NBIN - 1, (int)((float)NBIN * t * sqrtf(t)));
-                        const float f = (float)bl / (float)NBIN;
-                        const float lb2 = src.rho2 * cbrtf(f * f) * 0.9999f;  // margin for rounding
+                        const float t = fminf(qlast * rcp_a(src.rho2), 1.f);
+                        const int bl = min(NBIN - 1, (int)((float)NBIN * t * sqrt_a(t)));
+                        // bucket bl starts at t = (bl / NBIN)^(2/3)
+                        const float lb2 = src.rho2 * bucket_t[bl] * 0.9999f;  // margin for rounding
                         src.u = ((T)lb2 >= stop) ? count : u + G;
                         continue;
                     }
@@ -933,7 +964,7 @@ __global__ void VG_BOUNDS
                             if constexpr (F32) {
                                 if (filt && ok && cqq >= 1e-30f) {
                                     const float cc = st.radical ? 0.5f * (cqq + rp32 * rp32 - crj * crj) : 0.5f * cqq;
-                                    ok = may_cut<CAP>(S.v4, cqx, cqy, cqz, cc, tol32f * sqrtf(r2 * cqq));
+                                    ok = may_cut<CAP>(S.v4, cqx, cqy, cqz, cc, tol32f * sqrt_a(r2 * cqq));
                                 }
                             }
                             S.cbq[gl] = mk4<T>(cqx, cqy, cqz, cqq);
@@ -1200,22 +1231,26 @@ __global__ void VG_BOUNDS
                             x12z = P1.x * P2.y - P1.y * P2.x;
                     const T det = P1.x * x23x + P1.y * x23y + P1.z * x23z;
                     T nx, ny, nz;
-                    float kp = 1.f;
+                    float kp = 1.f, m123 = 0.f;
                     bool solved = false;
                     if constexpr (F32) {
-                        const float m123 = (P1.x * P1.x + P1.y * P1.y + P1.z * P1.z) *
+                        m123 = (P1.x * P1.x + P1.y * P1.y + P1.z * P1.z) *
                                            (P2.x * P2.x + P2.y * P2.y + P2.z * P2.z) * qq;
                         const float d2 = det * det;
                         if (VG_RARE(!(d2 * KAP_MAX2 >= m123))) {
                             const float3 v = solve_new64(&g, &st, &S.cc, S.pref, S.pimg, x, y, ref, img);
                             nx = v.x; ny = v.y; nz = v.z;
                             solved = true;
-                        } else {
-                            kp = fmaxf(1.f, sqrtf(m123) / (fabsf(det) * KAP0));
                         }
                     }
                     if (!solved) {
-                        const T id = (T)1 / det;
+                        T id;
+                        if constexpr (F32) {
+                            id = rcp_a(det);
+                            kp = fmaxf(1.f, sqrt_a(m123) * fabsf(id) * (1.f / KAP0));
+                        } else {
+                            id = (T)1 / det;
+                        }
                         nx = (P1.w * x23x + P2.w * x31x + c * x12x) * id;
                         ny = (P1.w * x23y + P2.w * x31y + c * x12y) * id;
                         nz = (P1.w * x23z + P2.w * x31z + c * x12z) * id;
