@@ -213,6 +213,14 @@ __device__ __forceinline__ int floordiv(int a, int b) {
     if ((a % b != 0) && ((a < 0) != (b < 0))) q--;
     return q;
 }
+// floor(a / b) for b > 0, without a division when a lies within one period
+// of [0, b) (block offsets of the prefetch and of the walk's near shells)
+__device__ __forceinline__ int floordiv_near(int a, int b) {
+    if ((unsigned)a < (unsigned)b) return 0;
+    if (a < 0 && a >= -b) return -1;
+    if (a >= b && a < 2 * b) return 1;
+    return floordiv(a, b);
+}
 __device__ __forceinline__ int tri_a(unsigned t) { return t & 0xff; }
 __device__ __forceinline__ int tri_b(unsigned t) { return (t >> 8) & 0xff; }
 __device__ __forceinline__ int tri_c(unsigned t) { return (t >> 16) & 0xff; }
@@ -469,7 +477,7 @@ __device__ __forceinline__ bool resolve(const Grid &g, long long base, const int
         int ta = b[a] + o[a];
         m[a] = 0;
         if (g.per[a]) {
-            m[a] = floordiv(ta, g.nb[a]);
+            m[a] = floordiv_near(ta, g.nb[a]);
             ta -= m[a] * g.nb[a];
         } else if (ta < 0 || ta >= g.nb[a]) {
             return false;
@@ -715,7 +723,7 @@ __global__ void VG_BOUNDS
 #pragma unroll 1
                         for (int r0 = 0; r0 < nrows; r0 += G) {
                             const int r = r0 + gl;
-                            int oy = 0, oz = 0, krow = 0, ox = 0, oxhi = -1;
+                            int oy = 0, oz = 0, krow = 0, ox = 0, oxhi = -1, myz = 0;
                             bool rowok = false;
                             if (r < nrows) {
                                 oy = r % wy - rg1;
@@ -723,6 +731,8 @@ __global__ void VG_BOUNDS
                                 int kk, mx, my, mz;
                                 rowok = row_gap2(g, o1, o2, oy, oz) < rho2 &&
                                         resolve(g, SY.blk_base, S.cc.b, 0, oy, oz, kk, mx, my, mz);
+                                // image shifts are at most RGMAX blocks: 4 bits each
+                                myz = ((my + 8) << 20) | ((mz + 8) << 24);
                                 krow = kk - bx;
                                 if (rowok) {
                                     // the blocks of the row within rho: an interval around 0
@@ -741,7 +751,7 @@ __global__ void VG_BOUNDS
                                 if (have) {
                                     const int tx = bx + ox;
                                     if (g.per[0]) {
-                                        m0 = floordiv(tx, g.nb[0]);
+                                        m0 = floordiv_near(tx, g.nb[0]);
                                         xa = tx - m0 * g.nb[0];
                                         xb = min(g.nb[0] - 1, xa + (oxhi - ox));
                                     } else {
@@ -764,7 +774,8 @@ __global__ void VG_BOUNDS
                                     S.w.run.j0[slot] = j0r;
                                     // x offset of a particle = oxb + its block index
                                     S.w.run.oxb[slot] = (ox - xa) - krow;
-                                    S.w.run.oyz[slot] = (oy + 64) | ((oz + 64) << 8);
+                                    // offsets (oy, oz) and the run's image shift (m0, my, mz)
+                                    S.w.run.oyz[slot] = (oy + 64) | ((oz + 64) << 8) | ((m0 + 8) << 16) | myz;
                                 }
                                 nrun += __popc(hb);
                                 npart += ltot;
@@ -793,11 +804,7 @@ __global__ void VG_BOUNDS
                                 const float4 pj = __ldg(&st.p32[j]);
                                 cand32(g, o0, o1, o2, pj, oxj, oy, oz, qx, qy, qz, qq);
                                 keep = qq < rho2 && !(j == i && oxj == 0 && oy == 0 && oz == 0);
-                                if (keep) {
-                                    int kk, mx, my, mz;
-                                    resolve(g, SY.blk_base, S.cc.b, oxj, oy, oz, kk, mx, my, mz);
-                                    img = pack_img(mx, my, mz);
-                                }
+                                img = pack_img(((oyz >> 16) & 15) - 8, ((oyz >> 20) & 15) - 8, ((oyz >> 24) & 15) - 8);
                             }
                             const unsigned bal = gballot<G>(gmask, gbase, keep);
                             const int pos = count + __popc(bal & ((1u << gl) - 1));
@@ -1449,7 +1456,8 @@ __global__ void VG_BOUNDS
                             }
                             vol += (double)fv;
                             cx += fcx; cy += fcy; cz += fcz;
-                            farea = (T)0.5 * sqrt(fax * fax + fay * fay + faz * faz);
+                            if constexpr (F32) farea = 0.5f * sqrt_a(fax * fax + fay * fay + faz * faz);
+                            else farea = (T)0.5 * sqrt(fax * fax + fay * fay + faz * faz);
                             order = steps;
                         } else {
                             // degenerate cell: FP64 vertices, coincident ones merged
@@ -1533,8 +1541,8 @@ __global__ void VG_BOUNDS
                 if (F32 && pass == 0 && !degen && !anybad) {
                     // FP32 vertex error ~ 3e-7 max(R, h) (h: the block side that
                     // bounds the stored FP32 offsets) relative to the thickness 3V/A
-                    const float thick = (float)vol / (2.f * (float)area);
-                    const float scale = fmaxf(sqrtf((float)r2), fmaxf(g.hf[0], fmaxf(g.hf[1], g.hf[2])));
+                    const float thick = (float)vol * rcp_a(2.f * (float)area);
+                    const float scale = fmaxf(sqrt_a((float)r2), fmaxf(g.hf[0], fmaxf(g.hf[1], g.hf[2])));
                     if (!(thick * 10.f > scale)) {
                         degen = true;
                         __syncwarp(gmask);
@@ -1601,7 +1609,7 @@ __global__ void VG_BOUNDS
                     if (gl == 0) {
                         const double v6 = vol;
                         o.vol[out_i] = v6 * (1.0 / 6.0);
-                        if constexpr (F32) o.rfin[out_i] = sqrtf(r2);
+                        if constexpr (F32) o.rfin[out_i] = sqrt_a(r2);
                         else o.rfin[out_i] = (float)sqrt(r2);
                         o.area[out_i] = (double)area;
                         // centroid = sum det (u0 + a + b) / (4 sum det)
