@@ -35,11 +35,6 @@ template <> struct P2<double> { using t = D4; };
 
 __device__ __forceinline__ int imgc2(int img, int a) { return (int)(signed char)((img >> (8 * a)) & 0xff); }
 __device__ __forceinline__ int pack2(int mx, int my) { return (mx & 0xff) | ((my & 0xff) << 8); }
-__device__ __forceinline__ int fdiv2(int a, int b) {
-    int q = a / b;
-    if ((a % b != 0) && ((a < 0) != (b < 0))) q--;
-    return q;
-}
 __device__ __forceinline__ int la(unsigned v) { return v & 0xff; }
 __device__ __forceinline__ int lb(unsigned v) { return (v >> 8) & 0xff; }
 __device__ __forceinline__ unsigned mkv(int a, int b) { return (unsigned)a | ((unsigned)b << 8); }
@@ -179,10 +174,17 @@ __device__ __noinline__ int classify64_2(const Grid *g, const Store *st, const C
 template <typename T>
 __device__ __forceinline__ void meet(typename P2<T>::t A, T bx, T by, T bc, T &x, T &y, float &kap) {
     const T det = A.x * by - A.y * bx;
-    x = (A.z * by - bc * A.y) / det;
-    y = (A.x * bc - bx * A.z) / det;
     const float m = (float)((A.x * A.x + A.y * A.y) * (bx * bx + by * by));
-    kap = fmaxf(1.f, sqrtf(m) / (fabsf((float)det) * KAP0_2));
+    if constexpr (sizeof(T) == 4) {
+        const float id = rcp_a(det);
+        x = (A.z * by - bc * A.y) * id;
+        y = (A.x * bc - bx * A.z) * id;
+        kap = fmaxf(1.f, sqrt_a(m) * fabsf(id) * (1.f / KAP0_2));
+    } else {
+        x = (A.z * by - bc * A.y) / det;
+        y = (A.x * bc - bx * A.z) / det;
+        kap = fmaxf(1.f, sqrtf(m) / (fabsf((float)det) * KAP0_2));
+    }
 }
 
 template <typename T, int G, int CAP, bool BATCH>
@@ -343,9 +345,9 @@ __global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Store st
             }
             // the block: resolve, distance bound, particles
             int t0 = b0 + ox, t1 = b1 + oy, m0 = 0, m1 = 0;
-            if (g.per[0]) { m0 = fdiv2(t0, g.nb[0]); t0 -= m0 * g.nb[0]; }
+            if (g.per[0]) { m0 = floordiv_near(t0, g.nb[0]); t0 -= m0 * g.nb[0]; }
             else if (t0 < 0 || t0 >= g.nb[0]) continue;
-            if (g.per[1]) { m1 = fdiv2(t1, g.nb[1]); t1 -= m1 * g.nb[1]; }
+            if (g.per[1]) { m1 = floordiv_near(t1, g.nb[1]); t1 -= m1 * g.nb[1]; }
             else if (t1 < 0 || t1 >= g.nb[1]) continue;
             {
                 float lo0 = (float)ox * g.hf[0] - o0, lo1 = (float)oy * g.hf[1] - o1;
@@ -389,7 +391,7 @@ __global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Store st
                     // ---------------------------------------- cut by q.r = c
                     if (pp.collect && gl == 0) { S.cnt[0]++; S.cnt[1] += nvert; }
                     T tau;
-                    if constexpr (F32) tau = tol32f * sqrtf(r2 * cq);
+                    if constexpr (F32) tau = tol32f * sqrt_a(r2 * cq);
                     else tau = (T)(tau_rel_s * sqrt((double)cq));
                     unsigned outm = 0, nearm = 0, onm = 0;
 #pragma unroll
@@ -574,7 +576,9 @@ __global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Store st
                     area += (double)cr;
                     cxs += (ax + bx) * cr;
                     cys += (ay + by) * cr;
-                    per += sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
+                    const T l2 = (bx - ax) * (bx - ax) + (by - ay) * (by - ay);
+                    if constexpr (F32) per += sqrt_a(l2);
+                    else per += sqrt(l2);
                 } else {
                     const double ax = S.dpos[s * G + gl][0] - (double)rx, ay = S.dpos[s * G + gl][1] - (double)ry;
                     const double bx = S.dpos[nx][0] - (double)rx, by = S.dpos[nx][1] - (double)ry;
@@ -604,8 +608,8 @@ __global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Store st
             if (F32 && pass == 0 && !degen && !anybad) {
                 // FP32 vertex error ~ 3e-7 max(R, h) (h: the block side that
                 // bounds the stored FP32 offsets) relative to the thickness 2A/P
-                const float thick = (float)area / (float)per;
-                const float scale = fmaxf(sqrtf((float)r2), fmaxf(g.hf[0], g.hf[1]));
+                const float thick = (float)area * rcp_a((float)per);
+                const float scale = fmaxf(sqrt_a((float)r2), fmaxf(g.hf[0], g.hf[1]));
                 if (!(thick * 10.f > scale)) {
                     degen = true;
                     __syncwarp(gmask);

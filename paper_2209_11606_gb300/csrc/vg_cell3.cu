@@ -185,42 +185,6 @@ __constant__ float bucket_t[NBIN] = {0.f, 0.25f, 0.396850263f, 0.520020956f,
                                      0.629960525f, 0.731004435f, 0.825481812f, 0.914826428f};
 static_assert(NBIN == 8, "bucket_t holds NBIN = 8 bounds");
 
-// Hardware approximations (PTX rcp/sqrt/lg2/ex2 .approx, a few ulps) where
-// a value only needs a few ulps: the FP32 band is tol32 = 1e-5 (about 80
-// ulps) wide, and the prefetch radius and its bucket bounds are heuristics
-// or carry relative margins of 1e-4.
-__device__ __forceinline__ float rcp_a(float x) {
-    float r;
-    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ float sqrt_a(float x) {
-    float r;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-// x^(1/3) = 2^(log2(x) / 3), x > 0
-__device__ __forceinline__ float cbrt_a(float x) {
-    float l, r;
-    asm("lg2.approx.f32 %0, %1;" : "=f"(l) : "f"(x));
-    l *= (1.f / 3.f);
-    asm("ex2.approx.f32 %0, %1;" : "=f"(r) : "f"(l));
-    return r;
-}
-
-__device__ __forceinline__ int floordiv(int a, int b) {
-    int q = a / b;
-    if ((a % b != 0) && ((a < 0) != (b < 0))) q--;
-    return q;
-}
-// floor(a / b) for b > 0, without a division when a lies within one period
-// of [0, b) (block offsets of the prefetch and of the walk's near shells)
-__device__ __forceinline__ int floordiv_near(int a, int b) {
-    if ((unsigned)a < (unsigned)b) return 0;
-    if (a < 0 && a >= -b) return -1;
-    if (a >= b && a < 2 * b) return 1;
-    return floordiv(a, b);
-}
 __device__ __forceinline__ int tri_a(unsigned t) { return t & 0xff; }
 __device__ __forceinline__ int tri_b(unsigned t) { return (t >> 8) & 0xff; }
 __device__ __forceinline__ int tri_c(unsigned t) { return (t >> 16) & 0xff; }
