@@ -124,7 +124,7 @@ struct Smem {
     T sx[G * VPL], sy[G * VPL], sz[G * VPL];
     float skap[G * VPL];
     float4 v4[G * VPL];                     // FP32 form: the cell's vertices (x, y, z, kappa); free slots 0
-    unsigned long long E[MAXP][MAXP / 64];  // removed directed edges of one cut
+    unsigned E[MAXP][MAXP / 32];  // removed directed edges of one cut (32-bit words: native shared atomics)
     union {
         FT ftab[G][MAXP];              // face walk tables, one row per face of a round
         struct {
@@ -473,7 +473,7 @@ __global__ void VG_BOUNDS
     S_t &S = reinterpret_cast<S_t *>(smem_raw)[warp * (32 / G) + lane / G];
     Src &src = S.src;
     // the edge matrix starts clear; every cut leaves it clear
-    for (int u = gl; u < MAXP * NW; u += G) (&S.E[0][0])[u] = 0ull;
+    for (int u = gl; u < MAXP * (MAXP / 32); u += G) (&S.E[0][0])[u] = 0u;
     if (gl == 0) S.sys_id = -1;
     __syncwarp(gmask);
     const Sys &SY = sys_ref<BATCH>(st, S.sysc);
@@ -1110,9 +1110,9 @@ __global__ void VG_BOUNDS
                 for (int s = 0; s < VPL; s++) {
                     if (outm & (1u << s)) {
                         const int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
-                        atomicOr(&S.E[a][b >> 6], 1ull << (b & 63));
-                        atomicOr(&S.E[b][cc >> 6], 1ull << (cc & 63));
-                        atomicOr(&S.E[cc][a >> 6], 1ull << (a & 63));
+                        atomicOr(&S.E[a][b >> 5], 1u << (b & 31));
+                        atomicOr(&S.E[b][cc >> 5], 1u << (cc & 31));
+                        atomicOr(&S.E[cc][a >> 5], 1u << (a & 31));
                     }
                 }
                 __syncwarp(gmask);
@@ -1124,22 +1124,23 @@ __global__ void VG_BOUNDS
                     if (outm & (1u << s)) {
                         const int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
                         // edge (x,y) borders the kept part iff its twin (y,x) was not removed
-                        if (!((S.E[b][a >> 6] >> (a & 63)) & 1)) bnd[s] |= 1;
-                        if (!((S.E[cc][b >> 6] >> (b & 63)) & 1)) bnd[s] |= 2;
-                        if (!((S.E[a][cc >> 6] >> (cc & 63)) & 1)) bnd[s] |= 4;
+                        if (!((S.E[b][a >> 5] >> (a & 31)) & 1)) bnd[s] |= 1;
+                        if (!((S.E[cc][b >> 5] >> (b & 31)) & 1)) bnd[s] |= 2;
+                        if (!((S.E[a][cc >> 5] >> (cc & 31)) & 1)) bnd[s] |= 4;
                         nc += __popc(bnd[s]);
                     } else if (tri[s] != TRI_EMPTY) {
                         kc++;
                     }
                 }
                 __syncwarp(gmask);
-                // every gl has read the matrix: clear the rows this cut marked
+                // every gl has read the matrix: each clears the words it set
 #pragma unroll
                 for (int s = 0; s < VPL; s++) {
                     if (outm & (1u << s)) {
                         const int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
-#pragma unroll
-                        for (int w2 = 0; w2 < NW; w2++) { S.E[a][w2] = 0; S.E[b][w2] = 0; S.E[cc][w2] = 0; }
+                        S.E[a][b >> 5] = 0u;
+                        S.E[b][cc >> 5] = 0u;
+                        S.E[cc][a >> 5] = 0u;
                     }
                 }
                 int pk, K, N;
