@@ -1105,70 +1105,104 @@ __global__ void VG_BOUNDS
                         if (~live[w2]) np = w2 * 64 + __ffsll((long long)~live[w2]) - 1;
                 }
                 if (VG_RARE(np < 0)) { flags |= 2; break; }
-                // mark the directed edges of removed triangles
+                // the removed triangles: R of them, numbered in (slot, lane) order
+                const unsigned lt = (1u << gl) - 1;
+                int R = 0, rpos[VPL];
 #pragma unroll
                 for (int s = 0; s < VPL; s++) {
-                    if (outm & (1u << s)) {
-                        const int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
-                        atomicOr(&S.E[a][b >> 5], 1u << (b & 31));
-                        atomicOr(&S.E[b][cc >> 5], 1u << (cc & 31));
-                        atomicOr(&S.E[cc][a >> 5], 1u << (a & 31));
-                    }
+                    const unsigned m = gballot<G>(gmask, gbase, (outm >> s) & 1);
+                    rpos[s] = R + __popc(m & lt);
+                    R += __popc(m);
                 }
-                __syncwarp(gmask);
-                unsigned bnd[VPL];
-                int kc = 0, nc = 0;
+                const int K = ntri - R;  // kept vertices
+                int N = 0;
+                if (R * 3 <= G) {
+                    // every directed edge of a removed triangle in a lane of its own;
+                    // an edge (x,y) borders the kept part iff its twin (y,x) was not
+                    // removed, and the twin carries the same unordered pair: a match
+                    // over the group finds it
 #pragma unroll
-                for (int s = 0; s < VPL; s++) {
-                    bnd[s] = 0;
-                    if (outm & (1u << s)) {
-                        const int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
-                        // edge (x,y) borders the kept part iff its twin (y,x) was not removed
-                        if (!((S.E[b][a >> 5] >> (a & 31)) & 1)) bnd[s] |= 1;
-                        if (!((S.E[cc][b >> 5] >> (b & 31)) & 1)) bnd[s] |= 2;
-                        if (!((S.E[a][cc >> 5] >> (cc & 31)) & 1)) bnd[s] |= 4;
-                        nc += __popc(bnd[s]);
-                    } else if (tri[s] != TRI_EMPTY) {
-                        kc++;
+                    for (int s = 0; s < VPL; s++) {
+                        if (outm & (1u << s)) {
+                            const int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
+                            S.elist[3 * rpos[s]] = a | (b << 8);
+                            S.elist[3 * rpos[s] + 1] = b | (cc << 8);
+                            S.elist[3 * rpos[s] + 2] = cc | (a << 8);
+                        }
                     }
-                }
-                __syncwarp(gmask);
-                // every gl has read the matrix: each clears the words it set
-#pragma unroll
-                for (int s = 0; s < VPL; s++) {
-                    if (outm & (1u << s)) {
-                        const int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
-                        S.E[a][b >> 5] = 0u;
-                        S.E[b][cc >> 5] = 0u;
-                        S.E[cc][a >> 5] = 0u;
-                    }
-                }
-                int pk, K, N;
-                if constexpr (VPL <= 4) {
-                    // exclusive prefix by bit planes: independent ballots
-                    // instead of a chain of shuffles
-                    const unsigned lt = (1u << gl) - 1;
-                    int pkk = 0, pkn = 0;
-                    K = 0;
-                    N = 0;
-#pragma unroll
-                    for (int b = 0; (1 << b) <= VPL; b++) {
-                        const unsigned m = gballot<G>(gmask, gbase, (kc >> b) & 1);
-                        pkk += __popc(m & lt) << b;
-                        K += __popc(m) << b;
-                    }
-#pragma unroll
-                    for (int b = 0; (1 << b) <= 3 * VPL; b++) {
-                        const unsigned m = gballot<G>(gmask, gbase, (nc >> b) & 1);
-                        pkn += __popc(m & lt) << b;
-                        N += __popc(m) << b;
-                    }
-                    pk = pkk | (pkn << 16);
+                    __syncwarp(gmask);
+                    const bool have = gl < 3 * R;
+                    const int e = have ? S.elist[gl] : 0;
+                    const int ex = e & 0xff, ey = e >> 8;
+                    const unsigned key = have ? (unsigned)(min(ex, ey) | (max(ex, ey) << 8)) : 0x10000u + gl;
+                    // every lane of the group takes part in the match (not behind &&)
+                    const unsigned same = __match_any_sync(gmask, key);
+                    const bool bd = have && __popc(same) == 1;
+                    const unsigned bm = gballot<G>(gmask, gbase, bd);
+                    N = __popc(bm);
+                    __syncwarp(gmask);  // every lane has read its edge
+                    if (bd) S.elist[__popc(bm & lt)] = e;
                 } else {
-                    int tot2;
-                    pk = gexcl_scan<G>(gmask, kc | (nc << 16), gl, tot2);
-                    K = tot2 & 0xffff;
-                    N = tot2 >> 16;
+                    // many removed: mark their directed edges in the bit matrix
+#pragma unroll
+                    for (int s = 0; s < VPL; s++) {
+                        if (outm & (1u << s)) {
+                            const int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
+                            atomicOr(&S.E[a][b >> 5], 1u << (b & 31));
+                            atomicOr(&S.E[b][cc >> 5], 1u << (cc & 31));
+                            atomicOr(&S.E[cc][a >> 5], 1u << (a & 31));
+                        }
+                    }
+                    __syncwarp(gmask);
+                    unsigned bnd[VPL];
+                    int nc = 0;
+#pragma unroll
+                    for (int s = 0; s < VPL; s++) {
+                        bnd[s] = 0;
+                        if (outm & (1u << s)) {
+                            const int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
+                            if (!((S.E[b][a >> 5] >> (a & 31)) & 1)) bnd[s] |= 1;
+                            if (!((S.E[cc][b >> 5] >> (b & 31)) & 1)) bnd[s] |= 2;
+                            if (!((S.E[a][cc >> 5] >> (cc & 31)) & 1)) bnd[s] |= 4;
+                            nc += __popc(bnd[s]);
+                        }
+                    }
+                    __syncwarp(gmask);
+                    // every gl has read the matrix: each clears the words it set
+#pragma unroll
+                    for (int s = 0; s < VPL; s++) {
+                        if (outm & (1u << s)) {
+                            const int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
+                            S.E[a][b >> 5] = 0u;
+                            S.E[b][cc >> 5] = 0u;
+                            S.E[cc][a >> 5] = 0u;
+                        }
+                    }
+                    int npos;
+                    if constexpr (VPL <= 4) {
+                        // exclusive prefix by bit planes: independent ballots
+                        // instead of a chain of shuffles
+                        npos = 0;
+#pragma unroll
+                        for (int b = 0; (1 << b) <= 3 * VPL; b++) {
+                            const unsigned m = gballot<G>(gmask, gbase, (nc >> b) & 1);
+                            npos += __popc(m & lt) << b;
+                            N += __popc(m) << b;
+                        }
+                    } else {
+                        npos = gexcl_scan<G>(gmask, nc, gl, N);
+                    }
+                    if (K + N <= CAP) {
+#pragma unroll
+                        for (int s = 0; s < VPL; s++) {
+                            if (outm & (1u << s)) {
+                                const int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
+                                if (bnd[s] & 1) S.elist[npos++] = a | (b << 8);
+                                if (bnd[s] & 2) S.elist[npos++] = b | (cc << 8);
+                                if (bnd[s] & 4) S.elist[npos++] = cc | (a << 8);
+                            }
+                        }
+                    }
                 }
                 const int tot = K + N;
                 if (VG_RARE(pp.collect) && gl == 0) S.cnt[3] += N;
@@ -1177,19 +1211,9 @@ __global__ void VG_BOUNDS
                     flags |= rc == 2 ? 4 : 2;
                     break;
                 }
-                {
-                    int npos = pk >> 16;
 #pragma unroll
-                    for (int s = 0; s < VPL; s++) {
-                        if (outm & (1u << s)) {
-                            const int a = tri_a(tri[s]), b = tri_b(tri[s]), cc = tri_c(tri[s]);
-                            if (bnd[s] & 1) S.elist[npos++] = a | (b << 8);
-                            if (bnd[s] & 2) S.elist[npos++] = b | (cc << 8);
-                            if (bnd[s] & 4) S.elist[npos++] = cc | (a << 8);
-                            tri[s] = TRI_EMPTY;  // removed: its slot is free
-                        }
-                    }
-                }
+                for (int s = 0; s < VPL; s++)
+                    if (outm & (1u << s)) tri[s] = TRI_EMPTY;  // removed: its slot is free
                 __syncwarp(gmask);
                 // new vertices, one per gl: planes x, y and the cutting plane
                 for (int q = gl; q < N; q += G) {
