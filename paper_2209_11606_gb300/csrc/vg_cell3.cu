@@ -120,9 +120,6 @@ struct Smem {
     typename V4T<T>::t pl[MAXP];  // plane normal (x,y,z) and constant (w), cell frame
     int pref[MAXP];               // neighbour's sorted index, or wall code -1..-6
     int pimg[MAXP];               // packed image shift of the neighbour
-    unsigned stri[G * VPL];       // staging for compaction and statistics
-    T sx[G * VPL], sy[G * VPL], sz[G * VPL];
-    float skap[G * VPL];
     float4 v4[G * VPL];                     // FP32 form: the cell's vertices (x, y, z, kappa); free slots 0
     unsigned E[MAXP][MAXP / 32];  // removed directed edges of one cut (32-bit words: native shared atomics)
     union {
@@ -140,7 +137,11 @@ struct Smem {
             int2 r[KMAX];    // sorted index and packed image
             int slot[KMAX];  // sorted order of the slots
         } pf;
-        double dpos[G * VPL][3];   // FP64 vertices (degenerate cells)
+        struct {
+            unsigned stri[G * VPL];            // the cell's triangles, by slot
+            T sx[G * VPL], sy[G * VPL], sz[G * VPL];
+            double dpos[G * VPL][3];           // FP64 vertices (degenerate cells)
+        } v;                                   // statistics: the finished cell
     } x;
     FT sfirst[G];              // a triangle of each face of a round
     int elist[G * VPL];        // boundary edges (x | y << 8) of one cut
@@ -1214,69 +1215,88 @@ __global__ void VG_BOUNDS
 #pragma unroll
                 for (int s = 0; s < VPL; s++)
                     if (outm & (1u << s)) tri[s] = TRI_EMPTY;  // removed: its slot is free
-                __syncwarp(gmask);
-                // new vertices, one per gl: planes x, y and the cutting plane
-                for (int q = gl; q < N; q += G) {
-                    const int xy = S.elist[q];
-                    const int x = xy & 0xff, y = xy >> 8;
-                    const auto P1 = S.pl[x];
-                    const auto P2 = S.pl[y];
-                    const T x23x = P2.y * qz - P2.z * qy, x23y = P2.z * qx - P2.x * qz, x23z = P2.x * qy - P2.y * qx;
-                    const T x31x = qy * P1.z - qz * P1.y, x31y = qz * P1.x - qx * P1.z, x31z = qx * P1.y - qy * P1.x;
-                    const T x12x = P1.y * P2.z - P1.z * P2.y, x12y = P1.z * P2.x - P1.x * P2.z,
-                            x12z = P1.x * P2.y - P1.y * P2.x;
-                    const T det = P1.x * x23x + P1.y * x23y + P1.z * x23z;
-                    T nx, ny, nz;
-                    float kp = 1.f, m123 = 0.f;
-                    bool solved = false;
-                    if constexpr (F32) {
-                        m123 = (P1.x * P1.x + P1.y * P1.y + P1.z * P1.z) *
-                                           (P2.x * P2.x + P2.y * P2.y + P2.z * P2.z) * qq;
-                        const float d2 = det * det;
-                        if (VG_RARE(!(d2 * KAP_MAX2 >= m123))) {
-                            const float3 v = solve_new64(&g, &st, &S.cc, S.pref, S.pimg, x, y, ref, img);
-                            nx = v.x; ny = v.y; nz = v.z;
-                            solved = true;
-                        }
-                    }
-                    if (!solved) {
-                        T id;
-                        if constexpr (F32) {
-                            id = rcp_a(det);
-                            kp = fmaxf(1.f, sqrt_a(m123) * fabsf(id) * (1.f / KAP0));
-                        } else {
-                            id = (T)1 / det;
-                        }
-                        nx = (P1.w * x23x + P2.w * x31x + c * x12x) * id;
-                        ny = (P1.w * x23y + P2.w * x31y + c * x12y) * id;
-                        nz = (P1.w * x23z + P2.w * x31z + c * x12z) * id;
-                    }
-                    S.stri[q] = mk_tri(x, y, np);
-                    S.sx[q] = nx; S.sy[q] = ny; S.sz[q] = nz;
-                    S.skap[q] = kp;
-                }
                 if (gl == 0) {
                     S.pl[np] = mk4<T>(qx, qy, qz, c);
                     S.pref[np] = ref;
                     S.pimg[np] = img;
                 }
                 __syncwarp(gmask);
-                // kept vertices stay in place; free slots take the new ones in order
+                // kept vertices stay in place; free slots take the new ones in
+                // order, each solving its own from the boundary edge list
                 ntri = tot;
+                unsigned need = 0;
+                int rk[VPL];
+                {
+                    int rank0 = 0;
+#pragma unroll
+                    for (int s = 0; s < VPL; s++) {
+                        const bool fr = tri[s] == TRI_EMPTY;
+                        const unsigned fm = gballot<G>(gmask, gbase, fr);
+                        rk[s] = rank0 + __popc(fm & lt);
+                        rank0 += __popc(fm);
+                        if (fr && rk[s] < N) need |= 1u << s;
+                    }
+                }
+                // a new vertex: planes x, y and the cutting plane; a lane with two
+                // slots to fill takes a second round
+#pragma unroll 1
+                while (__any_sync(gmask, need)) {
+                    if (need) {
+                        const int s0 = __ffs(need) - 1;
+                        int q = rk[0];
+#pragma unroll
+                        for (int s = 1; s < VPL; s++)
+                            if (s == s0) q = rk[s];
+                        const int xy = S.elist[q];
+                        const int x = xy & 0xff, y = xy >> 8;
+                        const auto P1 = S.pl[x];
+                        const auto P2 = S.pl[y];
+                        const T x23x = P2.y * qz - P2.z * qy, x23y = P2.z * qx - P2.x * qz, x23z = P2.x * qy - P2.y * qx;
+                        const T x31x = qy * P1.z - qz * P1.y, x31y = qz * P1.x - qx * P1.z, x31z = qx * P1.y - qy * P1.x;
+                        const T x12x = P1.y * P2.z - P1.z * P2.y, x12y = P1.z * P2.x - P1.x * P2.z,
+                                x12z = P1.x * P2.y - P1.y * P2.x;
+                        const T det = P1.x * x23x + P1.y * x23y + P1.z * x23z;
+                        T nx, ny, nz;
+                        float kp = 1.f, m123 = 0.f;
+                        bool solved = false;
+                        if constexpr (F32) {
+                            m123 = (P1.x * P1.x + P1.y * P1.y + P1.z * P1.z) *
+                                   (P2.x * P2.x + P2.y * P2.y + P2.z * P2.z) * qq;
+                            const float d2 = det * det;
+                            if (VG_RARE(!(d2 * KAP_MAX2 >= m123))) {
+                                const float3 v = solve_new64(&g, &st, &S.cc, S.pref, S.pimg, x, y, ref, img);
+                                nx = v.x; ny = v.y; nz = v.z;
+                                solved = true;
+                            }
+                        }
+                        if (!solved) {
+                            T id;
+                            if constexpr (F32) {
+                                id = rcp_a(det);
+                                kp = fmaxf(1.f, sqrt_a(m123) * fabsf(id) * (1.f / KAP0));
+                            } else {
+                                id = (T)1 / det;
+                            }
+                            nx = (P1.w * x23x + P2.w * x31x + c * x12x) * id;
+                            ny = (P1.w * x23y + P2.w * x31y + c * x12y) * id;
+                            nz = (P1.w * x23z + P2.w * x31z + c * x12z) * id;
+                        }
+                        const unsigned tn = mk_tri(x, y, np);
+#pragma unroll
+                        for (int s = 0; s < VPL; s++) {
+                            if (s == s0) {
+                                tri[s] = tn;
+                                vx[s] = nx; vy[s] = ny; vz[s] = nz;
+                                kap[s] = kp;
+                            }
+                        }
+                        need &= need - 1;
+                    }
+                }
                 T rr = 0;
-                int rank0 = 0;
                 rows = 0;
 #pragma unroll
                 for (int s = 0; s < VPL; s++) {
-                    const bool fr = tri[s] == TRI_EMPTY;
-                    const unsigned fm = gballot<G>(gmask, gbase, fr);
-                    const int rank = rank0 + __popc(fm & ((1u << gl) - 1));
-                    rank0 += __popc(fm);
-                    if (fr && rank < N) {
-                        tri[s] = S.stri[rank];
-                        vx[s] = S.sx[rank]; vy[s] = S.sy[rank]; vz[s] = S.sz[rank];
-                        kap[s] = S.skap[rank];
-                    }
                     if (tri[s] != TRI_EMPTY) {
                         T q2 = vx[s] * vx[s] + vy[s] * vy[s] + vz[s] * vz[s];
                         if constexpr (F32) q2 *= 1.f + 4e-6f * kap[s];  // allowance for FP32 error
@@ -1306,7 +1326,7 @@ __global__ void VG_BOUNDS
 #pragma unroll
                 for (int s = 0; s < VPL; s++) {
                     const int t = s * G + gl;
-                    S.stri[t] = tri[s]; S.sx[t] = vx[s]; S.sy[t] = vy[s]; S.sz[t] = vz[s];
+                    S.x.v.stri[t] = tri[s]; S.x.v.sx[t] = vx[s]; S.x.v.sy[t] = vy[s]; S.x.v.sz[t] = vz[s];
                 }
                 // reference point for the fans: a vertex of the cell (a radical
                 // cell may lie far from its particle, where fans from the
@@ -1339,19 +1359,19 @@ __global__ void VG_BOUNDS
 #pragma unroll 1
                     for (int s = 0; s < VPL; s++) {
                         const int t = s * G + gl;
-                        const unsigned tr = S.stri[t];
+                        const unsigned tr = S.x.v.stri[t];
                         if (tr != TRI_EMPTY) {
                             if constexpr (F32) {
-                                vertex64(&g, &st, &S.cc, S.pref, S.pimg, tr, S.x.dpos[t]);
+                                vertex64(&g, &st, &S.cc, S.pref, S.pimg, tr, S.x.v.dpos[t]);
                             } else {
-                                S.x.dpos[t][0] = S.sx[t]; S.x.dpos[t][1] = S.sy[t]; S.x.dpos[t][2] = S.sz[t];
+                                S.x.v.dpos[t][0] = S.x.v.sx[t]; S.x.v.dpos[t][1] = S.x.v.sy[t]; S.x.v.dpos[t][2] = S.x.v.sz[t];
                             }
                         }
                     }
                 }
                 __syncwarp(gmask);
                 double dref[3];
-                if (degen) { dref[0] = S.x.dpos[tref][0]; dref[1] = S.x.dpos[tref][1]; dref[2] = S.x.dpos[tref][2]; }
+                if (degen) { dref[0] = S.x.v.dpos[tref][0]; dref[1] = S.x.v.dpos[tref][1]; dref[2] = S.x.v.dpos[tref][2]; }
                 else { dref[0] = (double)rx; dref[1] = (double)ry; dref[2] = (double)rz; }
                 int F = 0;
 #pragma unroll
@@ -1386,7 +1406,7 @@ __global__ void VG_BOUNDS
 #pragma unroll 1
                     for (int s = 0; s < VPL; s++) {
                         const int t = s * G + gl;
-                        const unsigned tr = S.stri[t];
+                        const unsigned tr = S.x.v.stri[t];
                         if (tr != TRI_EMPTY) {
                             const int pp3[3] = {tri_a(tr), tri_b(tr), tri_c(tr)};
 #pragma unroll
@@ -1415,20 +1435,20 @@ __global__ void VG_BOUNDS
                         bool keep = true;
                         T farea;
                         if (!degen) {
-                            const T u0x = S.sx[t0] - rx, u0y = S.sy[t0] - ry, u0z = S.sz[t0] - rz;
+                            const T u0x = S.x.v.sx[t0] - rx, u0y = S.x.v.sy[t0] - ry, u0z = S.x.v.sz[t0] - rz;
                             T fv = 0, fcx = 0, fcy = 0, fcz = 0, fax = 0, fay = 0, faz = 0;
 #pragma unroll 1
                             for (steps = 0; steps < CAP; steps++) {
-                                const unsigned tr = S.stri[cur];
+                                const unsigned tr = S.x.v.stri[cur];
                                 const int p0 = tri_a(tr), p1 = tri_b(tr), p2 = tri_c(tr);
                                 const int yy = p0 == a ? p2 : (p1 == a ? p0 : (p2 == a ? p1 : -1));
                                 if (yy < 0) { bad = true; break; }
                                 const int nx = S.w.ftab[gl][yy];
-                                if (nx >= CAP || S.stri[nx] == TRI_EMPTY) { bad = true; break; }
+                                if (nx >= CAP || S.x.v.stri[nx] == TRI_EMPTY) { bad = true; break; }
                                 if (nx == t0) { steps++; closed = true; break; }
                                 if (cur != t0) {
-                                    const T ax = S.sx[cur] - rx, ay = S.sy[cur] - ry, az = S.sz[cur] - rz;
-                                    const T bx = S.sx[nx] - rx, by = S.sy[nx] - ry, bz = S.sz[nx] - rz;
+                                    const T ax = S.x.v.sx[cur] - rx, ay = S.x.v.sy[cur] - ry, az = S.x.v.sz[cur] - rz;
+                                    const T bx = S.x.v.sx[nx] - rx, by = S.x.v.sy[nx] - ry, bz = S.x.v.sz[nx] - rz;
                                     const T det = u0x * (ay * bz - az * by) - u0y * (ax * bz - az * bx) +
                                                   u0z * (ax * by - ay * bx);
                                     fv += det;
@@ -1451,24 +1471,24 @@ __global__ void VG_BOUNDS
                         } else {
                             // degenerate cell: FP64 vertices, coincident ones merged
                             const double eps = pp.merge_rel * g.s, eps2 = eps * eps;
-                            const double fx = S.x.dpos[t0][0] - dref[0], fy = S.x.dpos[t0][1] - dref[1],
-                                         fz = S.x.dpos[t0][2] - dref[2];
+                            const double fx = S.x.v.dpos[t0][0] - dref[0], fy = S.x.v.dpos[t0][1] - dref[1],
+                                         fz = S.x.v.dpos[t0][2] - dref[2];
                             double px = fx, py = fy, pz = fz, per = 0, fv = 0, fcx = 0, fcy = 0, fcz = 0;
                             double fax = 0, fay = 0, faz = 0;
                             int distinct = 1;
 #pragma unroll 1
                             for (steps = 0; steps < CAP; steps++) {
-                                const unsigned tr = S.stri[cur];
+                                const unsigned tr = S.x.v.stri[cur];
                                 const int p0 = tri_a(tr), p1 = tri_b(tr), p2 = tri_c(tr);
                                 const int yy = p0 == a ? p2 : (p1 == a ? p0 : (p2 == a ? p1 : -1));
                                 if (yy < 0) { bad = true; break; }
                                 const int nx = S.w.ftab[gl][yy];
-                                if (nx >= CAP || S.stri[nx] == TRI_EMPTY) { bad = true; break; }
+                                if (nx >= CAP || S.x.v.stri[nx] == TRI_EMPTY) { bad = true; break; }
                                 if (nx == t0) { steps++; closed = true; break; }
-                                const double A[3] = {S.x.dpos[cur][0] - dref[0], S.x.dpos[cur][1] - dref[1],
-                                                     S.x.dpos[cur][2] - dref[2]};
-                                const double B[3] = {S.x.dpos[nx][0] - dref[0], S.x.dpos[nx][1] - dref[1],
-                                                     S.x.dpos[nx][2] - dref[2]};
+                                const double A[3] = {S.x.v.dpos[cur][0] - dref[0], S.x.v.dpos[cur][1] - dref[1],
+                                                     S.x.v.dpos[cur][2] - dref[2]};
+                                const double B[3] = {S.x.v.dpos[nx][0] - dref[0], S.x.v.dpos[nx][1] - dref[1],
+                                                     S.x.v.dpos[nx][2] - dref[2]};
                                 if (cur != t0) {
                                     const double det = fx * (A[1] * B[2] - A[2] * B[1]) - fy * (A[0] * B[2] - A[2] * B[0]) +
                                                        fz * (A[0] * B[1] - A[1] * B[0]);
@@ -1546,12 +1566,12 @@ __global__ void VG_BOUNDS
 #pragma unroll 1
                     for (int s = 0; s < VPL; s++) {
                         const int t = s * G + gl;
-                        if (S.stri[t] != TRI_EMPTY) {
+                        if (S.x.v.stri[t] != TRI_EMPTY) {
                             bool first = true;
                             for (int q = 0; q < t && first; q++) {
-                                if (S.stri[q] == TRI_EMPTY) continue;
-                                const double dx = S.x.dpos[q][0] - S.x.dpos[t][0], dy = S.x.dpos[q][1] - S.x.dpos[t][1],
-                                             dz = S.x.dpos[q][2] - S.x.dpos[t][2];
+                                if (S.x.v.stri[q] == TRI_EMPTY) continue;
+                                const double dx = S.x.v.dpos[q][0] - S.x.v.dpos[t][0], dy = S.x.v.dpos[q][1] - S.x.v.dpos[t][1],
+                                             dz = S.x.v.dpos[q][2] - S.x.v.dpos[t][2];
                                 if (dx * dx + dy * dy + dz * dz <= eps2) first = false;
                             }
                             cntv += first;
