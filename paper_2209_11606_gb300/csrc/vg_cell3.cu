@@ -54,8 +54,10 @@ constexpr int NBIN = 8;           // prefetch: radial buckets
 constexpr float KAP0 = 4.0f;      // condition number covered by the base FP32 band
 constexpr float KAP_MAX2 = 1e8f;  // condition number^2 beyond which a new vertex is solved in FP64
 constexpr int MAX_SHELL_EXTRA = 4;
+// resident CTAs per SM the register budget is sized for: tier 0 (64-vertex
+// cells) five (96 registers a thread, 20 warps an SM), the larger tiers four
 #ifndef VG_MINB
-#define VG_MINB 4
+#define VG_MINB 5
 #endif
 #ifndef VG_MAXT
 #define VG_MAXT 128
@@ -70,7 +72,7 @@ constexpr int MAX_SHELL_EXTRA = 4;
 #ifdef VG_MAXREG
 #define VG_BOUNDS __maxnreg__(VG_MAXREG)
 #else
-#define VG_BOUNDS __launch_bounds__(VG_MAXT, VG_MINB)
+#define VG_BOUNDS __launch_bounds__(VG_MAXT, MAXP == 64 ? VG_MINB : 4)
 #endif
 
 template <typename T> struct V4T;
@@ -1679,6 +1681,9 @@ cudaError_t launch_t(const Store &s, const Out &o, const Params &p, const Offset
     auto kfn = k_cells3<T, VPL, MAXP, BATCH, G>;
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // shared memory before L1: the resident CTAs are bounded by it
+    e = cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, warps * 32, smem);
     if (e != cudaSuccess) return e;
@@ -1693,8 +1698,8 @@ cudaError_t launch_t(const Store &s, const Out &o, const Params &p, const Offset
 
 }  // namespace
 
-// Tier 0 (cells up to 64 vertices and 64 planes) runs two cells per warp
-// (16 lanes, 4 vertex slots per lane); the larger tiers one cell per warp.
+// Every tier runs one cell per warp (32 lanes); tier 0 holds cells up to 64
+// vertices and 64 planes, tier 1 up to 128, tier 2 up to 256.
 cudaError_t launch_cells3(const Store &s, const Out &o, const Params &p, const Offsets &off, int precision,
                           unsigned *ticket, int sm_count, int warps_per_cta, const int *cells, int ncells, int tier,
                           cudaStream_t st) {
