@@ -735,8 +735,11 @@ __global__ void VG_BOUNDS
                                 }
                                 int ltot;
                                 const int lex = gexcl_scan<G>(gmask, len, gl, ltot);
-                                const int slot = nrun + __popc(hb & ((1u << gl) - 1));
-                                if (have && slot < NRUN) {
+                                // runs without particles take no entry: starts stay distinct
+                                const bool ent = have && len > 0;
+                                const unsigned hn = gballot<G>(gmask, gbase, ent);
+                                const int slot = nrun + __popc(hn & ((1u << gl) - 1));
+                                if (ent && slot < NRUN) {
                                     S.w.run.start[slot] = npart + lex;
                                     S.w.run.j0[slot] = j0r;
                                     // x offset of a particle = oxb + its block index
@@ -744,7 +747,7 @@ __global__ void VG_BOUNDS
                                     // offsets (oy, oz) and the run's image shift (m0, my, mz)
                                     S.w.run.oyz[slot] = (oy + 64) | ((oz + 64) << 8) | ((m0 + 8) << 16) | myz;
                                 }
-                                nrun += __popc(hb);
+                                nrun += __popc(hn);
                                 npart += ltot;
                                 if (have) ox += xb - xa + 1;
                             }
@@ -752,18 +755,23 @@ __global__ void VG_BOUNDS
                         if (nrun > NRUN) { give_up = true; break; }
                         __syncwarp(gmask);
                         // 2. all particles of all runs, G at a time
+                        int rp = 0;  // the first run that starts at or after v0
 #pragma unroll 1
                         for (int v0 = 0; v0 < npart; v0 += G) {
+                            // the runs that start in this round, one per lane: a bit each
+                            unsigned sb = 0;
+                            if (rp + gl < nrun) {
+                                const int s0 = S.w.run.start[rp + gl];
+                                if (s0 < v0 + G) sb = 1u << (s0 - v0);
+                            }
+                            const unsigned smask = __reduce_or_sync(gmask, sb);
                             const int v = v0 + gl;
                             bool keep = false;
                             float qx = 0.f, qy = 0.f, qz = 0.f, qq = 0.f;
                             int j = 0, img = 0;
                             if (v < npart) {
-                                int lo = 0, hi = nrun - 1;  // last run with start <= v
-                                while (lo < hi) {
-                                    const int mid = (lo + hi + 1) >> 1;
-                                    if (S.w.run.start[mid] <= v) lo = mid; else hi = mid - 1;
-                                }
+                                // last run with start <= v
+                                const int lo = rp + __popc(smask & (0xffffffffu >> (31 - gl))) - 1;
                                 j = S.w.run.j0[lo] + (v - S.w.run.start[lo]);
                                 const int oyz = S.w.run.oyz[lo];
                                 const int oy = (oyz & 0xff) - 64, oz = ((oyz >> 8) & 0xff) - 64;
@@ -780,6 +788,7 @@ __global__ void VG_BOUNDS
                                 S.x.pf.r[pos] = make_int2(j, img);
                             }
                             count += __popc(bal);
+                            rp += __popc(smask);
                         }
                         __syncwarp(gmask);
                         if (count <= KMAX) break;
@@ -1378,7 +1387,11 @@ __global__ void VG_BOUNDS
                 int F = 0;
 #pragma unroll
                 for (int w2 = 0; w2 < NW; w2++) F += __popcll(live[w2]);
+                // six times the volume: FP64 sums for FP64 vertices, else the
+                // vertices' own type (fans from a vertex of the convex cell are
+                // all non-negative, so the sum is well conditioned)
                 double vol = 0.0;
+                T volt = 0;
                 T cx = 0, cy = 0, cz = 0, area = 0;
                 int order_sum = 0, faces_kept = 0;
                 bool bad = false;
@@ -1465,7 +1478,7 @@ __global__ void VG_BOUNDS
                                 }
                                 cur = nx;
                             }
-                            vol += (double)fv;
+                            volt += fv;
                             cx += fcx; cy += fcy; cz += fcz;
                             if constexpr (F32) farea = 0.5f * sqrt_a(fax * fax + fay * fay + faz * faz);
                             else farea = (T)0.5 * sqrt(fax * fax + fay * fay + faz * faz);
@@ -1543,7 +1556,8 @@ __global__ void VG_BOUNDS
                     }
                     __syncwarp(gmask);
                 }
-                vol = gsum<G>(gmask, vol);
+                if (degen) vol = gsum<G>(gmask, vol);
+                else vol = (double)gsum<G>(gmask, volt);
                 cx = gsum<G>(gmask, cx); cy = gsum<G>(gmask, cy); cz = gsum<G>(gmask, cz);
                 area = gsum<G>(gmask, area);
                 const int nfk = __reduce_add_sync(gmask, faces_kept);
@@ -1587,6 +1601,10 @@ __global__ void VG_BOUNDS
                 if (anybad) {
                     fail = true;  // inconsistent topology: the FP64 big-cell tier redoes it
                 } else {
+                    // the cell's place in the face list, asked for before the sort
+                    // so that the atomic's round trip overlaps it
+                    long long fbase = 0;
+                    if (gl == 0) fbase = (long long)atomicAdd(o.fcount, (unsigned long long)nfk);
                     // one round of faces: one key per lane, a shorter network
                     const bool one = F <= G;
                     if (one) {
@@ -1597,8 +1615,6 @@ __global__ void VG_BOUNDS
                         bitonic<R, G>(key, gl, gmask);
                     }
                     const int kstride = one ? 1 : R;
-                    long long fbase = 0;
-                    if (gl == 0) fbase = (long long)atomicAdd(o.fcount, (unsigned long long)nfk);
                     fbase = __shfl_sync(gmask, fbase, 0, G);
                     const bool overflow = fbase + nfk > o.fcap;
                     if (!overflow) {
