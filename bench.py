@@ -57,12 +57,15 @@ METRIC_2D = "2D Voronoi cells/s, 1 GB300, chosen vs plain FP64 form; % of roofli
 # FP32 peak derived from unit counts and clock: 152 SMs x 128 FP32 lanes x
 # 2 FLOP (FMA) x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# algorithmic FLOP counts per unit of work (see the design notes)
+# algorithmic FLOP per unit of work: a vertex tested against a plane (3 FMA),
+# a candidate (offset, |q|^2, plane constant), a new vertex (Cramer's rule on
+# three planes), a fan tetrahedron of the statistics (determinant, centroid,
+# vector area)
 FLOP_VTEST, FLOP_CAND, FLOP_NEWV, FLOP_FANTET = 6, 12, 51, 42
 # DRAM bytes (read + write) of one k_cells3<float,2,64> launch over the 1M
 # uniform cells, from the ncu capture summarised in
 # profiles/k_cells3_fp32_uniform1m_ncu.md (null for other workloads)
-CELL_KERNEL_DRAM_BYTES_UNIFORM1M = 149.632e6 + 261.173e6
+CELL_KERNEL_DRAM_BYTES_UNIFORM1M = 173.474e6 + 289.317e6
 MLP_ALPHA, MLP_KMIN, MLP_KMAX = 1.5, 24.0, 1024.0
 PKG = os.path.join(ROOT, "paper_2209_11606_gb300")
 MLP_PARAMS = os.path.join(PKG, "mlp_params_gb300.json")
