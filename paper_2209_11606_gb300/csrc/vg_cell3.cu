@@ -1387,11 +1387,7 @@ __global__ void VG_BOUNDS
                 int F = 0;
 #pragma unroll
                 for (int w2 = 0; w2 < NW; w2++) F += __popcll(live[w2]);
-                // six times the volume: FP64 sums for FP64 vertices, else the
-                // vertices' own type (fans from a vertex of the convex cell are
-                // all non-negative, so the sum is well conditioned)
-                double vol = 0.0;
-                T volt = 0;
+                double vol = 0.0;  // six times the volume, accumulated in FP64
                 T cx = 0, cy = 0, cz = 0, area = 0;
                 int order_sum = 0, faces_kept = 0;
                 bool bad = false;
@@ -1478,7 +1474,7 @@ __global__ void VG_BOUNDS
                                 }
                                 cur = nx;
                             }
-                            volt += fv;
+                            vol += (double)fv;
                             cx += fcx; cy += fcy; cz += fcz;
                             if constexpr (F32) farea = 0.5f * sqrt_a(fax * fax + fay * fay + faz * faz);
                             else farea = (T)0.5 * sqrt(fax * fax + fay * fay + faz * faz);
@@ -1556,8 +1552,7 @@ __global__ void VG_BOUNDS
                     }
                     __syncwarp(gmask);
                 }
-                if (degen) vol = gsum<G>(gmask, vol);
-                else vol = (double)gsum<G>(gmask, volt);
+                vol = gsum<G>(gmask, vol);
                 cx = gsum<G>(gmask, cx); cy = gsum<G>(gmask, cy); cz = gsum<G>(gmask, cz);
                 area = gsum<G>(gmask, area);
                 const int nfk = __reduce_add_sync(gmask, faces_kept);
