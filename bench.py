@@ -188,11 +188,11 @@ def graph_steps(V, torch, ctx, stream, flush, steps):
     return [a.elapsed_time(b) for a, b in evs]
 
 
-def batched_run(V, torch, stream, flush, steps: int = 5, seed: int = 5):
+def batched_run(V, torch, stream, flush, mlp, steps: int = 5, seed: int = 5):
     """The 256-system batched workload: one container, one graph replay per
     step (one sort over all systems' blocks, one persistent cell launch),
-    with N_opt per distribution class and the launch parameters from the
-    autotuner (cached per class)."""
+    with N_opt per distribution class and the launch parameters, fixed or
+    learned preload targets among them, from the autotuner (cached)."""
     from paper_2209_11606_gb300 import autotune as A, workloads as W
     systems = W.batched_systems(256, 1000, 200_000, seed=seed)
     t0 = time.perf_counter()
@@ -200,7 +200,7 @@ def batched_run(V, torch, stream, flush, steps: int = 5, seed: int = 5):
     key = "batched256-seed%d" % seed
     tb = cache.get(key)
     if tb is None:
-        tb = A.tune_batch(systems, torch, cache)
+        tb = A.tune_batch(systems, torch, cache, predictor=mlp, mlp_args=(MLP_ALPHA, MLP_KMIN, MLP_KMAX))
         tb = {"n_opt": tb["n_opt"], "launch": tb["launch"], "classes": tb["classes"]}
         cache.put(key, tb)
     tune_s = time.perf_counter() - t0
@@ -210,6 +210,8 @@ def batched_run(V, torch, stream, flush, steps: int = 5, seed: int = 5):
     ctx = V.vg_batch_create(3, descs, stream=stream)
     try:
         cfg = A.config_from(tb["launch"])
+        if cfg.use_mlp:
+            V.vg_set_predictor(ctx, mlp, MLP_ALPHA, MLP_KMIN, MLP_KMAX)
         V.vg_graph_capture(ctx, counts, pos, None, cfg)
         for _ in range(3):
             V.vg_graph_launch(ctx)
@@ -225,9 +227,10 @@ def batched_run(V, torch, stream, flush, steps: int = 5, seed: int = 5):
         return {"value": n * steps / (sum(ms) / 1000.0), "unit": "cells/s", "steps": steps,
                 "ms_per_step": sum(ms) / steps, "cells_per_step": n, "systems": len(systems),
                 "mix": mix, "n_opt_by_class": per_class,
-                "launch": {k: tb["launch"][k] for k in ("order", "warps_per_cta", "chunk")},
+                "launch": {k: tb["launch"].get(k, 0) for k in ("order", "warps_per_cta", "chunk", "use_mlp")},
                 "tuning_seconds": tune_s,
-                "form": "FP32 cuts + FP64 re-test, autotuned N_opt and launch, one graph replay",
+                "form": "FP32 cuts + FP64 re-test, autotuned N_opt, launch and preload (fixed or learned), "
+                        "one graph replay",
                 "workload": "256 3D systems, sizes log-uniform in [1000, 200000], uniform / perturbed "
                             "FCC (sigma 0.05 a) / 50 Gaussian blobs (sigma 0.02 side), random "
                             f"periodicity (seed {seed})"}
@@ -467,7 +470,7 @@ def main():
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "retest_per_cell": float(w["r"].mean())}
     if not args.no_batched and args.workload == "uniform1m":
-        line["batched"] = batched_run(V, torch, stream, flush)
+        line["batched"] = batched_run(V, torch, stream, flush, mlp)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = {k: v for k, v in
                                 cpu_baseline(s, grid, n if args.workload == "uniform1m" else 100_000).items()

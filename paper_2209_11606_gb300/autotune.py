@@ -11,6 +11,9 @@ Here the scan is automatic: for a system, every combination of
 * warps per CTA in {1, 2, 4} (one warp per cell, so CTA sizes 32..128),
 * candidate order in {sorted prefetch, block walk},
 * cells per work-queue ticket in {1, 2, 4},
+* for the sorted prefetch, a fixed preload target or the learned one (when
+  a predictor is given: per-block targets from the MLP of Sec. 2.1.3's
+  candidate count, computed at insert),
 
 is timed on a seeded random sample of the cells (vg_compute_subset, CUDA
 events around the cell kernels), and the fastest is kept.  Results are cached
@@ -86,11 +89,12 @@ class Cache:
         os.replace(tmp, self.path)
 
 
-def _cfg(order: str, warps: int, chunk: int):
+def _cfg(order: str, warps: int, chunk: int, use_mlp: int = 0):
     cfg = V.vg_config_default()
     cfg.order = V.VG_WALK if order == "walk" else V.VG_PREFETCH
     cfg.warps_per_cta = warps
     cfg.chunk = chunk
+    cfg.use_mlp = int(use_mlp)
     return cfg
 
 
@@ -158,15 +162,17 @@ def tuned(s, torch, cache: Cache | None = None, cls: str | None = None, **kw) ->
 
 def config_from(best: dict):
     """vg_config of a tuned entry."""
-    return _cfg(best["order"], int(best["warps_per_cta"]), int(best["chunk"]))
+    return _cfg(best["order"], int(best["warps_per_cta"]), int(best["chunk"]), int(best.get("use_mlp", 0)))
 
 
 def tune_batch(systems, torch, cache: Cache | None = None, sample_frac: float = 0.05, seed: int = 0,
-               reps: int = 2) -> dict:
+               reps: int = 2, predictor=None, mlp_args=(1.5, 24.0, 1024.0)) -> dict:
     """Parameters for a batch of systems: N_opt per distribution class (tuned
     on the class's largest system with the default launch), then the launch
-    parameters (order, warps per CTA, chunk) on a sample of the whole batch
-    with those grids.  Returns {"n_opt": [...], "launch": {...}, "classes": [...]}."""
+    parameters (order, warps per CTA, chunk, and with a `predictor` handle
+    fixed or learned preload targets, `mlp_args` = (alpha, kmin, kmax)) on a
+    sample of the whole batch with those grids.  Returns {"n_opt": [...],
+    "launch": {...}, "classes": [...]}."""
     classes = [distribution_class(x.pos, x.lo, x.hi) for x in systems]
     n_opt_of = {}
     for cls in sorted(set(classes)):
@@ -193,14 +199,18 @@ def tune_batch(systems, torch, cache: Cache | None = None, sample_frac: float = 
     ctx = V.vg_batch_create(systems[0].dim, descs)
     table = []
     try:
+        if predictor is not None:
+            V.vg_set_predictor(ctx, predictor, *mlp_args)
         V.vg_batch_insert(ctx, counts, pos, rad)
         for order in ORDERS:
             if order == "prefetch" and systems[0].dim != 3:
                 continue
+            mlps = (0, 1) if order == "prefetch" and predictor is not None else (0,)
             for w in WARPS:
                 for ch in CHUNKS:
-                    ms = _time_subset(ctx, sample, _cfg(order, w, ch), reps)
-                    table.append({"order": order, "warps_per_cta": w, "chunk": ch, "ms": ms})
+                    for um in mlps:
+                        ms = _time_subset(ctx, sample, _cfg(order, w, ch, um), reps)
+                        table.append({"order": order, "warps_per_cta": w, "chunk": ch, "use_mlp": um, "ms": ms})
     finally:
         V.vg_destroy(ctx)
     launch = min(table, key=lambda r: r["ms"])
