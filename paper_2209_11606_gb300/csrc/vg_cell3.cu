@@ -693,8 +693,11 @@ __global__ void VG_BOUNDS
                             int oy = 0, oz = 0, krow = 0, ox = 0, oxhi = -1, myz = 0;
                             bool rowok = false;
                             if (r < nrows) {
-                                oy = r % wy - rg1;
-                                oz = r / wy - rg2;
+                                // r / wy for r < 64, wy <= 7: the approximate quotient of
+                                // r + 1/2 is within 0.5 / wy of the exact one
+                                const int rq = (int)(((float)r + 0.5f) * rcp_a((float)wy));
+                                oy = r - rq * wy - rg1;
+                                oz = rq - rg2;
                                 int kk, mx, my, mz;
                                 rowok = row_gap2(g, o1, o2, oy, oz) < rho2 &&
                                         resolve(g, SY.blk_base, S.cc.b, 0, oy, oz, kk, mx, my, mz);

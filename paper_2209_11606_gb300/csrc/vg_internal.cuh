@@ -117,12 +117,13 @@ __device__ __forceinline__ float cbrt_a(float x) {
     return r;
 }
 
-__device__ __forceinline__ int floordiv(int a, int b) {
+static __device__ __noinline__ int floordiv(int a, int b) {
     int q = a / b;
     if ((a % b != 0) && ((a < 0) != (b < 0))) q--;
     return q;
 }
 // floor(a / b) for b > 0, without a division when a lies within one period
+// (the general case, rare, stays out of line)
 // of [0, b) (block offsets of the prefetch and of the walk's near shells)
 __device__ __forceinline__ int floordiv_near(int a, int b) {
     if ((unsigned)a < (unsigned)b) return 0;
