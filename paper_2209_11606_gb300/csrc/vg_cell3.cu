@@ -169,15 +169,19 @@ __device__ __forceinline__ int pack_img(int mx, int my, int mz) {
 // classifying it; every kept candidate still goes through the exact test.
 // A free slot holds (0, 0, 0, 0): it keeps a candidate only if c <= 0 (a
 // radical plane that the particle itself lies beyond), which is harmless.
-template <int CAP>
-__device__ __forceinline__ bool may_cut(const float4 *v4, float qx, float qy, float qz, float c, float tau) {
+// Only the first n entries are read: the rows of slots that hold any vertex
+// (n a multiple of 8).
+__device__ __forceinline__ bool may_cut(const float4 *v4, int n, float qx, float qy, float qz, float c, float tau) {
     const float lim = -1.01f * tau;
     bool m = false;
-#pragma unroll 8
-    for (int t = 0; t < CAP; t++) {
-        const float4 v = v4[t];
-        const float d = fmaf(v.x, qx, fmaf(v.y, qy, fmaf(v.z, qz, -c)));
-        m |= d >= lim * v.w;
+#pragma unroll 1
+    for (int t0 = 0; t0 < n; t0 += 8) {
+#pragma unroll
+        for (int t = t0; t < t0 + 8; t++) {
+            const float4 v = v4[t];
+            const float d = fmaf(v.x, qx, fmaf(v.y, qy, fmaf(v.z, qz, -c)));
+            m |= d >= lim * v.w;
+        }
     }
     return m;
 }
@@ -896,7 +900,8 @@ __global__ void VG_BOUNDS
                             if constexpr (F32) {
                                 if (filt && ok && q4.w >= 1e-30f) {
                                     const float cc = st.radical ? 0.5f * (q4.w + rp32 * rp32 - crj * crj) : 0.5f * q4.w;
-                                    ok = may_cut<CAP>(S.v4, q4.x, q4.y, q4.z, cc, tol32f * sqrt_a(r2 * q4.w));
+                                    ok = may_cut(S.v4, G * (32 - __clz(rows)), q4.x, q4.y, q4.z, cc,
+                                                 tol32f * sqrt_a(r2 * q4.w));
                                 }
                             }
                         }
@@ -950,7 +955,8 @@ __global__ void VG_BOUNDS
                             if constexpr (F32) {
                                 if (filt && ok && cqq >= 1e-30f) {
                                     const float cc = st.radical ? 0.5f * (cqq + rp32 * rp32 - crj * crj) : 0.5f * cqq;
-                                    ok = may_cut<CAP>(S.v4, cqx, cqy, cqz, cc, tol32f * sqrt_a(r2 * cqq));
+                                    ok = may_cut(S.v4, G * (32 - __clz(rows)), cqx, cqy, cqz, cc,
+                                                 tol32f * sqrt_a(r2 * cqq));
                                 }
                             }
                             S.cbq[gl] = mk4<T>(cqx, cqy, cqz, cqq);
