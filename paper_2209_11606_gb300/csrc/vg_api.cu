@@ -360,12 +360,15 @@ vg_status insert_all(vg_ctx *c, const std::vector<long long> &counts, const doub
     return VG_OK;
 }
 
-vg_status check_config(vg_ctx *c, const vg_config &cfg) {
+// `inserts`: the call inserts first (a graph capture), so an attached
+// predictor supplies the per-block preload targets itself.
+vg_status check_config(vg_ctx *c, const vg_config &cfg, bool inserts = false) {
     if (cfg.precision != VG_FP64 && cfg.precision != VG_FP32_RETEST) return fail(c, VG_ERR_ARG, "precision");
     if (cfg.order != VG_WALK && cfg.order != VG_PREFETCH) return fail(c, VG_ERR_ARG, "order");
     if (!(cfg.tol32 > 0) || !(cfg.tau_rel > 0) || !(cfg.merge_rel > 0)) return fail(c, VG_ERR_ARG, "tolerances");
     if (cfg.warps_per_cta > 4) return fail(c, VG_ERR_ARG, "warps_per_cta above 4 (CTAs of at most 128 threads)");
-    if (cfg.use_mlp && !c->kblock_valid) return fail(c, VG_ERR_STATE, "use_mlp without vg_mlp_predict after the insert");
+    if (cfg.use_mlp && !c->kblock_valid && !(inserts && c->pred))
+        return fail(c, VG_ERR_STATE, "use_mlp without vg_mlp_predict after the insert");
     return VG_OK;
 }
 
@@ -640,7 +643,7 @@ vg_status vg_graph_capture(vg_ctx *c, const int64_t *counts, const double *pos, 
     if (!c) return VG_ERR_ARG;
     vg_config cfg;
     if (cfg_in) cfg = *cfg_in; else vg_config_default(&cfg);
-    vg_status s = check_config(c, cfg);
+    vg_status s = check_config(c, cfg, true);
     if (s != VG_OK) return s;
     if (!counts) return fail(c, VG_ERR_ARG, "counts is NULL");
     std::vector<long long> cv(c->sys.size());

@@ -1,0 +1,148 @@
+"""Parity at the full sizes of the measured workloads, in the launch
+configuration the benchmark times: one CUDA graph replay (sort, learned
+preload targets where the benchmark uses them, cell kernels, face CSR) with
+the same block grid, candidate order and predictor settings.
+
+At these sizes the oracle computes a seeded random sample of cells (its
+grid walk over all particles, one cell at a time), compared element by
+element: topology (status, V/E/F, neighbour ids and images, face orders)
+bit-exact, volume, area and centroid within 1e-5 relative.  The whole output
+is checked by properties that hold at any size: every cell computed, cell
+volumes (areas) summing to the box, Euler's relation V - E + F = 2 per 3D
+cell (V = E per 2D cell), and neighbour symmetry (j is a face neighbour of
+i with image m iff i is one of j with image -m)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2209_11606_gb300 import workloads as W
+from tests.compare import compare
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+# the benchmark's predictor settings: preload target clamp(alpha exp(y), kmin, kmax)
+MLP_ALPHA, MLP_KMIN, MLP_KMAX = 1.5, 24.0, 1024.0
+PARAMS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                      "paper_2209_11606_gb300", "mlp_params_gb300.json")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_11606_gb300 import build
+    build.build()
+
+
+def bench_form(s, grid, order, learned):
+    """Host results of one graph replay in the benchmark's configuration."""
+    import torch
+    from paper_2209_11606_gb300 import predictor as P, vorogpu as V
+    pos = torch.from_numpy(np.ascontiguousarray(s.pos)).cuda()
+    rad = None if s.radii is None else torch.from_numpy(np.ascontiguousarray(s.radii)).cuda()
+    ctx = V.vg_create(s.dim, s.lo, s.hi, s.periodic, grid)
+    mlp = None
+    try:
+        if learned:
+            with open(PARAMS) as f:
+                params = np.asarray(json.load(f)["params"], dtype=np.float32)
+            mlp = P.predictor(params)
+            V.vg_set_predictor(ctx, mlp, MLP_ALPHA, MLP_KMIN, MLP_KMAX)
+        cfg = V.vg_config_default()
+        cfg.precision = V.VG_FP32_RETEST
+        cfg.order = V.VG_PREFETCH if order == "prefetch" else V.VG_WALK
+        cfg.use_mlp = int(learned)
+        V.vg_graph_capture(ctx, [s.n], pos, rad, cfg)
+        V.vg_graph_launch(ctx)
+        V.vg_graph_sync(ctx)
+        out = V._fetch(ctx, s.n, s.dim, False)
+        out["grid"] = V.vg_get_grid(ctx, s.dim)
+        return out
+    finally:
+        V.vg_destroy(ctx)
+        if mlp is not None:
+            V.vg_mlp_destroy(mlp)
+
+
+def sampled_parity(s, got, m, seed=0):
+    rng = np.random.default_rng(seed)
+    cells = np.sort(rng.choice(s.n, size=min(m, s.n), replace=False))
+    ref = oracle.compute(s.pos, s.lo, s.hi, s.periodic, radii=s.radii, method="grid",
+                         nblocks=got["grid"], cells=cells, threads=os.cpu_count() or 1)
+    rep = compare(got, ref, RTOL, cells=cells)
+    assert rep["topology_ok"], rep
+    assert rep["values_ok"], rep
+    return rep
+
+
+def whole_output_properties(s, got, symmetry=True, empty_ok=False):
+    st = got["status"]
+    ok = st == 0
+    if empty_ok:
+        assert np.all(ok | (st == 1)), np.unique(st, return_counts=True)  # 1: VG_CELL_EMPTY
+    else:
+        assert ok.all(), np.unique(st, return_counts=True)
+    box = float(np.prod(np.asarray(s.hi) - np.asarray(s.lo)))
+    total = float(got["vol"][ok].sum())
+    assert abs(total - box) <= 1e-6 * box, (total, box)
+    if s.dim == 3:
+        assert np.all((got["nv"] - got["ne"] + got["nf"])[ok] == 2)
+    else:
+        assert np.all(got["nv"][ok] == got["ne"][ok])
+    if symmetry:
+        nf = np.diff(got["face_off"])
+        owner = np.repeat(np.arange(s.n, dtype=np.int64), nf)
+        nbr = got["nbr_id"].astype(np.int64)
+        img = np.asarray(got["nbr_img"], dtype=np.int64)[:, :s.dim]
+        keep = nbr >= 0  # walls have no partner
+        code = np.zeros(int(keep.sum()), np.int64)
+        back = np.zeros_like(code)
+        for a in range(s.dim):  # image shifts -1..1 per axis, 2 bits each
+            code = code * 4 + (img[keep, a] + 1)
+            back = back * 4 + (1 - img[keep, a])
+        fwd = (owner[keep] * s.n + nbr[keep]) * 64 + code
+        rev = (nbr[keep] * s.n + owner[keep]) * 64 + back
+        assert np.abs(img[keep]).max(initial=0) <= 1
+        assert np.array_equal(np.sort(fwd), np.sort(rev))
+
+
+def test_uniform1m_learned_preload():
+    s = W.workload("uniform1m")
+    got = bench_form(s, (58, 58, 58), "prefetch", True)
+    sampled_parity(s, got, 5000)
+    whole_output_properties(s, got)
+
+
+def test_bcc1m_learned_preload():
+    s = W.workload("bcc1m")
+    got = bench_form(s, (64, 64, 64), "prefetch", True)
+    sampled_parity(s, got, 5000)
+    whole_output_properties(s, got)
+
+
+def test_radical2m_walk():
+    s = W.workload("radical2m")
+    got = bench_form(s, None, "walk", False)
+    sampled_parity(s, got, 3000)
+    whole_output_properties(s, got, empty_ok=True)
+
+
+def test_hex10m_2d_walk():
+    s = W.workload("hex10m")
+    got = bench_form(s, None, "walk", False)
+    sampled_parity(s, got, 3000)
+    whole_output_properties(s, got)
+
+
+def test_slabs102m_learned_preload():
+    # 102.4M cells: sampled parity and the volume sum (the symmetry check
+    # would sort 1.5G faces on the host)
+    s = W.fcc_uniform_slabs(seed=6)
+    got = bench_form(s, None, "prefetch", True)
+    sampled_parity(s, got, 2000)
+    whole_output_properties(s, got, symmetry=False)
