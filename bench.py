@@ -65,7 +65,7 @@ FLOP_VTEST, FLOP_CAND, FLOP_NEWV, FLOP_FANTET = 6, 12, 51, 42
 # DRAM bytes (read + write) of one k_cells3<float,2,64> launch over the 1M
 # uniform cells, from the ncu capture summarised in
 # profiles/k_cells3_fp32_uniform1m_ncu.md (null for other workloads)
-CELL_KERNEL_DRAM_BYTES_UNIFORM1M = 173.474e6 + 289.317e6
+CELL_KERNEL_DRAM_BYTES_UNIFORM1M = 174.202e6 + 287.125e6
 MLP_ALPHA, MLP_KMIN, MLP_KMAX = 1.5, 24.0, 1024.0
 PKG = os.path.join(ROOT, "paper_2209_11606_gb300")
 MLP_PARAMS = os.path.join(PKG, "mlp_params_gb300.json")
