@@ -187,8 +187,14 @@ __device__ __forceinline__ void meet(typename P2<T>::t A, T bx, T by, T bc, T &x
     }
 }
 
+// resident 128-thread CTAs per SM the register budget is sized for (four:
+// 128 registers, where ptxas also spills least)
+#ifndef VG2_MINB
+#define VG2_MINB 4
+#endif
+
 template <typename T, int G, int CAP, bool BATCH>
-__global__ void __launch_bounds__(128) k_cells2(const __grid_constant__ Store st,
+__global__ void __launch_bounds__(128, VG2_MINB) k_cells2(const __grid_constant__ Store st,
                                                 const __grid_constant__ Out o, const __grid_constant__ Params pp,
                                                 const __grid_constant__ Offsets off, unsigned *ticket,
                                                 const int *cells, int ncells, int tier) {
