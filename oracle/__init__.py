@@ -11,7 +11,9 @@ Functions follow the paper:
 * :func:`compute` -- Voronoi (or radical) cells: the box of Eqs. (1)-(2)
   clipped by the half-spaces of Eq. (3); ``method="brute"`` clips by every
   particle and periodic image (the definition, Sec. 2.1.2), ``method="grid"``
-  walks the block grid outward and stops at the radius bound (Sec. 2.1.3).
+  walks the block grid outward and stops at the radius bound (Sec. 2.1.3);
+  ``clip`` starts every cell from a cube centred on its particle (clipped
+  cells, Sec. 3.1.3).
 * :func:`grid_size` -- the block-count rule of Sec. 2.1.4.
 * :func:`block_sort` -- the counting sort of particles into blocks
   (Sec. 2.1.1 and Sec. 2.2.5), written as a stable sort by block index.
@@ -62,7 +64,7 @@ def _load():
         P = ctypes.c_void_p
         lib.vo_compute.restype = ctypes.c_int
         lib.vo_compute.argtypes = [ctypes.c_int, ctypes.c_longlong, P, P, P, P, P,
-                                   ctypes.c_int, P, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_int, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_longlong, P, ctypes.c_int,
                                    P, P, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_int]
         lib.vo_grid_size.restype = None
@@ -136,13 +138,16 @@ def quantize_local_f32(pos, lo, hi, nblocks) -> np.ndarray:
 
 def compute(pos, lo, hi, periodic, radii=None, method: str = "grid", nblocks=None,
             cells=None, maxf: int | None = None, threads: int = 0,
-            tau_rel: float = TAU_REL, merge_rel: float = MERGE_REL) -> dict:
+            tau_rel: float = TAU_REL, merge_rel: float = MERGE_REL, clip: float = 0.0) -> dict:
     """Cells of the particles `cells` (default: all).  Returns a dict of
     per-cell arrays (vol, area, centroid relative to the particle, nv, ne,
     nf, status, rmax, ntested, ncut) and a CSR of faces (face_off, nbr_id,
     nbr_img (n_faces x 3), face_order) in canonical order: ascending
     (neighbour id, image shift), walls (negative ids) first.  In 2D, `vol`
-    is the area and `area` the perimeter."""
+    is the area and `area` the perimeter.  `clip` > 0: clipped cells
+    (Sec. 3.1.3), each starting from the box intersected with the cube (2D:
+    square) of side `clip` centred on its particle, whose faces count as
+    walls."""
     lib = _load()
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     n, d = pos.shape
@@ -183,7 +188,7 @@ def compute(pos, lo, hi, periodic, radii=None, method: str = "grid", nblocks=Non
     simg = np.zeros((nc, maxf, 3), dtype=np.int32)
     sord = np.zeros((nc, maxf), dtype=np.int32)
     rc = lib.vo_compute(d, n, _ptr(pos), _ptr(rad), _ptr(lo), _ptr(hi), _ptr(per), m, _ptr(nb),
-                        tau_rel, merge_rel, nc, _ptr(cl), maxf,
+                        tau_rel, merge_rel, float(clip), nc, _ptr(cl), maxf,
                         _ptr(vol), _ptr(area), _ptr(cen), _ptr(nv), _ptr(ne), _ptr(nf), _ptr(st),
                         _ptr(sid), _ptr(simg), _ptr(sord), _ptr(rmax), _ptr(ntest), _ptr(ncut),
                         int(threads))

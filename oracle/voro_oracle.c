@@ -92,6 +92,7 @@ typedef struct {
     double lo[3], hi[3], L[3];
     int per[3];
     double s, tau_rel, merge_rel, rmax;
+    double clip;       /* clipped cells (Sec. 3.1.3): cube side, 0 = none */
     /* grid */
     int nb[3];
     double h[3];
@@ -195,12 +196,32 @@ static int face_ok(double (*p)[3], int k, double eps) {
 /* ------------------------------------------------------------ 3D cell */
 
 /* Initial cell, Eqs. (1)-(2): the box relative to particle p. */
-static void init3(cell3 *cl, const ctx_t *cx, const double *p, long long self) {
-    double lo[3], hi[3];
-    for (int a = 0; a < 3; a++) {
+/* Initial cell bounds relative to p along each axis (Eqs. (1)-(2)): the box,
+ * or half the period on a periodic axis.  A clipped cell (Sec. 3.1.3) starts
+ * from the intersection with the cube of side `clip` centred on p; a face
+ * the cube supplies is a wall face (wall[a] set for a periodic axis whose
+ * half period exceeds the half side). */
+static void init_bounds(const ctx_t *cx, const double *p, int d, double *lo, double *hi, int *wall) {
+    for (int a = 0; a < d; a++) {
+        wall[a] = !cx->per[a];
         if (cx->per[a]) { lo[a] = -0.5 * cx->L[a]; hi[a] = 0.5 * cx->L[a]; }
         else { lo[a] = cx->lo[a] - p[a]; hi[a] = cx->hi[a] - p[a]; }
+        if (cx->clip > 0) {
+            const double hc = 0.5 * cx->clip;
+            if (cx->per[a]) {
+                if (hc < hi[a]) { lo[a] = -hc; hi[a] = hc; wall[a] = 1; }
+            } else {
+                if (-hc > lo[a]) lo[a] = -hc;
+                if (hc < hi[a]) hi[a] = hc;
+            }
+        }
     }
+}
+
+static void init3(cell3 *cl, const ctx_t *cx, const double *p, long long self) {
+    double lo[3], hi[3];
+    int wall[3];
+    init_bounds(cx, p, 3, lo, hi, wall);
     cl->nf = 0;
     cl->cap_hit = 0;
     for (int a = 0; a < 3; a++) {
@@ -210,7 +231,7 @@ static void init3(cell3 *cl, const ctx_t *cx, const double *p, long long self) {
             f->n[a] = side ? 1.0 : -1.0;
             f->c = side ? hi[a] : -lo[a];
             f->img[0] = f->img[1] = f->img[2] = 0;
-            if (cx->per[a]) { f->id = self; f->img[a] = side ? 1 : -1; }
+            if (!wall[a]) { f->id = self; f->img[a] = side ? 1 : -1; }
             else f->id = -(1 + 2 * a + side);
             int b = (a + 1) % 3, c = (a + 2) % 3, k = 0;
             for (int ib = 0; ib < 2; ib++)
@@ -308,10 +329,8 @@ static double maxr3(const cell3 *cl) {
 
 static void init2(cell2 *cl, const ctx_t *cx, const double *p, long long self) {
     double lo[2], hi[2];
-    for (int a = 0; a < 2; a++) {
-        if (cx->per[a]) { lo[a] = -0.5 * cx->L[a]; hi[a] = 0.5 * cx->L[a]; }
-        else { lo[a] = cx->lo[a] - p[a]; hi[a] = cx->hi[a] - p[a]; }
-    }
+    int wall[2];
+    init_bounds(cx, p, 2, lo, hi, wall);
     /* counter-clockwise: bottom (y-), right (x+), top (y+), left (x-) */
     double vx[4] = {lo[0], hi[0], hi[0], lo[0]}, vy[4] = {lo[1], lo[1], hi[1], hi[1]};
     int ax[4] = {1, 0, 1, 0}, sd[4] = {0, 1, 1, 0};
@@ -322,7 +341,7 @@ static void init2(cell2 *cl, const ctx_t *cx, const double *p, long long self) {
         cl->v[i][1] = vy[i];
         int a = ax[i], s = sd[i];
         cl->limg[i][0] = cl->limg[i][1] = 0;
-        if (cx->per[a]) { cl->lid[i] = self; cl->limg[i][a] = s ? 1 : -1; }
+        if (!wall[a]) { cl->lid[i] = self; cl->limg[i][a] = s ? 1 : -1; }
         else cl->lid[i] = -(1 + 2 * a + s);
     }
 }
@@ -629,13 +648,15 @@ static void stats2(const cell2 *cl, stats_t *st) {
  * `pos` (n x dim, FP64) in the box [lo, hi] with the given periodic flags.
  * `radii` (NULL: plain Voronoi) selects the radical variant.  `method` 0 is
  * the brute-force definition, 1 the block-grid walk with `nblocks` blocks.
- * Per-cell outputs are indexed by position in `cells`; faces go to slabs of
+ * `clip` > 0 gives clipped cells (Sec. 3.1.3): each cell starts from the
+ * box intersected with the cube of side `clip` centred on its particle, and
+ * the cube's faces are reported as walls.  Per-cell outputs are indexed by position in `cells`; faces go to slabs of
  * `maxf` entries per cell (id, image shift x3, face order), in canonical
  * order: ascending (id, image shift).  Returns 0, or -1 on bad arguments.
  */
 int vo_compute(int dim, long long n, const double *pos, const double *radii,
                const double *lo, const double *hi, const int *periodic,
-               int method, const int *nblocks, double tau_rel, double merge_rel,
+               int method, const int *nblocks, double tau_rel, double merge_rel, double clip,
                long long ncell, const long long *cells, int maxf,
                double *vol, double *area, double *cen, int *nv, int *ne, int *nf,
                int *status, long long *nbr_id, int *nbr_img, int *face_order,
@@ -655,6 +676,7 @@ int vo_compute(int dim, long long n, const double *pos, const double *radii,
     cx.s = pow(V / (n > 0 ? (double)n : 1.0), 1.0 / dim);
     cx.tau_rel = tau_rel;
     cx.merge_rel = merge_rel;
+    cx.clip = clip > 0 ? clip : 0.0;
     cx.rmax = 0;
     if (radii) for (long long i = 0; i < n; i++) if (radii[i] > cx.rmax) cx.rmax = radii[i];
     long long nblk = 1;
