@@ -101,6 +101,11 @@ typedef struct {
     int collect_stats; /* 1 = fill the per-cell work counters */
     int time_kernels;  /* 1 = record CUDA events around the cell kernels on the
                           context's stream (read with vg_get_kernel_ms) */
+    double clip;       /* clipped cells (Sec. 3.1.3): > 0 starts every cell
+                          from the box intersected with the cube (2D: square)
+                          of side `clip` centred on its particle; the cube's
+                          faces are reported as walls (ids -1..-6 by axis and
+                          side).  0 (default): plain cells */
 } vg_config;
 
 /* Fills `cfg` with the defaults listed above (FP32_RETEST, PREFETCH). */

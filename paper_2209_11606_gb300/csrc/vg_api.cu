@@ -366,6 +366,7 @@ vg_status check_config(vg_ctx *c, const vg_config &cfg, bool inserts = false) {
     if (cfg.precision != VG_FP64 && cfg.precision != VG_FP32_RETEST) return fail(c, VG_ERR_ARG, "precision");
     if (cfg.order != VG_WALK && cfg.order != VG_PREFETCH) return fail(c, VG_ERR_ARG, "order");
     if (!(cfg.tol32 > 0) || !(cfg.tau_rel > 0) || !(cfg.merge_rel > 0)) return fail(c, VG_ERR_ARG, "tolerances");
+    if (!(cfg.clip >= 0) || !(cfg.clip < 1e300)) return fail(c, VG_ERR_ARG, "clip must be finite and >= 0");
     if (cfg.warps_per_cta > 4) return fail(c, VG_ERR_ARG, "warps_per_cta above 4 (CTAs of at most 128 threads)");
     if (cfg.use_mlp && !c->kblock_valid && !(inserts && c->pred))
         return fail(c, VG_ERR_STATE, "use_mlp without vg_mlp_predict after the insert");
@@ -382,6 +383,7 @@ cudaError_t enqueue_cells(vg_ctx *c, const vg_config &cfg, cudaStream_t s, const
     st.n = (int)c->n; st.radical = c->radical;
     Params pp;
     pp.tol32 = cfg.tol32; pp.tau_rel = cfg.tau_rel; pp.merge_rel = cfg.merge_rel;
+    pp.clip = cfg.clip;
     pp.prefetch_k = cfg.prefetch_k; pp.order = cfg.order;
     pp.chunk = cfg.chunk > 0 ? cfg.chunk : 2;
     pp.collect = cfg.collect_stats ? 1 : 0;
@@ -436,6 +438,7 @@ void vg_config_default(vg_config *cfg) {
     cfg->tol32 = 1e-5;
     cfg->tau_rel = 1e-11;
     cfg->merge_rel = 1e-9;
+    cfg->clip = 0.0;
     cfg->prefetch_k = 0;
     cfg->use_mlp = 0;
     cfg->chunk = 0;

@@ -43,6 +43,7 @@ struct CellC2 {
     int i, self_id, b[2];
     double p[2], rp;
     double rmax;  // largest radius of the cell's system (radical) or 0
+    double hc;    // clipped cells: half the square side, 0 = none
 };
 
 template <typename T, int CAP>
@@ -137,6 +138,8 @@ __device__ __forceinline__ void line64(const Grid &g, const Store &s, const Cell
         n[0] = n[1] = 0.0;
         n[a] = side ? 1.0 : -1.0;
         cst = side ? __dsub_rn(g.hi[a], c.p[a]) : __dsub_rn(c.p[a], g.lo[a]);
+        // a clipped cell's square side (on a periodic axis every wall is one)
+        if (c.hc > 0.0 && (g.per[a] || c.hc < cst)) cst = c.hc;
         return;
     }
     const D4 q = s.p64[ref];
@@ -246,6 +249,7 @@ __global__ void __launch_bounds__(128, VG2_MINB) k_cells2(const __grid_constant_
             S.cc.p[0] = p64.x; S.cc.p[1] = p64.y;
             S.cc.rp = p64.w;
             S.cc.rmax = st.radical ? (BATCH ? S.sysc.rmax : st.sys[0].rmax) : 0.0;
+            S.cc.hc = 0.5 * pp.clip;
             S.cnt[0] = S.cnt[1] = S.cnt[2] = S.cnt[3] = 0;
         }
         __syncwarp(gmask);
@@ -271,13 +275,28 @@ __global__ void __launch_bounds__(128, VG2_MINB) k_cells2(const __grid_constant_
                     hi[a] = g.hi[a] - S.cc.p[a];
                 }
             }
+            // clipped cells (Sec. 3.1.3): the box meets the square of side clip
+            // around the particle; on a periodic axis a square smaller than the
+            // period replaces the self-image lines by walls
+            if (pp.clip > 0.0) {
+                const T hc = (T)(0.5 * pp.clip);
+#pragma unroll
+                for (int a = 0; a < 2; a++) {
+                    if (g.per[a]) {
+                        if (pp.clip < g.L[a]) { lo[a] = -hc; hi[a] = hc; }
+                    } else {
+                        lo[a] = lo[a] > -hc ? lo[a] : -hc;
+                        hi[a] = hi[a] < hc ? hi[a] : hc;
+                    }
+                }
+            }
             if (gl < 4) {
                 // lines: 0 x-, 1 x+, 2 y-, 3 y+
                 const int a = gl >> 1, side = gl & 1;
                 T n[2] = {0, 0};
                 T c;
                 int ref, img;
-                if (g.per[a]) {
+                if (g.per[a] && !(pp.clip > 0.0 && pp.clip < g.L[a])) {
                     const T L = F32 ? (T)g.Lf[a] : (T)g.L[a];
                     n[a] = side ? L : -L;
                     c = (T)0.5 * L * L;

@@ -98,6 +98,7 @@ struct CellC {
     double p[3];  // FP64 position
     double rp;    // radius (radical) or 0
     double rmax;  // largest radius of the cell's system (radical) or 0
+    double hc;    // clipped cells: half the cube side, 0 = none
 };
 
 // Candidate source, warp-uniform.
@@ -337,6 +338,8 @@ __device__ __forceinline__ void plane64(const Grid &g, const Store &s, const Cel
         n[0] = n[1] = n[2] = 0.0;
         n[a] = side ? 1.0 : -1.0;
         c = side ? __dsub_rn(g.hi[a], ci.p[a]) : __dsub_rn(ci.p[a], g.lo[a]);
+        // a clipped cell's cube face (on a periodic axis every wall is one)
+        if (ci.hc > 0.0 && (g.per[a] || ci.hc < c)) c = ci.hc;
         return;
     }
     D4 q = s.p64[ref];
@@ -527,6 +530,7 @@ __global__ void VG_BOUNDS
                     S.cc.p[0] = p64.x; S.cc.p[1] = p64.y; S.cc.p[2] = p64.z;
                     S.cc.rp = p64.w;
                     S.cc.rmax = st.radical ? (BATCH ? S.sysc.rmax : st.sys[0].rmax) : 0.0;
+                    S.cc.hc = 0.5 * pp.clip;
                 }
                 if (pp.collect && gl < 6) S.cnt[gl] = 0;
             }
@@ -551,12 +555,27 @@ __global__ void VG_BOUNDS
                         hi[a] = g.hi[a] - S.cc.p[a];
                     }
                 }
+                // clipped cells (Sec. 3.1.3): the box meets the cube of side clip
+                // around the particle; on a periodic axis a cube smaller than the
+                // period replaces the self-image planes by walls
+                if (VG_RARE(pp.clip > 0.0)) {
+                    const T hc = (T)(0.5 * pp.clip);
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        if (g.per[a]) {
+                            if (pp.clip < g.L[a]) { lo[a] = -hc; hi[a] = hc; }
+                        } else {
+                            lo[a] = lo[a] > -hc ? lo[a] : -hc;
+                            hi[a] = hi[a] < hc ? hi[a] : hc;
+                        }
+                    }
+                }
                 if (gl < 6) {
                     const int a = gl >> 1, side = gl & 1;
                     T n[3] = {0, 0, 0};
                     T c;
                     int ref, img;
-                    if (g.per[a]) {
+                    if (g.per[a] && !(pp.clip > 0.0 && pp.clip < g.L[a])) {
                         if constexpr (F32) {
                             n[a] = side ? g.Lf[a] : -g.Lf[a];
                             c = 0.5f * g.Lf[a] * g.Lf[a];

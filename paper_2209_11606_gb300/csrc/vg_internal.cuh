@@ -91,6 +91,7 @@ struct Params {
     int chunk;
     int collect;
     const float *kblock;   // per-block candidate target from the MLP, or null
+    double clip;           // clipped cells: cube side, 0 = none
 };
 
 // Hardware approximations (PTX rcp/sqrt/lg2/ex2 .approx, a few ulps) where
