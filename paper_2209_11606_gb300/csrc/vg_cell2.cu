@@ -344,7 +344,8 @@ __global__ void __launch_bounds__(128, VG2_MINB) k_cells2(const __grid_constant_
 
         // ------------------------------------------- walk (Sec. 2.1.3), per block
         const float hmin = fminf(g.hf[0], g.hf[1]);
-        const int maxs = SY.off_shell + 4 + 2 * max(g.nb[0], g.nb[1]);
+        // shells up to 23000 keep (2 shell + 1)^2 within 32-bit indices
+        const int maxs = min(23000, SY.off_shell + 4 + 2 * max(g.nb[0], g.nb[1]));
         const int ocount = SY.off_count, obase = SY.off_base;
         int e = 0, shell = 0, sidx = 0, mode = 1;  // 1 list, 2 shells, 3 done
         for (int guard = 0; guard < (1 << 30) && mode != 3 && !(flags & 6); guard++) {

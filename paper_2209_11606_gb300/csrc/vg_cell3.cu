@@ -1016,7 +1016,8 @@ __global__ void VG_BOUNDS
                         const float hmin = fminf(g.hf[0], fminf(g.hf[1], g.hf[2]));
                         const float sb = (float)(shell - 1) * hmin;
                         if ((T)(sb * sb) * (T)0.99998 >= stop) { src.mode = 3; continue; }
-                        const int maxs = SY.off_shell + MAX_SHELL_EXTRA + 2 * max(g.nb[0], max(g.nb[1], g.nb[2]));
+                        // shells up to 640 keep (2 shell + 1)^3 within 32-bit indices
+                        const int maxs = min(640, SY.off_shell + MAX_SHELL_EXTRA + 2 * max(g.nb[0], max(g.nb[1], g.nb[2])));
                         if (shell > maxs) { src.limit = 1; src.mode = 3; continue; }
                         const int wd = 2 * shell + 1, sidx = src.sidx;
                         if (sidx >= wd * wd * wd) { src.shell = shell + 1; src.sidx = 0; continue; }
