@@ -170,6 +170,53 @@ __device__ __forceinline__ int pack_img(int mx, int my, int mz) {
 // classifying it; every kept candidate still goes through the exact test.
 // A free slot holds (0, 0, 0, 0): it keeps a candidate only if c <= 0 (a
 // radical plane that the particle itself lies beyond), which is harmless.
+// Member si of the surface of Chebyshev shell s (the (2s+1)^3 cube minus its
+// interior): two z faces of (2s+1)^2 blocks, two y faces of (2s+1)(2s-1),
+// two x faces of (2s-1)^2.
+__device__ __forceinline__ void shell_member(int si, int s, int &ox, int &oy, int &oz) {
+    const int wd = 2 * s + 1, fa = wd * wd, fb = wd * (wd - 2), fc = (wd - 2) * (wd - 2);
+    if (si < 2 * fa) {
+        const int r = si < fa ? si : si - fa;
+        oz = si < fa ? -s : s;
+        ox = r % wd - s;
+        oy = r / wd - s;
+    } else if (si < 2 * (fa + fb)) {
+        const int t = si - 2 * fa, r = t < fb ? t : t - fb;
+        oy = t < fb ? -s : s;
+        ox = r % wd - s;
+        oz = r / wd - (s - 1);
+    } else {
+        const int t = si - 2 * (fa + fb), r = t < fc ? t : t - fc;
+        ox = t < fc ? -s : s;
+        oy = r % (wd - 2) - (s - 1);
+        oz = r / (wd - 2) - (s - 1);
+    }
+}
+
+// Block bound (Sec. 2.1.3): a particle q can cut the cell only if some vertex v
+// lies beyond its plane, |q - v|^2 < |v|^2 (radical: + rmax^2 - r_p^2, the
+// largest radius bounding r_q), so a block whose box [lo, hi] (relative to
+// the particle) meets none of those balls holds no cutting particle.  Each
+// ball is widened by sl * kappa (FP32 vertex error) and 1e-4 relative.
+__device__ __noinline__ bool block_touches(const float4 *v4, int n, float lo0, float lo1, float lo2, float hi0,
+                                           float hi1, float hi2, float extra, float sl) {
+    bool m = false;
+#pragma unroll 1
+    for (int t0 = 0; t0 < n; t0 += 8) {
+#pragma unroll
+        for (int t = t0; t < t0 + 8; t++) {
+            const float4 v = v4[t];
+            const float dx = fmaxf(0.f, fmaxf(lo0 - v.x, v.x - hi0));
+            const float dy = fmaxf(0.f, fmaxf(lo1 - v.y, v.y - hi1));
+            const float dz = fmaxf(0.f, fmaxf(lo2 - v.z, v.z - hi2));
+            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float rv = sqrt_a(fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, extra)))) + sl * v.w;
+            m |= d2 < rv * rv * 1.0001f;
+        }
+    }
+    return m;
+}
+
 // Only the first n entries are read: the rows of slots that hold any vertex
 // (n a multiple of 8).
 __device__ __forceinline__ bool may_cut(const float4 *v4, int n, float qx, float qy, float qz, float c, float tau) {
@@ -1019,20 +1066,20 @@ __global__ void VG_BOUNDS
                         // shells up to 640 keep (2 shell + 1)^3 within 32-bit indices
                         const int maxs = min(640, SY.off_shell + MAX_SHELL_EXTRA + 2 * max(g.nb[0], max(g.nb[1], g.nb[2])));
                         if (shell > maxs) { src.limit = 1; src.mode = 3; continue; }
+                        // the shell's surface only: two z faces (wd^2 each), two y faces
+                        // (wd (wd - 2)), two x faces ((wd - 2)^2)
                         const int wd = 2 * shell + 1, sidx = src.sidx;
-                        if (sidx >= wd * wd * wd) { src.shell = shell + 1; src.sidx = 0; continue; }
+                        const int fa = wd * wd, fb = wd * (wd - 2), fc = (wd - 2) * (wd - 2);
+                        if (sidx >= 2 * (fa + fb + fc)) { src.shell = shell + 1; src.sidx = 0; continue; }
                         const int si = sidx + gl;
-                        if (si < wd * wd * wd) {
-                            ox = si % wd - shell;
-                            oy = (si / wd) % wd - shell;
-                            oz = si / (wd * wd) - shell;
+                        if (si < 2 * (fa + fb + fc)) {
+                            shell_member(si, shell, ox, oy, oz);
                             const float lbmax = (float)SY.off_shell * hmin;
                             const float lbx = fmaxf(0.f, (float)(abs(ox) - 1)) * g.hf[0];
                             const float lby = fmaxf(0.f, (float)(abs(oy) - 1)) * g.hf[1];
                             const float lbz = fmaxf(0.f, (float)(abs(oz) - 1)) * g.hf[2];
                             // shell members that the offset list did not hold
-                            cand = max(abs(ox), max(abs(oy), abs(oz))) == shell &&
-                                   !(lbx * lbx + lby * lby + lbz * lbz < lbmax * lbmax);
+                            cand = !(lbx * lbx + lby * lby + lbz * lbz < lbmax * lbmax);
                         }
                         src.sidx = sidx + G;
                     }
@@ -1047,6 +1094,18 @@ __global__ void VG_BOUNDS
                             j0b = __ldg(&st.bstart[kk]);
                             len = __ldg(&st.bstart[kk + 1]) - j0b;
                             cand = len > 0;
+                            if constexpr (F32) {
+                                // beyond the offset list (extended cells): the block bound, for
+                                // blocks whose particles would cost more than the test
+                                if (cand && mode == 2 && len >= 8) {
+                                    const float bl0 = (float)ox * g.hf[0] - o0, bl1 = (float)oy * g.hf[1] - o1,
+                                                bl2 = (float)oz * g.hf[2] - o2;
+                                    const float ex = st.radical ? (float)(S.cc.rmax * S.cc.rmax - S.cc.rp * S.cc.rp) : 0.f;
+                                    const float sl = 1e-5f * (sqrt_a((float)r2) + fmaxf(g.hf[0], fmaxf(g.hf[1], g.hf[2])));
+                                    cand = block_touches(S.v4, G * (32 - __clz(rows)), bl0, bl1, bl2, bl0 + g.hf[0],
+                                                         bl1 + g.hf[1], bl2 + g.hf[2], fmaxf(ex, 0.f), sl);
+                                }
+                            }
                             // particles the prefetch already offered: inside its
                             // block box, in a row it gathered, closer than its radius
                             const float rho2 = src.rho2;

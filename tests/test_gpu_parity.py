@@ -162,3 +162,18 @@ def test_radical_2d(precision, order, rtol):
     # rounding of both implementations is amplified by those edges'
     # conditioning (observed 4e-12), so the FP64 bar for them is 1e-11
     assert rep["area_max_rel"] <= max(rtol, 1e-11), rep
+
+
+@pytest.mark.parametrize("precision,order,rtol", FORMS)
+def test_localized_extended_cells(precision, order, rtol):
+    # Sec. 3.1 'localized': the cells at the cluster's surface reach the walls,
+    # so their walks run far past the offset list (shell enumeration and, in
+    # the FP32 form, the block bound)
+    s = W.localized(200_000, 3, 0.1, seed=31)
+    check(s, (27, 27, 27), precision, order, rtol)
+
+
+@pytest.mark.parametrize("precision,order,rtol", FORMS[:2])
+def test_extreme_clustering_3d(precision, order, rtol):
+    s = W.extreme_clustering(20_000, 3, seed=32)
+    check(s, (34, 34, 34), precision, order, rtol)
