@@ -29,6 +29,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -52,7 +53,20 @@ WORKLOADS = {
     "hex10m": ("hex10m: 2D, 10,000,314 points of a perturbed hexagonal lattice (2943 x 3398, sigma 0.05 of the "
                "column spacing, seed 3) in the periodic unit square, blocks by the n_opt = 3.4 rule; "
                "chosen form = FP32 cuts + FP64 re-test, block walk"),
+    # the three example cases of Sec. 3.1 (walled unit cube, N = 10^8, grids of
+    # Table 3) and the clipped cells of Sec. 3.1.3
+    "homog3d": ("homog3d: 10^8 points uniform in the walled unit cube (seed 11), 279^3 blocks (Table 3, "
+                "n_opt 4.6); chosen form = FP32 cuts + FP64 re-test, distance-sorted preload (72)"),
+    "local3d": ("local3d: the 9,999,326 of 10^8 uniform points (seed 12) inside the central cube of volume 0.1, "
+                "walled unit cube, 126^3 blocks (Table 3, n_opt 49); chosen form = FP32 cuts + FP64 re-test, "
+                "distance-sorted preload (72), block bound beyond the near shells"),
+    "local3d_clip": ("local3d_clip: local3d with every cell clipped by the cube of side 1.5 sqrt(3) d0, "
+                     "d0 = (10^8)^(-1/3) (Sec. 3.1.3); chosen form as local3d"),
+    "extreme3d": ("extreme3d: 10^8 points, each coordinate 1/2 + 4 (X - 1/2)^3 (seed 13), walled unit cube, "
+                  "584^3 blocks (Table 3, n_opt 0.5); chosen form = FP32 cuts + FP64 re-test, "
+                  "distance-sorted preload (72)"),
 }
+PAPER3D = ("homog3d", "local3d", "local3d_clip", "extreme3d")
 METRIC_2D = "2D Voronoi cells/s, 1 GB300, chosen vs plain FP64 form; % of roofline"
 # FP32 peak derived from unit counts and clock: 152 SMs x 128 FP32 lanes x
 # 2 FLOP (FMA) x 2.07 GHz
@@ -65,7 +79,7 @@ FLOP_VTEST, FLOP_CAND, FLOP_NEWV, FLOP_FANTET = 6, 12, 51, 42
 # DRAM bytes (read + write) of one k_cells3<float,2,64> launch over the 1M
 # uniform cells, from the ncu capture summarised in
 # profiles/k_cells3_fp32_uniform1m_ncu.md (null for other workloads)
-CELL_KERNEL_DRAM_BYTES_UNIFORM1M = 174.202e6 + 287.125e6
+CELL_KERNEL_DRAM_BYTES_UNIFORM1M = 172.645e6 + 289.882e6
 MLP_ALPHA, MLP_KMIN, MLP_KMAX = 1.5, 24.0, 1024.0
 PKG = os.path.join(ROOT, "paper_2209_11606_gb300")
 MLP_PARAMS = os.path.join(PKG, "mlp_params_gb300.json")
@@ -82,12 +96,25 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the alternative FP32 forms")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 form")
     return ap.parse_args()
+
+
+def clip_of(name: str) -> float:
+    """Cube side of the clipped cells of Sec. 3.1.3 (0: plain cells)."""
+    return 1.5 * math.sqrt(3.0) * 1e8 ** (-1.0 / 3.0) if name == "local3d_clip" else 0.0
 
 
 def workload(name: str, rank: int):
     """(system, block grid or None for the n_opt rule, chosen order, learned preload)."""
     from paper_2209_11606_gb300 import workloads as W
+    if name == "homog3d":
+        return W.uniform(100_000_000, 3, 1.0, False, seed=11 + rank), (279,) * 3, "prefetch", False
+    if name in ("local3d", "local3d_clip"):
+        return W.localized(100_000_000, 3, 0.1, seed=12 + rank), (126,) * 3, "prefetch", False
+    if name == "extreme3d":
+        return W.extreme_clustering(100_000_000, 3, seed=13 + rank), (584,) * 3, "prefetch", False
     if name == "uniform1m":
         return W.uniform(1_000_000, 3, 100.0, True, seed=1 + rank), (58, 58, 58), "prefetch", True
     if name == "slabs102m":
@@ -238,7 +265,7 @@ def batched_run(V, torch, stream, flush, mlp, steps: int = 5, seed: int = 5):
         V.vg_destroy(ctx)
 
 
-def cpu_baseline(s, grid, cells: int, seed: int = 0):
+def cpu_baseline(s, grid, cells: int, seed: int = 0, clip: float = 0.0):
     """Times the FP64 oracle on a sample of `cells` cells of system s."""
     import oracle
     rng = np.random.default_rng(seed)
@@ -249,7 +276,7 @@ def cpu_baseline(s, grid, cells: int, seed: int = 0):
         grid = oracle.grid_size(s.n, s.lo, s.hi, 4.6 if s.dim == 3 else 3.4)
     t0 = time.perf_counter()
     oracle.compute(s.pos, s.lo, s.hi, s.periodic, radii=s.radii, method="grid", nblocks=grid, cells=sample,
-                   threads=threads)
+                   threads=threads, clip=clip)
     dt = time.perf_counter() - t0
     return {"value": len(sample) / dt, "unit": "cells/s", "cores": threads, "kind": "oracle",
             "sample": f"{len(sample)} random cells of the {s.n}-point workload (FP64 block-grid "
@@ -263,11 +290,11 @@ def run_reference(args, rank, world):
     s, grid, _, _ = workload(args.workload, 0)
     per_step = 100_000
     for _ in range(args.warmup):
-        cpu_baseline(s, grid, 20_000, seed=99)
+        cpu_baseline(s, grid, 20_000, seed=99, clip=clip_of(args.workload))
     total, cells = 0.0, 0
     res = None
     for k in range(args.steps):
-        res = cpu_baseline(s, grid, per_step, seed=k)
+        res = cpu_baseline(s, grid, per_step, seed=k, clip=clip_of(args.workload))
         total += res["seconds"]
         cells += per_step
     v = cells / total
@@ -304,7 +331,7 @@ def main():
     B.build()
     from paper_2209_11606_gb300 import predictor as P, vorogpu as V
 
-    big = args.workload == "slabs102m"
+    big = args.workload in ("slabs102m",) + PAPER3D
     s, grid, chosen_order, learned_on = workload(args.workload, rank)
     n, dim = s.n, s.dim
     order_code = V.VG_PREFETCH if chosen_order == "prefetch" else V.VG_WALK
@@ -317,8 +344,10 @@ def main():
     ctx = V.vg_create(dim, s.lo, s.hi, s.periodic, grid, stream=stream)
     if learned_on:
         V.vg_set_predictor(ctx, mlp, MLP_ALPHA, MLP_KMIN, MLP_KMAX)
+    clip = clip_of(args.workload)
     cfg = V.vg_config_default()
     cfg.precision, cfg.order, cfg.use_mlp = V.VG_FP32_RETEST, order_code, int(learned_on)
+    cfg.clip = clip
 
     # warm-up through the eager calls, then the step as one graph: sort ->
     # learned preload targets -> cells -> faces, the cell kernels timed by
@@ -328,6 +357,7 @@ def main():
         V.vg_compute(ctx, cfg)
     torch.cuda.synchronize()
     gcfg = V.vg_config_default()
+    gcfg.clip = clip
     gcfg.precision, gcfg.order, gcfg.use_mlp, gcfg.time_kernels = cfg.precision, cfg.order, cfg.use_mlp, 1
     V.vg_graph_capture(ctx, [n], pos_d, rad_d, gcfg)
     for _ in range(max(args.warmup, 3)):
@@ -398,6 +428,7 @@ def main():
     learned = None
     if learned_on:
         c_fixed = V.vg_config_default()
+        c_fixed.clip = clip
         w_fixed, fb_fixed = work(c_fixed)
         learned = {"fallback_rate": float(fb.mean()), "preload_per_cell": float(w["p"].mean()),
                    "fixed_k_fallback_rate": float(fb_fixed.mean()),
@@ -408,6 +439,7 @@ def main():
     def form_rate(order, use_mlp, precision=V.VG_FP32_RETEST, reps=5):
         c2 = V.vg_config_default()
         c2.precision, c2.order, c2.use_mlp = precision, order, use_mlp
+        c2.clip = clip
         V.vg_graph_capture(ctx, [n], pos_d, rad_d, c2)
         V.vg_graph_launch(ctx)
         V.vg_graph_sync(ctx)
@@ -415,11 +447,11 @@ def main():
         return n * reps / (sum(ms) / 1000.0)
 
     forms = {}
-    if learned_on or chosen_order != "walk":
+    if not args.no_forms and (learned_on or chosen_order != "walk"):
         forms["fp32_walk"] = form_rate(V.VG_WALK, 0)
-    if dim == 3 and (learned_on or chosen_order != "prefetch"):
+    if not args.no_forms and dim == 3 and (learned_on or chosen_order != "prefetch"):
         forms["fp32_prefetch_fixed_k72"] = form_rate(V.VG_PREFETCH, 0)
-    plain64 = form_rate(V.VG_WALK, 0, V.VG_FP64, reps=1 if big else 3)
+    plain64 = None if args.no_plain else form_rate(V.VG_WALK, 0, V.VG_FP64, reps=1 if big else 3)
 
     # ---- end to end through the public API, host buffers -----------------------
     e2e = None
@@ -463,9 +495,9 @@ def main():
             "step": "one CUDA graph replay: counting sort, learned preload targets, cell kernels "
                     "(3 capacity tiers), face CSR",
             "roofline": roof,
-            "plain_fp64": {"value": plain64, "unit": "cells/s",
-                           "form": "FP64 everywhere, block walk (Sec. 2.1.3), graph replay"},
-            "chosen_vs_plain": value / world / plain64,
+            "plain_fp64": None if plain64 is None else
+            {"value": plain64, "unit": "cells/s", "form": "FP64 everywhere, block walk (Sec. 2.1.3), graph replay"},
+            "chosen_vs_plain": None if plain64 is None else value / world / plain64,
             "forms": forms, "learned_preload": learned,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "retest_per_cell": float(w["r"].mean())}
@@ -473,7 +505,8 @@ def main():
         line["batched"] = batched_run(V, torch, stream, flush, mlp)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = {k: v for k, v in
-                                cpu_baseline(s, grid, n if args.workload == "uniform1m" else 100_000).items()
+                                cpu_baseline(s, grid, n if args.workload == "uniform1m" else 100_000,
+                                             clip=clip).items()
                                 if k != "seconds"}
     V.vg_destroy(ctx)
     V.vg_mlp_destroy(mlp)
