@@ -66,7 +66,7 @@ def _load():
         lib.vo_compute.argtypes = [ctypes.c_int, ctypes.c_longlong, P, P, P, P, P,
                                    ctypes.c_int, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_longlong, P, ctypes.c_int,
-                                   P, P, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_int]
+                                   P, P, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_int, P, P, P]
         lib.vo_grid_size.restype = None
         lib.vo_grid_size.argtypes = [ctypes.c_int, ctypes.c_longlong, P, P, ctypes.c_double,
                                      ctypes.c_int, P]
@@ -138,7 +138,8 @@ def quantize_local_f32(pos, lo, hi, nblocks) -> np.ndarray:
 
 def compute(pos, lo, hi, periodic, radii=None, method: str = "grid", nblocks=None,
             cells=None, maxf: int | None = None, threads: int = 0,
-            tau_rel: float = TAU_REL, merge_rel: float = MERGE_REL, clip: float = 0.0) -> dict:
+            tau_rel: float = TAU_REL, merge_rel: float = MERGE_REL, clip: float = 0.0,
+            weinberg: bool = False) -> dict:
     """Cells of the particles `cells` (default: all).  Returns a dict of
     per-cell arrays (vol, area, centroid relative to the particle, nv, ne,
     nf, status, rmax, ntested, ncut) and a CSR of faces (face_off, nbr_id,
@@ -147,7 +148,10 @@ def compute(pos, lo, hi, periodic, radii=None, method: str = "grid", nblocks=Non
     is the area and `area` the perimeter.  `clip` > 0: clipped cells
     (Sec. 3.1.3), each starting from the box intersected with the cube (2D:
     square) of side `clip` centred on its particle, whose faces count as
-    walls."""
+    walls.  `weinberg`: also the Weinberg code of each 3D cell's edge graph
+    (Sec. 4) as `w_len` (darts, 2E), `w_hash` (FNV-1a 64 over the 2E+1 vertex
+    labels of the minimal code, two little-endian bytes each) and `w_sym` (the
+    number of start darts and orientations that give it)."""
     lib = _load()
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     n, d = pos.shape
@@ -187,20 +191,26 @@ def compute(pos, lo, hi, periodic, radii=None, method: str = "grid", nblocks=Non
     sid = np.zeros((nc, maxf), dtype=np.int64)
     simg = np.zeros((nc, maxf, 3), dtype=np.int32)
     sord = np.zeros((nc, maxf), dtype=np.int32)
+    wl = np.zeros(nc, dtype=np.int32) if weinberg else None
+    wh = np.zeros(nc, dtype=np.uint64) if weinberg else None
+    ws = np.zeros(nc, dtype=np.int32) if weinberg else None
     rc = lib.vo_compute(d, n, _ptr(pos), _ptr(rad), _ptr(lo), _ptr(hi), _ptr(per), m, _ptr(nb),
                         tau_rel, merge_rel, float(clip), nc, _ptr(cl), maxf,
                         _ptr(vol), _ptr(area), _ptr(cen), _ptr(nv), _ptr(ne), _ptr(nf), _ptr(st),
                         _ptr(sid), _ptr(simg), _ptr(sord), _ptr(rmax), _ptr(ntest), _ptr(ncut),
-                        int(threads))
+                        int(threads), _ptr(wl), _ptr(wh), _ptr(ws))
     if rc != 0:
         raise ValueError("oracle rejected its arguments")
     nfc = np.where(st == ST_OK, nf, 0).astype(np.int64)
     off = np.zeros(nc + 1, dtype=np.int64)
     np.cumsum(nfc, out=off[1:])
     mask = np.arange(maxf)[None, :] < nfc[:, None]
-    return {
+    out = {
         "vol": vol, "area": area, "centroid": cen, "nv": nv, "ne": ne, "nf": nf,
         "status": st, "rmax": rmax, "ntested": ntest, "ncut": ncut,
         "face_off": off, "nbr_id": sid[mask], "nbr_img": simg[mask][:, :d] if d < 3 else simg[mask],
         "face_order": sord[mask],
     }
+    if weinberg:
+        out.update({"w_len": wl, "w_hash": wh, "w_sym": ws})
+    return out

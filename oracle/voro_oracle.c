@@ -541,7 +541,81 @@ static int cell_grid(const ctx_t *cx, job_t *jb, const int *bp) {
 typedef struct {
     double vol, area, cen[3], R;
     int nv, ne, nf;
+    /* Weinberg code of the edge graph (Sec. 4): darts traversed (2E, 0 when
+     * not computed), FNV-1a 64 hash of the 2E+1 vertex labels (each label
+     * as two little-endian bytes), number of (start, orientation) pairs that
+     * give the minimal code */
+    int wlen, wsym;
+    unsigned long long whash;
 } stats_t;
+
+/* Weinberg's traversal of a planar graph given by its darts (from, to), the
+ * reverse of each dart and a rotation rot[d]: the next dart leaving from[d]
+ * in cyclic order.  From a start dart, arriving at y by dart d: at a new
+ * vertex leave by the next dart after the reverse of d; at an old vertex
+ * return along the reverse of d if it is untraversed, else leave by the
+ * first untraversed dart after the reverse of d.  The code lists the labels
+ * (order of first visit, from 1) of the start and of every arrival, 2E + 1
+ * entries.  The cell's code is the lexicographic minimum over every start
+ * dart and both rotation directions; `sym` counts the pairs that reach it.
+ * Returns 0 if some traversal ends before using every dart. */
+static int weinberg(int V, int D, const int *dfrom, const int *dto, const int *rev, const int *rot,
+                    const int *rotinv, int *best, int *cur, int *lab, unsigned char *used, int *sym) {
+    int have = 0;
+    *sym = 0;
+    for (int o = 0; o < 2; o++) {
+        const int *R = o ? rotinv : rot;
+        for (int s0 = 0; s0 < D; s0++) {
+            for (int v = 0; v < V; v++) lab[v] = 0;
+            memset(used, 0, (size_t)D);
+            int nl = 1, d = s0;
+            lab[dfrom[s0]] = nl;
+            cur[0] = 1;
+            for (int k = 0; k < D; k++) {
+                used[d] = 1;
+                const int y = dto[d];
+                int nd = -1;
+                if (!lab[y]) {
+                    lab[y] = ++nl;
+                    nd = R[rev[d]];
+                } else if (!used[rev[d]]) {
+                    nd = rev[d];
+                } else {
+                    int e = R[rev[d]];
+                    while (used[e] && e != rev[d]) e = R[e];
+                    if (!used[e]) nd = e;
+                }
+                cur[k + 1] = lab[y];
+                if (k + 1 < D) {
+                    if (nd < 0) return 0;
+                    d = nd;
+                }
+            }
+            int c = 0;
+            if (have)
+                for (int k = 0; k <= D && !c; k++) c = cur[k] < best[k] ? -1 : (cur[k] > best[k] ? 1 : 0);
+            if (!have || c < 0) {
+                memcpy(best, cur, sizeof(int) * (size_t)(D + 1));
+                have = 1;
+                *sym = 1;
+            } else if (c == 0) {
+                (*sym)++;
+            }
+        }
+    }
+    return 1;
+}
+
+static unsigned long long fnv1a_labels(const int *code, int n) {
+    unsigned long long h = 14695981039346656037ull;
+    for (int k = 0; k < n; k++) {
+        h ^= (unsigned long long)(code[k] & 0xff);
+        h *= 1099511628211ull;
+        h ^= (unsigned long long)((code[k] >> 8) & 0xff);
+        h *= 1099511628211ull;
+    }
+    return h;
+}
 
 /* 3D: volume and centroid by fans from each face's first vertex to a fixed
  * apex o (the tetrahedral decomposition of a closed surface does not depend
@@ -613,6 +687,56 @@ static void stats3(const cell3 *cl, double eps, stats_t *st, int *forder) {
     st->nv = nv;
     st->ne = ne;
     st->R = maxr3(cl);
+    /* darts of the merged face cycles (faces are counterclockwise seen from
+     * outside, so each dart lies on exactly one face); rot(v->w) = (v->u) with
+     * u the vertex before v on the face of v->w */
+    st->wlen = 0; st->wsym = 0; st->whash = 0;
+    {
+        int D = 0;
+        int *df = (int *)malloc(sizeof(int) * (tot ? tot : 1)), *dt = (int *)malloc(sizeof(int) * (tot ? tot : 1));
+        int *dp = (int *)malloc(sizeof(int) * (tot ? tot : 1));
+        k = 0;
+        int ok = 1;
+        for (int i = 0; i < cl->nf; i++) {
+            const int nvf = cl->f[i].nv;
+            int cyc[OR_MAXFV], m = 0;
+            for (int j = 0; j < nvf; j++) {
+                const int c = cid[k + j];
+                if (m == 0 || cyc[m - 1] != c) cyc[m++] = c;
+            }
+            while (m > 1 && cyc[m - 1] == cyc[0]) m--;
+            k += nvf;
+            if (m < 3) continue;  /* a face merged away */
+            for (int j = 0; j < m; j++) {
+                df[D] = cyc[j]; dt[D] = cyc[(j + 1) % m]; dp[D] = cyc[(j + m - 1) % m];
+                D++;
+            }
+        }
+        int *rev = (int *)malloc(sizeof(int) * (D ? D : 1)), *rot = (int *)malloc(sizeof(int) * (D ? D : 1));
+        int *rinv = (int *)malloc(sizeof(int) * (D ? D : 1));
+        for (int d = 0; d < D && ok; d++) {
+            rev[d] = rot[d] = -1;
+            for (int e = 0; e < D; e++) {
+                if (df[e] == dt[d] && dt[e] == df[d]) rev[d] = e;
+                if (df[e] == df[d] && dt[e] == dp[d]) rot[d] = e;
+            }
+            if (rev[d] < 0 || rot[d] < 0) ok = 0;
+        }
+        if (ok && D == 2 * ne) {
+            for (int d = 0; d < D; d++) rinv[rot[d]] = d;
+            int *best = (int *)malloc(sizeof(int) * (D + 1)), *curc = (int *)malloc(sizeof(int) * (D + 1));
+            int *labv = (int *)malloc(sizeof(int) * (nv ? nv : 1));
+            unsigned char *used = (unsigned char *)malloc((size_t)(D ? D : 1));
+            int sym = 0;
+            if (weinberg(nv, D, df, dt, rev, rot, rinv, best, curc, labv, used, &sym)) {
+                st->wlen = D;
+                st->wsym = sym;
+                st->whash = fnv1a_labels(best, D + 1);
+            }
+            free(best); free(curc); free(labv); free(used);
+        }
+        free(df); free(dt); free(dp); free(rev); free(rot); free(rinv);
+    }
     free(pts); free(cid); free(ea); free(eb);
 }
 
@@ -648,6 +772,8 @@ static void stats2(const cell2 *cl, stats_t *st) {
  * `pos` (n x dim, FP64) in the box [lo, hi] with the given periodic flags.
  * `radii` (NULL: plain Voronoi) selects the radical variant.  `method` 0 is
  * the brute-force definition, 1 the block-grid walk with `nblocks` blocks.
+ * `wlen`, `whash`, `wsym` (NULL: skipped) receive each 3D cell's Weinberg
+ * code (Sec. 4): darts traversed, hash of the minimal code and its count.
  * `clip` > 0 gives clipped cells (Sec. 3.1.3): each cell starts from the
  * box intersected with the cube of side `clip` centred on its particle, and
  * the cube's faces are reported as walls.  Per-cell outputs are indexed by position in `cells`; faces go to slabs of
@@ -660,7 +786,8 @@ int vo_compute(int dim, long long n, const double *pos, const double *radii,
                long long ncell, const long long *cells, int maxf,
                double *vol, double *area, double *cen, int *nv, int *ne, int *nf,
                int *status, long long *nbr_id, int *nbr_img, int *face_order,
-               double *rmax, long long *ntested, long long *ncut, int nthreads) {
+               double *rmax, long long *ntested, long long *ncut, int nthreads,
+               int *wlen, unsigned long long *whash, int *wsym) {
     if ((dim != 2 && dim != 3) || n < 0 || !pos || maxf <= 0) return -1;
     ctx_t cx;
     memset(&cx, 0, sizeof cx);
@@ -755,6 +882,7 @@ int vo_compute(int dim, long long n, const double *pos, const double *radii,
             if (rmax) rmax[ci] = S.R;
             if (ntested) ntested[ci] = jb.ntested;
             if (ncut) ncut[ci] = jb.ncut;
+            if (wlen) { wlen[ci] = S.wlen; whash[ci] = S.whash; wsym[ci] = S.wsym; }
             /* faces in canonical order: ascending (id, image shift) */
             long long *oid = nbr_id + ci * maxf;
             int *oim = nbr_img + ci * maxf * 3, *oor = face_order + ci * maxf;
