@@ -106,6 +106,9 @@ typedef struct {
                           of side `clip` centred on its particle; the cube's
                           faces are reported as walls (ids -1..-6 by axis and
                           side).  0 (default): plain cells */
+    int weinberg;      /* 1 = also the Weinberg code of every 3D cell's edge
+                          graph (Sec. 4), read with vg_get_weinberg(); FP32
+                          form, eager vg_compute only.  Default 0 */
 } vg_config;
 
 /* Fills `cfg` with the defaults listed above (FP32_RETEST, PREFETCH). */
@@ -266,6 +269,28 @@ vg_status vg_get_work(vg_ctx *ctx, int32_t *n_tested, int32_t *n_vtests, int32_t
  * bounds the neighbour search (Sec. 2.1.3).  n floats, input order.
  */
 vg_status vg_get_radius(vg_ctx *ctx, float *rmax, int on_device);
+
+/*
+ * Weinberg codes (Sec. 4) from the last vg_compute() with cfg.weinberg = 1,
+ * per cell in input order (n entries each, host or device memory):
+ *   len  darts traversed, 2E (E edges of the cell); 0 = no code: the cell
+ *        is not OK, has vertices of degree above 3 (merged on an exact
+ *        lattice) or more than 64 vertices (a larger capacity tier)
+ *   hash FNV-1a 64 over the 2E+1 vertex labels of the minimal code (order of
+ *        first visit from 1, each label as two little-endian bytes); two
+ *        cells are topologically equal iff their codes are, so equal
+ *        hashes mark equal cells
+ *   sym  the number of (start dart, rotation direction) pairs that give the
+ *        minimal code: the order of the cell's combinatorial symmetry group
+ *        (mirror images included)
+ * The code traverses the edge graph from a start dart; at a new vertex it
+ * leaves by the next dart after the reverse of the arriving one, at an old
+ * vertex it returns along that reverse if untraversed, else leaves by the
+ * first untraversed dart after it; labels list the start and every arrival.
+ * The cell's code is the lexicographic minimum over all start darts and
+ * both rotation directions.  VG_ERR_STATE without such a compute.
+ */
+vg_status vg_get_weinberg(vg_ctx *ctx, int32_t *len, uint64_t *hash, int32_t *sym, int on_device);
 
 /*
  * Device time of the cell-kernel phase of every vg_compute() made with

@@ -246,6 +246,7 @@ vg_status prepare_insert(vg_ctx *c, const std::vector<long long> &counts, const 
     c->kblock_valid = 0;
     c->subset = 0;
     c->computed = 0;
+    c->wb_valid = 0;
     const int d = c->dim;
     vg_status ls = layout_systems(c, counts);
     if (ls != VG_OK) return ls;
@@ -367,6 +368,9 @@ vg_status check_config(vg_ctx *c, const vg_config &cfg, bool inserts = false) {
     if (cfg.order != VG_WALK && cfg.order != VG_PREFETCH) return fail(c, VG_ERR_ARG, "order");
     if (!(cfg.tol32 > 0) || !(cfg.tau_rel > 0) || !(cfg.merge_rel > 0)) return fail(c, VG_ERR_ARG, "tolerances");
     if (!(cfg.clip >= 0) || !(cfg.clip < 1e300)) return fail(c, VG_ERR_ARG, "clip must be finite and >= 0");
+    if (cfg.weinberg && (c->dim != 3 || cfg.precision != VG_FP32_RETEST))
+        return fail(c, VG_ERR_ARG, "Weinberg codes: 3D cells in the FP32 form");
+    if (cfg.weinberg && inserts) return fail(c, VG_ERR_ARG, "Weinberg codes: eager vg_compute only");
     if (cfg.warps_per_cta > 4) return fail(c, VG_ERR_ARG, "warps_per_cta above 4 (CTAs of at most 128 threads)");
     if (cfg.use_mlp && !c->kblock_valid && !(inserts && c->pred))
         return fail(c, VG_ERR_STATE, "use_mlp without vg_mlp_predict after the insert");
@@ -399,7 +403,10 @@ cudaError_t enqueue_cells(vg_ctx *c, const vg_config &cfg, cudaStream_t s, const
     o.w_pref = c->d_w_pref;
     o.retry = c->d_caplist; o.retry_count = c->d_capcount;
     o.retry2 = c->d_caplist2; o.retry2_count = c->d_capcount2;
+    o.topo = cfg.weinberg ? c->d_topo : nullptr;
+    o.topo_n = cfg.weinberg ? c->d_topo_n : nullptr;
     cudaError_t e;
+    if (cfg.weinberg && (e = cudaMemsetAsync(c->d_topo_n, 0, sizeof(int) * c->n, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->d_fcount, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->d_capcount, 0, sizeof(int), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->d_capcount2, 0, sizeof(int), s)) != cudaSuccess) return e;
@@ -439,6 +446,7 @@ void vg_config_default(vg_config *cfg) {
     cfg->tau_rel = 1e-11;
     cfg->merge_rel = 1e-9;
     cfg->clip = 0.0;
+    cfg->weinberg = 0;
     cfg->prefetch_k = 0;
     cfg->use_mlp = 0;
     cfg->chunk = 0;
@@ -554,6 +562,14 @@ vg_status vg_compute(vg_ctx *c, const vg_config *cfg_in) {
     release_graph(c);
     const long long n = c->n;
     const long long l0 = g_launch_count;
+    c->wb_valid = 0;
+    if (cfg.weinberg) {
+        VG_CUDA(ensure(c, c->d_topo, n * 64));
+        VG_CUDA(ensure(c, c->d_topo_n, n));
+        VG_CUDA(ensure(c, c->d_wlen, n));
+        VG_CUDA(ensure(c, c->d_wsym, n));
+        VG_CUDA(ensure(c, c->d_whash, n));
+    }
     // face buffer: start at 24 faces per cell, grow on overflow
     const long long want = std::max<long long>(1024, n * 24);
     if (c->fcap < want) {
@@ -584,6 +600,12 @@ vg_status vg_compute(vg_ctx *c, const vg_config *cfg_in) {
         c->fcap = need;
     }
     if ((s = ensure_csr(c)) != VG_OK) return s;
+    if (cfg.weinberg) {
+        cudaError_t ew = launch_weinberg(c->d_topo, c->d_topo_n, n, c->d_wlen, c->d_whash, c->d_wsym, c->sm_count,
+                                         c->stream);
+        if (ew != cudaSuccess) return cuda_fail(c, ew, "weinberg");
+        c->wb_valid = 1;
+    }
     cudaError_t e = enqueue_compact(c, c->stream);
     c->launches += g_launch_count - l0;
     if (e != cudaSuccess) return cuda_fail(c, e, "compact_faces");
@@ -637,6 +659,7 @@ vg_status vg_compute_subset(vg_ctx *c, const vg_config *cfg_in, const int32_t *c
     }
     c->launches += g_launch_count - l0;
     c->computed = 1;
+    c->wb_valid = 0;
     c->subset = 1;
     return VG_OK;
 }
@@ -754,6 +777,7 @@ vg_status vg_graph_launch(vg_ctx *c) {
     c->launches += c->graph_kernels;
     c->inserted = 1;
     c->computed = 1;
+    c->wb_valid = 0;
     c->subset = 0;
     c->graph_unchecked = 1;
     if (c->pred) c->kblock_valid = 1;
@@ -882,6 +906,16 @@ vg_status vg_get_radius(vg_ctx *c, float *rmax, int on_device) {
     return copy_out(c, rmax, c->d_rfin, sizeof(float) * c->n, on_device);
 }
 
+vg_status vg_get_weinberg(vg_ctx *c, int32_t *len, uint64_t *hash, int32_t *sym, int on_device) {
+    if (!c) return VG_ERR_ARG;
+    if (!c->computed) return fail(c, VG_ERR_STATE, "no computed cells");
+    if (!c->wb_valid) return fail(c, VG_ERR_STATE, "no Weinberg codes: compute with cfg.weinberg = 1");
+    vg_status s;
+    if ((s = copy_out(c, len, c->d_wlen, sizeof(int) * c->n, on_device))) return s;
+    if ((s = copy_out(c, hash, c->d_whash, sizeof(unsigned long long) * c->n, on_device))) return s;
+    return copy_out(c, sym, c->d_wsym, sizeof(int) * c->n, on_device);
+}
+
 vg_status vg_get_sorted(vg_ctx *c, int64_t *n_blocks, int32_t *block_start, int32_t *order, int on_device) {
     if (!c) return VG_ERR_ARG;
     if (c->graph_unchecked) {
@@ -930,6 +964,7 @@ void vg_destroy(vg_ctx *c) {
     release(c->d_caplist2); release(c->d_capcount2);
     release(c->d_off_code); release(c->d_off_lb); release(c->d_kblock); release(c->d_w_newv);
     release(c->d_w_pref); release(c->d_rfin);
+    release(c->d_topo); release(c->d_topo_n); release(c->d_wlen); release(c->d_wsym); release(c->d_whash);
     release(c->d_kstar); release(c->d_kmax); release(c->d_feat);
     release(c->d_rank); release(c->d_subset); release(c->d_subset_in);
     release(c->d_sys_init);
@@ -954,6 +989,7 @@ vg_status graph_check(vg_ctx *c) {
     vg_status s = read_input_flags(c);
     if (s != VG_OK) {
         c->computed = 0;
+        c->wb_valid = 0;
         return s;
     }
     unsigned long long used = 0;

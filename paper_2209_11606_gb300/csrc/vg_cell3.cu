@@ -512,7 +512,7 @@ __device__ __forceinline__ bool resolve(const Grid &g, long long base, const int
 
 // ---- the kernel ------------------------------------------------------------------
 
-template <typename T, int VPL, int MAXP, bool BATCH, int G>
+template <typename T, int VPL, int MAXP, bool BATCH, int G, bool TOPO = false>
 __global__ void VG_BOUNDS
     k_cells3(const __grid_constant__ Store st, const __grid_constant__ Out o,
              const __grid_constant__ Params pp, const __grid_constant__ Offsets off, unsigned *ticket,
@@ -1716,6 +1716,11 @@ __global__ void VG_BOUNDS
                             }
                         }
                     }
+                    if constexpr (TOPO) {
+                        // the triangles by slot, for the Weinberg codes (tier 0: 64 slots)
+#pragma unroll
+                        for (int s = 0; s < VPL; s++) o.topo[(long long)out_i * (G * VPL) + s * G + gl] = tri[s];
+                    }
                     if (gl == 0) {
                         const double v6 = vol;
                         o.vol[out_i] = v6 * (1.0 / 6.0);
@@ -1731,6 +1736,7 @@ __global__ void VG_BOUNDS
                         o.ne[out_i] = osum / 2;
                         o.nf[out_i] = nfk;
                         o.status[out_i] = overflow ? (unsigned char)VG_CELL_CAP : (unsigned char)VG_CELL_OK;
+                        if constexpr (TOPO) o.topo_n[out_i] = (nv == T_ && !overflow) ? T_ : 0;
                         o.fptr[out_i] = fbase;
                     }
                 }
@@ -1773,11 +1779,11 @@ __global__ void VG_BOUNDS
     }
 }
 
-template <typename T, int VPL, int MAXP, bool BATCH, int G>
+template <typename T, int VPL, int MAXP, bool BATCH, int G, bool TOPO = false>
 cudaError_t launch_t(const Store &s, const Out &o, const Params &p, const Offsets &off, unsigned *ticket,
                      int sm_count, int warps, const int *cells, int ncells, int tier, cudaStream_t st) {
     const size_t smem = sizeof(Smem<T, VPL, MAXP, G>) * warps * (32 / G);
-    auto kfn = k_cells3<T, VPL, MAXP, BATCH, G>;
+    auto kfn = k_cells3<T, VPL, MAXP, BATCH, G, TOPO>;
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // shared memory before L1: the resident CTAs are bounded by it
@@ -1814,6 +1820,9 @@ cudaError_t launch_cells3(const Store &s, const Out &o, const Params &p, const O
     if (precision == VG_FP64)
         return batch ? launch_t<double, VG_T0_VPL, 64, true, VG_T0_G>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st)
                      : launch_t<double, VG_T0_VPL, 64, false, VG_T0_G>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
+    if (o.topo)  // the cells' triangles are kept for Weinberg codes (FP32 form, tier 0)
+        return batch ? launch_t<float, VG_T0_VPL, 64, true, VG_T0_G, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st)
+                     : launch_t<float, VG_T0_VPL, 64, false, VG_T0_G, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
     return batch ? launch_t<float, VG_T0_VPL, 64, true, VG_T0_G>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st)
                  : launch_t<float, VG_T0_VPL, 64, false, VG_T0_G>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
 }

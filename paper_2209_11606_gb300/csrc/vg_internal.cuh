@@ -80,6 +80,10 @@ struct Out {
     int *retry_count;
     int *retry2;                  // sorted indices of cells for tier 2
     int *retry2_count;
+    // optional: the final cell's triangles (plane triples, 64 slots a cell)
+    // and their count, 0 where the cell has merged vertices or no entry
+    unsigned *topo;
+    int *topo_n;
 };
 
 struct Params {
@@ -163,6 +167,9 @@ cudaError_t exclusive_scan_i32(const int *in, int *out, long long n, void *tmp, 
 cudaError_t exclusive_scan_i64_from_i32(const int *in, long long *out, long long n, void *tmp,
                                         cudaStream_t st);
 
+// Weinberg codes (Sec. 4) of the cells whose topology the cell kernel stored.
+cudaError_t launch_weinberg(const unsigned *topo, const int *topo_n, long long n, int *wlen,
+                            unsigned long long *whash, int *wsym, int sm_count, cudaStream_t st);
 cudaError_t launch_cells3(const Store &s, const Out &o, const Params &p, const Offsets &off,
                           int precision, unsigned *ticket, int sm_count, int warps_per_cta,
                           const int *cells, int ncells, int tier, cudaStream_t st);
@@ -240,6 +247,11 @@ struct vg_ctx {
     int *d_w_tested = nullptr, *d_w_vtests = nullptr, *d_w_cuts = nullptr, *d_w_retest = nullptr;
     int *d_w_newv = nullptr, *d_w_pref = nullptr;
     float *d_rfin = nullptr;
+    // Weinberg codes: kept triangles, their counts, the codes
+    unsigned *d_topo = nullptr;
+    int *d_topo_n = nullptr, *d_wlen = nullptr, *d_wsym = nullptr;
+    unsigned long long *d_whash = nullptr;
+    int wb_valid = 0;
     // event pairs around the cell kernels (time_kernels)
     static constexpr int NEV = 256;
     cudaEvent_t ev[2 * NEV] = {};

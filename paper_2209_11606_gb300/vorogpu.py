@@ -26,7 +26,7 @@ VG_CELL_OK, VG_CELL_EMPTY, VG_CELL_CAP, VG_CELL_DUP, VG_CELL_LIMIT = 0, 1, 2, 3,
 
 EXPORTS = ["vg_config_default", "vg_create", "vg_batch_create", "vg_insert", "vg_batch_insert",
            "vg_compute", "vg_compute_subset", "vg_get_counts", "vg_get_cells", "vg_get_faces", "vg_get_work",
-           "vg_get_radius", "vg_get_sorted", "vg_get_grid", "vg_get_system_grid", "vg_get_launches",
+           "vg_get_radius", "vg_get_weinberg", "vg_get_sorted", "vg_get_grid", "vg_get_system_grid", "vg_get_launches",
            "vg_get_kernel_ms", "vg_graph_capture", "vg_graph_launch", "vg_graph_sync",
            "vg_sort_blocks_noalloc", "vg_last_error", "vg_destroy",
            "vg_mlp_create", "vg_mlp_destroy", "vg_mlp_last_error", "vg_mlp_set_params",
@@ -40,7 +40,7 @@ class VgConfig(ctypes.Structure):
                 ("tau_rel", ctypes.c_double), ("merge_rel", ctypes.c_double),
                 ("prefetch_k", ctypes.c_int), ("use_mlp", ctypes.c_int), ("chunk", ctypes.c_int),
                 ("warps_per_cta", ctypes.c_int), ("collect_stats", ctypes.c_int),
-                ("time_kernels", ctypes.c_int), ("clip", ctypes.c_double)]
+                ("time_kernels", ctypes.c_int), ("clip", ctypes.c_double), ("weinberg", ctypes.c_int)]
 
 
 class VgSystem(ctypes.Structure):
@@ -83,6 +83,7 @@ def load(path: str = LIB_PATH):
         "vg_get_faces": (I, [P, P, P, P, P, I]),
         "vg_get_work": (I, [P, P, P, P, P, P, P, P, I]),
         "vg_get_radius": (I, [P, P, I]),
+        "vg_get_weinberg": (I, [P, P, P, P, I]),
         "vg_get_kernel_ms": (I, [P, ctypes.POINTER(D), ctypes.POINTER(L)]),
         "vg_get_sorted": (I, [P, ctypes.POINTER(L), P, P, I]),
         "vg_get_grid": (I, [P, P]),
@@ -272,6 +273,15 @@ def vg_get_work(ctx, n_tested=None, n_vtests=None, n_cuts=None, n_newv=None, n_r
 def vg_get_radius(ctx, rmax):
     p, dev = _ptr(rmax)
     _check(ctx, load().vg_get_radius(ctx, p, dev))
+
+
+def vg_get_weinberg(ctx, length, hash_, sym):
+    """Weinberg codes of the last compute with cfg.weinberg = 1: darts (2E,
+    0 = none), FNV-1a 64 hash of the minimal code, symmetry count."""
+    ptrs = [_ptr(a) for a in (length, hash_, sym)]
+    if len({d for _, d in ptrs}) > 1:
+        raise ValueError("outputs must all be host or all device")
+    _check(ctx, load().vg_get_weinberg(ctx, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[0][1]))
 
 
 def vg_get_sorted(ctx, block_start=None, order=None):
@@ -485,6 +495,10 @@ def compute_host(pos, lo, hi, periodic, radii=None, nblocks=None, n_opt=0.0, pre
         vg_compute(ctx, _make_cfg(precision, order, work, cfg_kw))
         out = _fetch(ctx, n, d, work)
         out["grid"] = vg_get_grid(ctx, d)
+        if cfg_kw.get("weinberg"):
+            wl, wh, ws = np.zeros(n, np.int32), np.zeros(n, np.uint64), np.zeros(n, np.int32)
+            vg_get_weinberg(ctx, wl, wh, ws)
+            out.update({"w_len": wl, "w_hash": wh, "w_sym": ws})
         return out
     finally:
         vg_destroy(ctx)
