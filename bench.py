@@ -98,6 +98,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the alternative FP32 forms")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 form")
+    ap.add_argument("--weinberg", action="store_true",
+                    help="also time the cells with Weinberg codes (Sec. 4), eager calls")
     return ap.parse_args()
 
 
@@ -263,6 +265,33 @@ def batched_run(V, torch, stream, flush, mlp, steps: int = 5, seed: int = 5):
                             f"periodicity (seed {seed})"}
     finally:
         V.vg_destroy(ctx)
+
+
+def weinberg_run(V, torch, ctx, pos_d, rad_d, cfg, n, reps: int = 3):
+    """Cells with and without Weinberg codes (Sec. 4): eager insert + compute,
+    host clock around synchronised calls."""
+    def timed(weinberg):
+        c = V.vg_config_default()
+        c.precision, c.order, c.use_mlp, c.clip = cfg.precision, cfg.order, cfg.use_mlp, cfg.clip
+        c.weinberg = int(weinberg)
+        V.vg_insert(ctx, pos_d, rad_d)
+        V.vg_compute(ctx, c)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            V.vg_insert(ctx, pos_d, rad_d)
+            V.vg_compute(ctx, c)
+        torch.cuda.synchronize()
+        return n * reps / (time.perf_counter() - t0)
+    base = timed(False)
+    with_codes = timed(True)
+    wl, wh, ws = np.zeros(n, np.int32), np.zeros(n, np.uint64), np.zeros(n, np.int32)
+    V.vg_get_weinberg(ctx, wl, wh, ws)
+    coded = wl > 0
+    return {"cells_per_s": with_codes, "without_codes_cells_per_s": base, "unit": "cells/s",
+            "coded_fraction": float(coded.mean()), "distinct_codes": int(len(np.unique(wh[coded]))),
+            "form": "eager vg_insert + vg_compute with cfg.weinberg = 1 (cells, then a warp per cell "
+                    "for its Weinberg code), host clock"}
 
 
 def cpu_baseline(s, grid, cells: int, seed: int = 0, clip: float = 0.0):
@@ -501,6 +530,8 @@ def main():
             "forms": forms, "learned_preload": learned,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "retest_per_cell": float(w["r"].mean())}
+    if args.weinberg and dim == 3:
+        line["weinberg"] = weinberg_run(V, torch, ctx, pos_d, rad_d, cfg, n)
     if not args.no_batched and args.workload == "uniform1m":
         line["batched"] = batched_run(V, torch, stream, flush, mlp)
     if not args.no_cpu_baseline and world == 1:
