@@ -621,6 +621,7 @@ vg_status vg_compute_subset(vg_ctx *c, const vg_config *cfg_in, const int32_t *c
     if (cfg_in) cfg = *cfg_in; else vg_config_default(&cfg);
     vg_status s = check_config(c, cfg);
     if (s != VG_OK) return s;
+    if (cfg.weinberg) return fail(c, VG_ERR_ARG, "Weinberg codes: vg_compute only");
     if (m < 0 || m > c->n || (m > 0 && !cells)) return fail(c, VG_ERR_ARG, "bad cell list");
     if (c->graph_unchecked && (s = graph_check(c)) != VG_OK) return s;
     release_graph(c);
