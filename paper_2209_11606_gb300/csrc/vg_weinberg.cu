@@ -118,9 +118,9 @@ __global__ void __launch_bounds__(32 * WB_WARPS) k_weinberg(const unsigned *__re
                     if (active) {
                         S.used[lane][d >> 5] |= 1u << (d & 31);
                         const int y = S.dto[d], rv = S.drev[d];
-                        const int base = 3 * (rv / 3), kr = rv - base;
+                        // the darts leaving y are base .. base + 2, in rotation order
+                        const int base = 3 * (rv / 3);
                         auto R = [&](int e) { return base + (o ? (e - base + 2) % 3 : (e - base + 1) % 3); };
-                        (void)kr;
                         if (!S.lab[lane][y]) {
                             S.lab[lane][y] = (unsigned char)(++nl);
                             L = nl;
