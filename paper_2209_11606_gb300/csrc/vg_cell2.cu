@@ -87,7 +87,7 @@ __device__ __forceinline__ V gmax(unsigned gmask, V v) {
 #pragma unroll
     for (int d = G / 2; d > 0; d >>= 1) {
         V o = __shfl_xor_sync(gmask, v, d, G);
-        v = v > o ? v : o;
+        v = (o > v || o != o) ? o : v;  // a NaN wins on every lane alike
     }
     return v;
 }
@@ -343,15 +343,17 @@ __global__ void __launch_bounds__(128, VG2_MINB) k_cells2(const __grid_constant_
         T stop = stop2();
 
         // ------------------------------------------- walk (Sec. 2.1.3), per block
-        const float hmin = fminf(g.hf[0], g.hf[1]);
-        // shells up to 23000 keep (2 shell + 1)^2 within 32-bit indices
-        const int maxs = min(23000, SY.off_shell + 4 + 2 * max(g.nb[0], g.nb[1]));
+        const float hmin = fminf(g.hf[0], g.hf[1]), hmax = fmaxf(g.hf[0], g.hf[1]);
+        float eqm = 0.f;  // FP32: largest position error of the candidates so far
+        // shell s has 8 s blocks: up to 16000 shells the walk (about 4 s^2
+        // steps) ends before its guard of 2^30 steps
+        const int maxs = min(16000, SY.off_shell + 4 + 2 * max(g.nb[0], g.nb[1]));
         const int ocount = SY.off_count, obase = SY.off_base;
         int e = 0, shell = 0, sidx = 0, mode = 1;  // 1 list, 2 shells, 3 done
         for (int guard = 0; guard < (1 << 30) && mode != 3 && !(flags & 6); guard++) {
             int ox = 0, oy = 0;
             if (mode == 1) {
-                if (e >= ocount) { mode = 2; shell = SY.off_shell + 1; sidx = 0; continue; }
+                if (e >= ocount) { mode = 2; shell = 1; sidx = 0; continue; }
                 const float lbv = __ldg(&off.lb[obase + e]);
                 if ((T)(lbv * lbv) * (T)0.99998 >= stop) { mode = 3; continue; }
                 const int code = __ldg(&off.code[obase + e]);
@@ -362,12 +364,25 @@ __global__ void __launch_bounds__(128, VG2_MINB) k_cells2(const __grid_constant_
                 const float sb = (float)(shell - 1) * hmin;
                 if ((T)(sb * sb) * (T)0.99998 >= stop) { mode = 3; continue; }
                 if (shell > maxs) { limit = 1; mode = 3; continue; }
+                // the shell's surface only: two rows of wd, two columns of wd - 2
                 const int wd = 2 * shell + 1;
-                if (sidx >= wd * wd) { shell++; sidx = 0; continue; }
-                ox = sidx % wd - shell;
-                oy = sidx / wd - shell;
+                if (sidx >= 4 * wd - 4) { shell++; sidx = 0; continue; }
+                if (sidx < 2 * wd) {
+                    const int r = sidx < wd ? sidx : sidx - wd;
+                    ox = r - shell;
+                    oy = sidx < wd ? -shell : shell;
+                } else {
+                    const int t = sidx - 2 * wd, r = t < wd - 2 ? t : t - (wd - 2);
+                    ox = t < wd - 2 ? -shell : shell;
+                    oy = r - (shell - 1);
+                }
                 sidx++;
-                if (max(abs(ox), abs(oy)) != shell) continue;
+                // shell members that the offset list did not hold (its bound is
+                // below off_shell * h_min, in FP32, exactly as the list was cut)
+                const float lbmax = (float)SY.off_shell * hmin;
+                const float lbx = fmaxf(0.f, (float)(abs(ox) - 1)) * g.hf[0];
+                const float lby = fmaxf(0.f, (float)(abs(oy) - 1)) * g.hf[1];
+                if (lbx * lbx + lby * lby < lbmax * lbmax) continue;
             }
             // the block: resolve, distance bound, particles
             int t0 = b0 + ox, t1 = b1 + oy, m0 = 0, m1 = 0;
@@ -412,12 +427,20 @@ __global__ void __launch_bounds__(128, VG2_MINB) k_cells2(const __grid_constant_
                     const T cq = __shfl_sync(gmask, qq, src, G), cr = __shfl_sync(gmask, rj, src, G);
                     const int ref = jb + src;
                     if (cq >= stop) continue;
-                    if (cq < (T)1e-30) { flags |= 8; continue; }
+                    // coincident: in FP32 perhaps only after rounding, so a retry
+                    if (cq < (T)1e-30) { flags |= F32 ? 2 : 8; continue; }
                     const T c = st.radical ? (T)0.5 * (cq + (T)(S.cc.rp * S.cc.rp) - cr * cr) : (T)0.5 * cq;
                     // ---------------------------------------- cut by q.r = c
                     if (pp.collect && gl == 0) { S.cnt[0]++; S.cnt[1] += nvert; }
                     T tau;
-                    if constexpr (F32) tau = tol32f * sqrt_a(r2 * cq);
+                    if constexpr (F32) {
+                        // block-relative FP32 positions are off by a few units in
+                        // the last place of the block side, more with the block
+                        // offset; tiny cells need that absolute error in the band
+                        eqm = fmaxf(eqm, 1.2e-7f * (float)(abs(ox) + abs(oy) + 2) * hmax);
+                        const float rq = sqrt_a(cq);
+                        tau = tol32f * sqrt_a(r2) * rq + eqm * (sqrt_a(r2) + 2.f * rq);
+                    }
                     else tau = (T)(tau_rel_s * sqrt((double)cq));
                     unsigned outm = 0, nearm = 0, onm = 0;
 #pragma unroll
@@ -463,13 +486,19 @@ __global__ void __launch_bounds__(128, VG2_MINB) k_cells2(const __grid_constant_
                     Fm = gor64<G>(gmask, Fm);
                     Sm = gor64<G>(gmask, Sm);
                     kept = __reduce_add_sync(gmask, kept);
-                    if (kept == 0) { flags |= 4; break; }
+                    // no vertex left: an empty power cell, but for a Voronoi cell
+                    // (which holds its particle) a numerical failure
+                    if (kept == 0) { flags |= st.radical ? 4 : 2; break; }
                     const unsigned long long freep = ~live;
                     if (!freep) { flags |= 2; break; }
                     const int np = __ffsll((long long)freep) - 1;
                     if (np >= MAXP2) { flags |= 2; break; }
-                    // the lanes holding the run's ends make the two new vertices
+                    // the lanes holding the run's ends make the two new vertices;
+                    // each lies on an old edge, so within the old radius (a vertex
+                    // beyond it, or not finite, is a numerical failure)
                     int nA = 0, nB = 0;
+                    bool wild = false;
+                    const T r2lim = r2 * (T)1.01;
 #pragma unroll
                     for (int s = 0; s < VPL; s++) {
                         if (outm & (1u << s)) {
@@ -480,6 +509,7 @@ __global__ void __launch_bounds__(128, VG2_MINB) k_cells2(const __grid_constant_
                                 float kp;
                                 meet<T>(S.pl[x], cx, cy, c, nx, ny, kp);
                                 S.sv[0] = mkv(x, np); S.sx[0] = nx; S.sy[0] = ny; S.sk[0] = kp;
+                                wild |= !(nx * nx + ny * ny <= r2lim);
                                 nA++;
                             }
                             if (!((Fm >> y) & 1)) {
@@ -487,6 +517,7 @@ __global__ void __launch_bounds__(128, VG2_MINB) k_cells2(const __grid_constant_
                                 float kp;
                                 meet<T>(S.pl[y], cx, cy, c, nx, ny, kp);
                                 S.sv[1] = mkv(np, y); S.sx[1] = nx; S.sy[1] = ny; S.sk[1] = kp;
+                                wild |= !(nx * nx + ny * ny <= r2lim);
                                 nB++;
                             }
                             v[s] = EMPTY2;
@@ -494,7 +525,8 @@ __global__ void __launch_bounds__(128, VG2_MINB) k_cells2(const __grid_constant_
                     }
                     nA = __reduce_add_sync(gmask, nA);
                     nB = __reduce_add_sync(gmask, nB);
-                    if (nA != 1 || nB != 1 || kept + 2 > CAP) { flags |= 2; break; }
+                    wild = __any_sync(gmask, wild);
+                    if (nA != 1 || nB != 1 || wild || kept + 2 > CAP) { flags |= 2; break; }
                     if (gl == 0) {
                         typename P2<T>::t P;
                         P.x = cx; P.y = cy; P.z = c; P.w = 0;
@@ -535,6 +567,8 @@ __global__ void __launch_bounds__(128, VG2_MINB) k_cells2(const __grid_constant_
                 }
             }
         }
+
+        if (mode != 3 && !(flags & 6)) limit = 1;  // the guard ran out
 
         // ------------------------------------------------------------ statistics
         int status = VG_CELL_OK;

@@ -177,3 +177,21 @@ def test_localized_extended_cells(precision, order, rtol):
 def test_extreme_clustering_3d(precision, order, rtol):
     s = W.extreme_clustering(20_000, 3, seed=32)
     check(s, (34, 34, 34), precision, order, rtol)
+
+
+@pytest.mark.parametrize("precision,order,rtol", FORMS[:2])
+def test_extreme_clustering_2d(precision, order, rtol):
+    # Sec. 3.1 'extreme clustering' in 2D: cells near the centre are 1e-4 of
+    # a block side and smaller, where block-relative FP32 positions carry
+    # errors a relative band alone would miss
+    s = W.extreme_clustering(100_000, 2, seed=16)
+    check(s, (447, 447), precision, order, rtol)
+
+
+@pytest.mark.parametrize("precision,order,rtol", FORMS[:2])
+def test_localized_2d_fine_grid(precision, order, rtol):
+    # cells at the cluster's surface span tens of blocks, so the walk covers
+    # every shell past the offset list, the corners of the last listed shell
+    # included
+    s = W.localized(100_000, 2, 0.1, seed=23)
+    check(s, (200, 200), precision, order, rtol)
