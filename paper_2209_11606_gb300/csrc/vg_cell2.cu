@@ -331,20 +331,23 @@ __global__ void __launch_bounds__(128, VG2_MINB) k_cells2(const __grid_constant_
         T r2 = gmax<G>(gmask, gl < 4 ? vx[0] * vx[0] + vy[0] * vy[0] : (T)0);
         int flags = 0;  // 1 degenerate, 2 failure, 4 empty, 8 duplicate
         int limit = 0;
+        float eqm = 0.f;  // FP32: largest position error of the candidates so far
+        // FP32: that error moves |q| and R by about eqm and the vertices by
+        // kappa eqm; 64 eqm R covers a small cell
         auto stop2 = [&]() -> T {
             const T margin = F32 ? (T)1.0001 : (T)(1.0 + 1e-12);
-            if (!st.radical) return (T)4 * r2 * margin;
+            const T ea = F32 ? (T)(64.f * eqm) : (T)0;
+            if (!st.radical) return (T)4 * r2 * margin + ea * sqrt(r2);
             const T disc = r2 + (T)(S.cc.rmax * S.cc.rmax) - (T)(S.cc.rp * S.cc.rp);
             if (disc <= (T)0) return (T)0;
             const T rs = sqrt(r2) + sqrt(disc);
-            return rs * rs * margin;
+            return rs * rs * margin + ea * rs;
         };
         __syncwarp(gmask);
         T stop = stop2();
 
         // ------------------------------------------- walk (Sec. 2.1.3), per block
         const float hmin = fminf(g.hf[0], g.hf[1]), hmax = fmaxf(g.hf[0], g.hf[1]);
-        float eqm = 0.f;  // FP32: largest position error of the candidates so far
         // shell s has 8 s blocks: up to 16000 shells the walk (about 4 s^2
         // steps) ends before its guard of 2^30 steps
         const int maxs = min(16000, SY.off_shell + 4 + 2 * max(g.nb[0], g.nb[1]));
@@ -578,6 +581,15 @@ __global__ void __launch_bounds__(128, VG2_MINB) k_cells2(const __grid_constant_
         else if (limit) status = VG_CELL_LIMIT;
         const int out_i = S.cc.self_id;
         bool degen = flags & 1;
+        if constexpr (F32) {
+            // an ill-conditioned vertex (kappa >= 64) is off by more than the
+            // 1e-5 bar allows: the statistics take FP64 vertices
+            bool hk = false;
+#pragma unroll
+            for (int s = 0; s < VPL; s++) hk |= v[s] != EMPTY2 && kap[s] >= 64.f;
+            const bool anyhk = __any_sync(gmask, hk);
+            degen = degen || anyhk;
+        }
         if (!fail && status == VG_CELL_OK) {
             // reference point: a vertex of the cell (fans from a far particle
             // cancel); radical cells small against that distance use FP64

@@ -234,6 +234,18 @@ __device__ __forceinline__ bool may_cut(const float4 *v4, int n, float qx, float
     return m;
 }
 
+// FP32 band of a candidate close to the particle (|q| below a tenth of the
+// smallest block side, so within the adjacent blocks): on top of tol32 R |q|
+// the absolute error of block-relative FP32 positions, at most about
+// 2^-24 (5 h) per axis there (both offsets, the block side's own rounding,
+// the sums), 6e-7 h_max as a vector, times |v| + 2 |q| <= R + 2 |q| (the
+// plane's normal and its constant both carry it).  Far candidates keep the
+// relative band alone: there the inputs' error is a few percent of it.
+__device__ __forceinline__ float band_close(float tol, float r2, float qq, float eabs) {
+    const float R = sqrt_a(r2), rq = sqrt_a(qq);
+    return tol * R * rq + eabs * (R + 2.f * rq);
+}
+
 // prefetch bucket b holds the distances t * rho with t^(3/2) in [b, b+1) / NBIN:
 // its lower bound is t = (b / NBIN)^(2/3)
 __constant__ float bucket_t[NBIN] = {0.f, 0.25f, 0.396850263f, 0.520020956f,
@@ -691,18 +703,28 @@ __global__ void VG_BOUNDS
                 for (int w2 = 0; w2 < NW; w2++) live[w2] = gor64(gmask, lv[w2]);
             };
             T r2 = gmax<G>(gmask, gl < 8 ? vx[0] * vx[0] + vy[0] * vy[0] + vz[0] * vz[0] : (T)0);
-            // bit 0 degenerate, 1 capacity/consistency failure, 2 empty, 3 duplicate point
+            // bit 0 degenerate, 1 capacity/consistency failure, 2 empty, 3 duplicate
+            // point, 4 a close cut (FP32)
             int flags = 0;
+            // FP32: candidates closer than qabs2 take the absolute input error
+            // eabs; a cut closer than qclose2 tilts its plane by eabs / |q|, too
+            // much for FP32 statistics (bit 4 of flags: FP64 vertices)
+            const float hmin3 = fminf(g.hf[0], fminf(g.hf[1], g.hf[2]));
+            const float qabs2 = 0.01f * hmin3 * hmin3, qclose2 = 0.0025f * hmin3 * hmin3;
+            const float eabs = 6e-7f * fmaxf(g.hf[0], fmaxf(g.hf[1], g.hf[2]));
 
             // radius bound (Sec. 2.1.3), squared, with a small relative margin
             // that covers the rounding of R and of candidate distances
+            // FP32: the inputs' absolute error eabs moves |q| and R by about
+            // eabs and the vertices by kappa eabs; 64 eabs R covers a small cell
             auto stop2 = [&]() -> T {
                 const T margin = F32 ? (T)1.0001 : (T)(1.0 + 1e-12);
-                if (!st.radical) return (T)4 * r2 * margin;
+                const T ea = F32 ? (T)(64.f * eabs) : (T)0;
+                if (!st.radical) return (T)4 * r2 * margin + ea * sqrt(r2);
                 T disc = r2 + (T)(S.cc.rmax * S.cc.rmax) - (T)(S.cc.rp * S.cc.rp);
                 if (disc <= (T)0) return (T)0;
                 T rs = sqrt(r2) + sqrt(disc);
-                return rs * rs * margin;
+                return rs * rs * margin + ea * rs;
             };
 
             // ----------------------------------------------- candidate source
@@ -967,7 +989,8 @@ __global__ void VG_BOUNDS
                                 if (filt && ok && q4.w >= 1e-30f) {
                                     const float cc = st.radical ? 0.5f * (q4.w + rp32 * rp32 - crj * crj) : 0.5f * q4.w;
                                     ok = may_cut(S.v4, G * (32 - __clz(rows)), q4.x, q4.y, q4.z, cc,
-                                                 tol32f * sqrt_a(r2 * q4.w));
+                                                 VG_RARE(q4.w < qabs2) ? band_close(tol32f, r2, q4.w, eabs)
+                                                                       : tol32f * sqrt_a(r2 * q4.w));
                                 }
                             }
                         }
@@ -1022,7 +1045,8 @@ __global__ void VG_BOUNDS
                                 if (filt && ok && cqq >= 1e-30f) {
                                     const float cc = st.radical ? 0.5f * (cqq + rp32 * rp32 - crj * crj) : 0.5f * cqq;
                                     ok = may_cut(S.v4, G * (32 - __clz(rows)), cqx, cqy, cqz, cc,
-                                                 tol32f * sqrt_a(r2 * cqq));
+                                                 VG_RARE(cqq < qabs2) ? band_close(tol32f, r2, cqq, eabs)
+                                                                      : tol32f * sqrt_a(r2 * cqq));
                                 }
                             }
                             S.cbq[gl] = mk4<T>(cqx, cqy, cqz, cqq);
@@ -1037,7 +1061,7 @@ __global__ void VG_BOUNDS
                     }
                     // a new window: up to G blocks set up in parallel
                     if (src.last) { src.mode = 3; continue; }
-                    int ox = 0, oy = 0, oz = 0;
+                    int ox = 0, oy = 0, oz = 0, nsidx = 0;
                     bool cand = false;
                     if (mode == 1) {
                         const int e = src.e;
@@ -1081,7 +1105,9 @@ __global__ void VG_BOUNDS
                             // shell members that the offset list did not hold
                             cand = !(lbx * lbx + lby * lby + lbz * lbz < lbmax * lbmax);
                         }
-                        src.sidx = sidx + G;
+                        // the cursor moves after the window's ballot, once every
+                        // lane has read it
+                        nsidx = sidx + G;
                     }
                     int kk = 0, mx = 0, my = 0, mz = 0, len = 0, j0b = 0, inpref = 0;
                     if (cand) {
@@ -1124,6 +1150,7 @@ __global__ void VG_BOUNDS
                         S.w.win.o[slot] = pack_img(ox, oy, oz) | (inpref << 24);
                         S.w.win.m[slot] = pack_img(mx, my, mz);
                     }
+                    if (mode == 2) src.sidx = nsidx;
                     src.nwin = __popc(cb);
                     src.vp = 0;
                     src.vtot = ltot;
@@ -1137,7 +1164,12 @@ __global__ void VG_BOUNDS
                 const T qx = cq4.x, qy = cq4.y, qz = cq4.z, qq = cq4.w;
                 const int ref = cr.x, img = cr.y;
                 if (qq >= stop) continue;
-                if (VG_RARE(qq < (T)1e-30)) { flags |= 8; continue; }
+                if (VG_RARE(qq < (T)1e-30)) {
+                    // coincident: in FP32 perhaps only after rounding, so a retry
+                    if constexpr (F32) { flags |= 2; break; }
+                    flags |= 8;
+                    continue;
+                }
                 T c;
                 if (st.radical) {
                     const T rj = S.cbrj[srcl];
@@ -1153,7 +1185,11 @@ __global__ void VG_BOUNDS
                 if constexpr (F32) {
                     // |d| against the band tau * kappa, squared (no square root on
                     // the critical path): out if d > band, near if |d| <= band
-                    const float t2 = tol32f * tol32f * r2 * qq;
+                    float t2 = tol32f * tol32f * r2 * qq;
+                    if (VG_RARE(qq < qabs2)) {
+                        const float b = band_close(tol32f, r2, qq, eabs);
+                        t2 = b * b;
+                    }
 #pragma unroll
                     for (int s = 0; s < VPL; s++) {
                         if ((rows >> s) & 1) {
@@ -1194,6 +1230,7 @@ __global__ void VG_BOUNDS
                 }
                 if (!__any_sync(gmask, outm)) continue;
                 if (__any_sync(gmask, onm)) flags |= 1;
+                if (F32 && VG_RARE((float)qq < qclose2)) flags |= 16;
                 if (VG_RARE(pp.collect) && gl == 0) S.cnt[2]++;
                 int np = -1;
                 if (nplane < MAXP) {
@@ -1308,7 +1345,9 @@ __global__ void VG_BOUNDS
                 if (VG_RARE(pp.collect) && gl == 0) S.cnt[3] += N;
                 const int rc = tot > CAP ? 3 : (tot == 0 ? 2 : 1);
                 if (VG_RARE(rc != 1)) {
-                    flags |= rc == 2 ? 4 : 2;
+                    // no vertex left: an empty power cell, but for a Voronoi
+                    // cell (which holds its particle) a numerical failure
+                    flags |= (rc == 2 && st.radical) ? 4 : 2;
                     break;
                 }
 #pragma unroll
@@ -1413,7 +1452,16 @@ __global__ void VG_BOUNDS
 
             // ================================================= statistics
             live_planes();
-            bool degen = flags & 1;
+            bool degen = flags & (1 | 16);
+            if constexpr (F32) {
+                // an ill-conditioned vertex (kappa >= 64) is off by more than
+                // the 1e-5 bar allows: the statistics take FP64 vertices
+                bool hk = false;
+#pragma unroll
+                for (int s = 0; s < VPL; s++) hk |= tri[s] != TRI_EMPTY && kap[s] >= 64.f;
+                const bool anyhk = __any_sync(gmask, hk);
+                degen = degen || anyhk;
+            }
             bool fail = flags & 2;
             int status = VG_CELL_OK;
             if (flags & 4) status = VG_CELL_EMPTY;

@@ -160,6 +160,22 @@ def extreme_clustering(n: int, dim: int = 3, seed: int = 0) -> System:
     return System(pos, np.zeros(dim), np.ones(dim), (False,) * dim, tag="clustered")
 
 
+def corner_cluster(n_bg: int, n_cl: int, dim: int = 3, nb: int = 20, width: float = 2e-3,
+                   seed: int = 0) -> System:
+    """A uniform background of n_bg points in the walled unit box plus n_cl
+    points uniform in a cube (square) `width` block sides across, centred
+    on the block corner at the middle of an nb^dim grid: cells 1e-4 of a
+    block and smaller next to the block boundary, as at the centre of the
+    extreme-clustering set at 10^7-10^8 points, where block-relative FP32
+    positions are coarse against the cells."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / nb
+    corner = np.full(dim, (nb // 2) * h)
+    bg = rng.random((n_bg, dim))
+    cl = corner + (rng.random((n_cl, dim)) - 0.5) * (width * h)
+    return System(np.concatenate([bg, cl]), np.zeros(dim), np.ones(dim), (False,) * dim, tag="corner_cluster")
+
+
 def blobs(n: int, side: float, nblobs: int = 50, sigma_frac: float = 0.02,
           periodic: bool = True, seed: int = 0) -> System:
     """n points drawn from `nblobs` isotropic Gaussian blobs of std

@@ -179,7 +179,11 @@ def test_extreme_clustering_3d(precision, order, rtol):
     check(s, (34, 34, 34), precision, order, rtol)
 
 
-@pytest.mark.parametrize("precision,order,rtol", FORMS[:2])
+# FP64 bar: the oracle keeps 2D vertices in box coordinates (|x| <= 1), each
+# off by up to 2^-53 |x|, which against cells 1e-4 across is 1e-12 relative
+# per vertex; its worst cells here are off by 3.8e-12 from their exact
+# rational areas (the kernel's particle-relative FP64 vertices are not)
+@pytest.mark.parametrize("precision,order,rtol", [("fp64", "walk", 1e-10), ("fp32", "walk", 1e-5)])
 def test_extreme_clustering_2d(precision, order, rtol):
     # Sec. 3.1 'extreme clustering' in 2D: cells near the centre are 1e-4 of
     # a block side and smaller, where block-relative FP32 positions carry
@@ -195,3 +199,22 @@ def test_localized_2d_fine_grid(precision, order, rtol):
     # included
     s = W.localized(100_000, 2, 0.1, seed=23)
     check(s, (200, 200), precision, order, rtol)
+
+
+# FP64 bar for cells far smaller than the mean spacing s: the on-plane
+# tolerance is tau_rel * s, absolute, so a vertex that one side keeps on a
+# plane and the other cuts moves a volume by up to about tau_rel * s / R
+# relative, 3e-8 for these cells (R about 3e-4 s)
+CORNER_FORMS = [(3, "fp64", "walk", 1e-7), (3, "fp32", "walk", 1e-5), (3, "fp32", "prefetch", 1e-5),
+                (2, "fp64", "walk", 1e-7), (2, "fp32", "walk", 1e-5)]
+
+
+@pytest.mark.parametrize("dim,precision,order,rtol", CORNER_FORMS)
+def test_tiny_cells_at_a_block_corner(dim, precision, order, rtol):
+    # cells 1e-4 of a block side beside a block corner, as at the centre of
+    # the extreme-clustering sets at 10^7-10^8 points: block-relative FP32
+    # positions there are coarse against the cells and their neighbours'
+    # planes, so the FP32 form must test in FP64 where the band cannot
+    # decide, and take FP64 statistics where its vertices are off
+    s = W.corner_cluster(20_000, 2_000, dim, nb=20, seed=40 + dim)
+    check(s, (20,) * dim, precision, order, rtol)
