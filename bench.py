@@ -77,9 +77,11 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # vector area)
 FLOP_VTEST, FLOP_CAND, FLOP_NEWV, FLOP_FANTET = 6, 12, 51, 42
 # DRAM bytes (read + write) of one k_cells3<float,2,64> launch over the 1M
-# uniform cells, from the ncu capture summarised in
-# profiles/k_cells3_fp32_uniform1m_ncu.md (null for other workloads)
-CELL_KERNEL_DRAM_BYTES_UNIFORM1M = 172.645e6 + 289.882e6
+# uniform cells from an ncu capture, or None while the kernel has changed
+# since its counters were taken.  The last capture (172.645 MB read, 289.882
+# MB written, profiles/k_cells3_fp32_uniform1m_ncu.md) predates the FP32
+# safeguards for cells far smaller than a block, so it is not reported.
+CELL_KERNEL_DRAM_BYTES_UNIFORM1M = None
 MLP_ALPHA, MLP_KMIN, MLP_KMAX = 1.5, 24.0, 1024.0
 PKG = os.path.join(ROOT, "paper_2209_11606_gb300")
 MLP_PARAMS = os.path.join(PKG, "mlp_params_gb300.json")
