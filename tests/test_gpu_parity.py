@@ -179,10 +179,11 @@ def test_extreme_clustering_3d(precision, order, rtol):
     check(s, (34, 34, 34), precision, order, rtol)
 
 
-# FP64 bar: the oracle keeps 2D vertices in box coordinates (|x| <= 1), each
-# off by up to 2^-53 |x|, which against cells 1e-4 across is 1e-12 relative
-# per vertex; its worst cells here are off by 3.8e-12 from their exact
-# rational areas (the kernel's particle-relative FP64 vertices are not)
+# FP64 bar: the oracle places each new vertex by interpolating along the
+# edge it cuts, and the first edges are as long as the box, so a vertex is
+# off by up to about 2^-53 of the box side, 1e-12 of a cell 1e-4 across; its
+# worst cells here are 3.8e-12 from their exact rational areas (the kernel
+# intersects the two lines, whose error does not grow with the edge)
 @pytest.mark.parametrize("precision,order,rtol", [("fp64", "walk", 1e-10), ("fp32", "walk", 1e-5)])
 def test_extreme_clustering_2d(precision, order, rtol):
     # Sec. 3.1 'extreme clustering' in 2D: cells near the centre are 1e-4 of
