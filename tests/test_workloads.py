@@ -9,6 +9,7 @@ point beyond 2R cannot cut, Sec. 2.1.3)."""
 from fractions import Fraction
 
 import numpy as np
+import pytest
 
 import oracle
 from paper_2209_11606_gb300 import workloads as W
@@ -85,3 +86,29 @@ def test_oracle_exact_on_corner_cluster_cells_2d():
     # inside the cluster the cells are 1e-4 of a block (20 blocks per side);
     # one at its edge reaches out into the background
     assert np.median(r["rmax"]) < 1e-4 / 20 and r["rmax"].max() < 1e-2 / 20
+
+
+def test_oracle_matches_qhull_on_corner_cluster_cells_3d():
+    # an independent method for the 3D cells of the cluster: qhull's Voronoi
+    # diagram (its vertices in box coordinates, good to about 1e-10 of these
+    # cells) and the convex hull volume of each cell's vertices
+    spatial = pytest.importorskip("scipy.spatial")
+    s = W.corner_cluster(20_000, 2_000, 3, nb=20, seed=43)
+    cells = np.arange(20_000, 22_000, 250)
+    r = oracle.compute(s.pos, s.lo, s.hi, s.periodic, method="grid", nblocks=(20, 20, 20), cells=cells)
+    vor = spatial.Voronoi(s.pos)
+    ridges = {}
+    for (p, q) in vor.ridge_points:
+        ridges.setdefault(int(p), set()).add(int(q))
+        ridges.setdefault(int(q), set()).add(int(p))
+    checked = 0
+    for k, i in enumerate(cells):
+        region = vor.regions[vor.point_region[i]]
+        if -1 in region or r["rmax"][k] > 1e-3 / 20:
+            continue  # only cells inside the cluster (1e-4 of a block), far from every wall
+        vol = spatial.ConvexHull(vor.vertices[region]).volume
+        got = set(r["nbr_id"][r["face_off"][k]:r["face_off"][k + 1]].tolist())
+        assert got == ridges[int(i)], (i, got ^ ridges[int(i)])
+        assert abs(r["vol"][k] - vol) <= 1e-7 * vol, (i, r["vol"][k], vol)
+        checked += 1
+    assert checked >= 5
