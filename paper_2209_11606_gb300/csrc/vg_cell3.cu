@@ -1433,10 +1433,16 @@ __global__ void VG_BOUNDS
                 }
                 T rr = 0;
                 rows = 0;
+                // every vertex lies on an old edge, so within the old radius: one
+                // beyond it, or not finite, is a numerical failure (rr = inf
+                // carries it through the group maximum to every lane)
+                const T r2lim = r2 * (T)1.01;
+                bool wild = false;
 #pragma unroll
                 for (int s = 0; s < VPL; s++) {
                     if (tri[s] != TRI_EMPTY) {
                         T q2 = vx[s] * vx[s] + vy[s] * vy[s] + vz[s] * vz[s];
+                        wild |= !(q2 <= r2lim);
                         if constexpr (F32) q2 *= 1.f + 4e-6f * kap[s];  // allowance for FP32 error
                         rr = rr > q2 ? rr : q2;
                     }
@@ -1445,7 +1451,9 @@ __global__ void VG_BOUNDS
                                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
                     if (__any_sync(gmask, tri[s] != TRI_EMPTY)) rows |= 1u << s;
                 }
+                if (VG_RARE(wild)) rr = (T)INFINITY;
                 r2 = gmax<G>(gmask, rr);
+                if (VG_RARE(!(r2 < (T)INFINITY))) { flags |= 2; break; }
                 __syncwarp(gmask);
                 stop = stop2();
             }
