@@ -17,9 +17,6 @@ Functions follow the paper:
 * :func:`grid_size` -- the block-count rule of Sec. 2.1.4.
 * :func:`block_sort` -- the counting sort of particles into blocks
   (Sec. 2.1.1 and Sec. 2.2.5), written as a stable sort by block index.
-* :func:`quantize_local_f32` -- the FP32 block-local coordinates used by the
-  FP32 form (each coordinate stored as an FP32 offset from its block's lower
-  corner); given here so tests can state exactly what the FP32 form reads.
 """
 from __future__ import annotations
 
@@ -118,22 +115,6 @@ def block_sort(pos, lo, hi, nblocks):
     np.cumsum(counts, out=start[1:])
     order = np.argsort(k, kind="stable")
     return order, start
-
-
-def quantize_local_f32(pos, lo, hi, nblocks) -> np.ndarray:
-    """Positions as the FP32 form stores them: block corner
-    O = lo + b*h (FP64, b as in :func:`block_index`) plus the FP32-rounded
-    offset x - O; returned in FP64.  Multiplication and addition are done
-    as separate roundings."""
-    pos = np.asarray(pos, dtype=np.float64)
-    out = np.empty_like(pos)
-    for a in range(pos.shape[1]):
-        h = (hi[a] - lo[a]) / nblocks[a]
-        b = np.clip(np.floor((pos[:, a] - lo[a]) / h).astype(np.int64), 0, nblocks[a] - 1)
-        corner = lo[a] + b.astype(np.float64) * h
-        off = (pos[:, a] - corner).astype(np.float32).astype(np.float64)
-        out[:, a] = corner + off
-    return out
 
 
 def compute(pos, lo, hi, periodic, radii=None, method: str = "grid", nblocks=None,
