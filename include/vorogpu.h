@@ -77,7 +77,10 @@ enum {
     VG_CELL_OK = 0,
     VG_CELL_EMPTY = 1,   /* radical variant: the cell does not exist
                             (Sec. 2.2.3: compute_cell returns false) */
-    VG_CELL_CAP = 2,     /* vertex or face capacity exceeded on every tier */
+    VG_CELL_CAP = 2,     /* on every tier: vertex or face capacity exceeded,
+                            or a numerical failure (a new vertex off its old
+                            edge or not finite, a Voronoi cell with no vertex
+                            left, an inconsistent face walk) */
     VG_CELL_DUP = 3,     /* another particle sits on this one */
     VG_CELL_LIMIT = 4    /* the walk ran past its shell limit */
 };
@@ -155,26 +158,35 @@ vg_status vg_batch_create(vg_ctx **out, int dim, int nsys, const vg_system *syst
 /*
  * Replaces the particles of every system of a batched container.  counts[k]
  * (nsys entries) particles belong to system k; `pos` holds all systems' rows
- * one system after another (sum(counts) x dim doubles) and `radii` (or NULL)
- * likewise.  Cell i and neighbour ids use this concatenated numbering, so
- * system k's cells are the input indices [sum(counts[<k]), sum(counts[<=k])).
- * Validation and errors as vg_insert(); the per-system n_opt rule fixes the
- * grids here.
+ * one system after another (sum(counts) x dim values of type `dtype`) and
+ * `radii` (or NULL) likewise.  Cell i and neighbour ids use this
+ * concatenated numbering, so system k's cells are the input indices
+ * [sum(counts[<k]), sum(counts[<=k])).  Validation and errors as
+ * vg_insert(); the per-system n_opt rule fixes the grids here.
  */
-vg_status vg_batch_insert(vg_ctx *ctx, const int64_t *counts, const double *pos,
-                          const double *radii, int on_device);
+vg_status vg_batch_insert(vg_ctx *ctx, const int64_t *counts, const void *pos,
+                          const void *radii, int dtype, int on_device);
+
+/* Element type of the input positions and radii. */
+enum {
+    VG_F64 = 0,  /* double */
+    VG_F32 = 1   /* float: widened to double on the device before the sort,
+                    so the cells are those of the FP32 values read as FP64 */
+};
 
 /*
  * Replaces the container's particles (the paper's clear() followed by
  * add_parallel(), Sec. 2.2.5) and sorts them into blocks with a counting
- * sort on the GPU.  `pos` is n x dim doubles, row-major; `radii` is n doubles
- * or NULL (NULL: plain Voronoi; non-NULL: radical variant).  Coordinates on
- * a periodic axis are wrapped into [lo, hi); on a walled axis they must lie
+ * sort on the GPU.  `pos` is n x dim values, row-major, and `radii` n values
+ * or NULL (NULL: plain Voronoi; non-NULL: radical variant), both of type
+ * `dtype` (VG_F64 or VG_F32; VG_ERR_ARG otherwise).  Coordinates on a
+ * periodic axis are wrapped into [lo, hi); on a walled axis they must lie
  * in [lo, hi] (VG_ERR_OUT_OF_BOX otherwise; a point on hi goes to the last
- * block).  Inside a block particles are ordered by input index, so results
- * do not depend on thread timing.
+ * block).  A NaN or infinite coordinate, or a radius that is negative or
+ * not finite, gives VG_ERR_NONFINITE.  Inside a block particles are ordered
+ * by input index, so results do not depend on thread timing.
  */
-vg_status vg_insert(vg_ctx *ctx, int64_t n, const double *pos, const double *radii,
+vg_status vg_insert(vg_ctx *ctx, int64_t n, const void *pos, const void *radii, int dtype,
                     int on_device);
 
 /* Computes all cells with the given configuration (NULL: defaults). */
@@ -196,20 +208,22 @@ vg_status vg_compute_subset(vg_ctx *ctx, const vg_config *cfg, const int32_t *ce
  * the per-step host work of vg_insert + vg_compute).  Captures, into a graph
  * owned by the context: the counting sort of counts[k] particles of system k
  * (one entry per system; one for a vg_create container) read from the DEVICE
- * arrays `pos` (n x dim doubles) and `radii` (n doubles or NULL), the cell
- * kernels with `cfg` (NULL: defaults) and the face compaction.  Before
+ * arrays `pos` (n x dim values) and `radii` (n values or NULL) of type
+ * `dtype` (VG_F64 or VG_F32, as vg_insert()), the cell kernels with `cfg`
+ * (NULL: defaults) and the face compaction.  Before
  * capturing it runs one eager vg_insert + vg_compute on the same input: that
  * validates the input, sizes every buffer (the face buffer with 25 %
  * headroom) and leaves valid results.  The caller keeps `pos` and `radii` at
  * the same addresses while the graph exists and may overwrite their contents
  * between replays (same counts).  Any later vg_insert, vg_batch_insert or
  * vg_compute drops the graph.  With cfg->time_kernels = 1 every replay
- * records the cell-kernel time read by vg_get_kernel_ms().
+ * records the cell-kernel time read by vg_get_kernel_ms() and the sort time
+ * read by vg_get_sort_ms().
  * Errors: VG_ERR_ARG (host input pointers, bad counts), those of vg_insert()
  * and vg_compute(), VG_ERR_CUDA when capture or instantiation fails.
  */
-vg_status vg_graph_capture(vg_ctx *ctx, const int64_t *counts, const double *pos,
-                           const double *radii, const vg_config *cfg);
+vg_status vg_graph_capture(vg_ctx *ctx, const int64_t *counts, const void *pos,
+                           const void *radii, int dtype, const vg_config *cfg);
 
 /* Replays the captured graph on the context's stream; asynchronous.
  * VG_ERR_STATE when no graph is held. */
@@ -298,6 +312,15 @@ vg_status vg_get_weinberg(vg_ctx *ctx, int32_t *len, uint64_t *hash, int32_t *sy
  * milliseconds and the number of computes.  Synchronises the stream.
  */
 vg_status vg_get_kernel_ms(vg_ctx *ctx, double *total_ms, int64_t *count);
+
+/*
+ * Device time of the counting sort (FP32 widening, largest radius, block
+ * keys and slots, scans, scatter, in-block order, learned preload targets:
+ * Sec. 2.1.1 and Sec. 2.2.5) in every graph replay captured with
+ * time_kernels = 1 since the previous call of this function: the sum in
+ * milliseconds and the number of replays.  Synchronises the stream.
+ */
+vg_status vg_get_sort_ms(vg_ctx *ctx, double *total_ms, int64_t *count);
 
 /*
  * The sorted container: block_start has B+1 entries (B = product of the
@@ -428,12 +451,15 @@ vg_status vg_set_predictor(vg_ctx *ctx, vg_mlp *mlp, float alpha, float kmin, fl
  * Returns VG_ERR_ARG (with the reason in errbuf) when n or B exceeds the
  * limits above, VG_ERR_OUT_OF_BOX / VG_ERR_NONFINITE as vg_insert() does,
  * VG_ERR_CUDA on a CUDA failure.  It calls no cudaMalloc, cudaFree or other
- * allocating routine.  The first call on each device looks up the device
- * address of the scratch array (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls on a
- * device share the one scratch array, so calls that overlap on the GPU (from
- * two streams or two host threads) race and must be serialised by the
- * caller.
+ * allocating routine.  Every call ends by reading the error flags back to a
+ * host variable and synchronising `stream`.  The first call on each device
+ * looks up the device address of the scratch array (cudaGetSymbolAddress)
+ * with that device current and keeps it for the rest of the process; make
+ * that first call before any stream capture, and do not call this entry
+ * point after resetting the device (cudaDeviceReset), which would leave the
+ * kept address stale.  All calls on a device share the one scratch array,
+ * so calls that overlap on the GPU (from two streams or two host threads)
+ * race and must be serialised by the caller.
  */
 vg_status vg_sort_blocks_noalloc(int dim, const double *lo, const double *hi, const int *periodic,
                                  const int *nblocks, int64_t n, const double *pos,

@@ -228,18 +228,20 @@ void release_graph(vg_ctx *c) {
     if (c->graph) cudaGraphDestroy(c->graph);
     c->gexec = nullptr;
     c->graph = nullptr;
-    c->gev_node[0] = c->gev_node[1] = nullptr;
+    for (int k = 0; k < 4; k++) c->gev_node[k] = nullptr;
     c->graph_unchecked = 0;
 }
 
 // Host half of an insert: validation, layout of the systems, buffers, and
-// the copy of host input to the device.  Returns the device input pointers.
-vg_status prepare_insert(vg_ctx *c, const std::vector<long long> &counts, const double *pos, const double *radii,
-                         int on_device, const double **dpos, const double **drad) {
+// the copy of host input to the device.  Returns the device input pointers
+// (of type `dtype`; FP32 input is widened by enqueue_sort).
+vg_status prepare_insert(vg_ctx *c, const std::vector<long long> &counts, const void *pos, const void *radii,
+                         int dtype, int on_device, const void **dpos, const void **drad) {
     long long n = 0;
     for (long long k : counts) n += k;
     if (n > 0x7ffffffe) return fail(c, VG_ERR_ARG, "particle count out of range");
     if (n > 0 && !pos) return fail(c, VG_ERR_ARG, "pos is NULL");
+    if (dtype != VG_F64 && dtype != VG_F32) return fail(c, VG_ERR_ARG, "dtype must be VG_F64 or VG_F32");
     // buffers may move below: a captured graph would point at freed memory
     release_graph(c);
     c->inserted = 0;
@@ -277,9 +279,15 @@ vg_status prepare_insert(vg_ctx *c, const std::vector<long long> &counts, const 
     VG_CUDA(ensure(c, c->d_w_pref, n));
     VG_CUDA(ensure(c, c->d_rfin, n));
     VG_CUDA(ensure(c, c->d_w_fallback, n));
-    if (!on_device) {
+    // FP64 staging: host FP64 input is copied there, FP32 input (host or
+    // device) is widened into it
+    if (!on_device || dtype == VG_F32) {
         VG_CUDA(ensure(c, c->d_pos, n * d));
         if (radii) VG_CUDA(ensure(c, c->d_rad, n));
+    }
+    if (!on_device && dtype == VG_F32) {
+        VG_CUDA(ensure(c, c->d_pos32, n * d));
+        if (radii) VG_CUDA(ensure(c, c->d_rad32, n));
     }
     VG_CUDA(ensure(c, c->d_count, c->total_blk));
     if (c->pred) {
@@ -304,11 +312,14 @@ vg_status prepare_insert(vg_ctx *c, const std::vector<long long> &counts, const 
     *dpos = pos;
     *drad = radii;
     if (n > 0 && !on_device) {
-        VG_CUDA(cudaMemcpyAsync(c->d_pos, pos, sizeof(double) * n * d, cudaMemcpyHostToDevice, c->stream));
-        *dpos = c->d_pos;
+        const size_t es = dtype == VG_F32 ? sizeof(float) : sizeof(double);
+        void *stage_p = dtype == VG_F32 ? (void *)c->d_pos32 : (void *)c->d_pos;
+        void *stage_r = dtype == VG_F32 ? (void *)c->d_rad32 : (void *)c->d_rad;
+        VG_CUDA(cudaMemcpyAsync(stage_p, pos, es * n * d, cudaMemcpyHostToDevice, c->stream));
+        *dpos = stage_p;
         if (radii) {
-            VG_CUDA(cudaMemcpyAsync(c->d_rad, radii, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
-            *drad = c->d_rad;
+            VG_CUDA(cudaMemcpyAsync(stage_r, radii, es * n, cudaMemcpyHostToDevice, c->stream));
+            *drad = stage_r;
         }
     }
     c->n = n;
@@ -316,12 +327,24 @@ vg_status prepare_insert(vg_ctx *c, const std::vector<long long> &counts, const 
     return VG_OK;
 }
 
-// Device half of an insert: the counting sort of all systems, enqueued on
-// `s` with no host synchronisation (so it can be captured in a graph).
-cudaError_t enqueue_sort(vg_ctx *c, const double *dpos, const double *drad, cudaStream_t s) {
+// Device half of an insert: FP32 input widened to FP64, then the counting
+// sort of all systems, enqueued on `s` with no host synchronisation (so it
+// can be captured in a graph).
+cudaError_t enqueue_sort(vg_ctx *c, const void *src_pos, const void *src_rad, int dtype, cudaStream_t s) {
     const int nsys = (int)c->sys.size();
+    const double *dpos = (const double *)src_pos, *drad = (const double *)src_rad;
+    cudaError_t e = cudaSuccess;
+    if (dtype == VG_F32) {
+        e = widen_f32((const float *)src_pos, c->d_pos, c->n * c->dim, s);
+        dpos = c->d_pos;
+        if (e == cudaSuccess && src_rad) {
+            e = widen_f32((const float *)src_rad, c->d_rad, c->n, s);
+            drad = c->d_rad;
+        }
+        if (e != cudaSuccess) return e;
+    }
     // fresh descriptors: r_max is accumulated from 0 by system_rmax
-    cudaError_t e = cudaMemcpyAsync(c->d_sys, c->d_sys_init, sizeof(Sys) * nsys, cudaMemcpyDeviceToDevice, s);
+    e = cudaMemcpyAsync(c->d_sys, c->d_sys_init, sizeof(Sys) * nsys, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess && drad) e = system_rmax(c->d_sys, nsys, c->n, drad, s);
     if (e == cudaSuccess)
         e = sort_particles(c->d_sys, nsys, c->dim, c->total_blk, c->n, dpos, drad, c->d_key, c->d_slot, c->d_count,
@@ -346,13 +369,13 @@ vg_status read_input_flags(vg_ctx *c) {
 
 // Shared by vg_insert and vg_batch_insert: counts[k] particles of system k,
 // all systems' rows concatenated in `pos` / `radii`.
-vg_status insert_all(vg_ctx *c, const std::vector<long long> &counts, const double *pos, const double *radii,
-                     int on_device) {
-    const double *dpos = nullptr, *drad = nullptr;
-    vg_status s = prepare_insert(c, counts, pos, radii, on_device, &dpos, &drad);
+vg_status insert_all(vg_ctx *c, const std::vector<long long> &counts, const void *pos, const void *radii,
+                     int dtype, int on_device) {
+    const void *dpos = nullptr, *drad = nullptr;
+    vg_status s = prepare_insert(c, counts, pos, radii, dtype, on_device, &dpos, &drad);
     if (s != VG_OK) return s;
     const long long l0 = g_launch_count;
-    cudaError_t e = enqueue_sort(c, dpos, drad, c->stream);
+    cudaError_t e = enqueue_sort(c, dpos, drad, dtype, c->stream);
     c->launches += g_launch_count - l0;
     if (e != cudaSuccess) return cuda_fail(c, e, "sort_particles");
     if ((s = read_input_flags(c)) != VG_OK) return s;
@@ -531,15 +554,16 @@ vg_status vg_batch_create(vg_ctx **out, int dim, int nsys, const vg_system *syst
     return VG_OK;
 }
 
-vg_status vg_insert(vg_ctx *c, int64_t n, const double *pos, const double *radii, int on_device) {
+vg_status vg_insert(vg_ctx *c, int64_t n, const void *pos, const void *radii, int dtype, int on_device) {
     if (!c) return VG_ERR_ARG;
     if (c->batched) return fail(c, VG_ERR_STATE, "batched container: use vg_batch_insert");
     if (n < 0) return fail(c, VG_ERR_ARG, "negative particle count");
     std::vector<long long> counts(1, (long long)n);
-    return insert_all(c, counts, pos, radii, on_device);
+    return insert_all(c, counts, pos, radii, dtype, on_device);
 }
 
-vg_status vg_batch_insert(vg_ctx *c, const int64_t *counts, const double *pos, const double *radii, int on_device) {
+vg_status vg_batch_insert(vg_ctx *c, const int64_t *counts, const void *pos, const void *radii, int dtype,
+                          int on_device) {
     if (!c) return VG_ERR_ARG;
     if (!counts) return fail(c, VG_ERR_ARG, "counts is NULL");
     std::vector<long long> cv(c->sys.size());
@@ -547,7 +571,7 @@ vg_status vg_batch_insert(vg_ctx *c, const int64_t *counts, const double *pos, c
         if (counts[k] < 0) return fail(c, VG_ERR_ARG, "negative particle count");
         cv[k] = counts[k];
     }
-    return insert_all(c, cv, pos, radii, on_device);
+    return insert_all(c, cv, pos, radii, dtype, on_device);
 }
 
 vg_status vg_compute(vg_ctx *c, const vg_config *cfg_in) {
@@ -665,7 +689,7 @@ vg_status vg_compute_subset(vg_ctx *c, const vg_config *cfg_in, const int32_t *c
     return VG_OK;
 }
 
-vg_status vg_graph_capture(vg_ctx *c, const int64_t *counts, const double *pos, const double *radii,
+vg_status vg_graph_capture(vg_ctx *c, const int64_t *counts, const void *pos, const void *radii, int dtype,
                            const vg_config *cfg_in) {
     if (!c) return VG_ERR_ARG;
     vg_config cfg;
@@ -681,7 +705,7 @@ vg_status vg_graph_capture(vg_ctx *c, const int64_t *counts, const double *pos, 
         n += cv[k];
     }
     // a replay reads its input from fixed device addresses
-    for (const double *p : {pos, radii}) {
+    for (const void *p : {pos, radii}) {
         if (!p) continue;
         cudaPointerAttributes at;
         if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -694,7 +718,7 @@ vg_status vg_graph_capture(vg_ctx *c, const int64_t *counts, const double *pos, 
     std::vector<int64_t> keep(counts, counts + cv.size());
     // one eager pass validates the input, sizes every buffer and leaves
     // valid results
-    if ((s = insert_all(c, cv, pos, radii, 1)) != VG_OK) return s;
+    if ((s = insert_all(c, cv, pos, radii, dtype, 1)) != VG_OK) return s;
     vg_config eager = cfg;
     eager.time_kernels = 0;
     if ((s = vg_compute(c, &eager)) != VG_OK) return s;
@@ -711,12 +735,14 @@ vg_status vg_graph_capture(vg_ctx *c, const int64_t *counts, const double *pos, 
     if (!c->gstream) VG_CUDA(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
     const bool timed = cfg.time_kernels != 0;
     if (timed)
-        for (int k = 0; k < 2; k++)
+        for (int k = 0; k < 4; k++)
             if (!c->gev[k]) VG_CUDA(cudaEventCreate(&c->gev[k]));
     const long long l0 = g_launch_count;
     cudaStream_t gs = c->gstream;
     VG_CUDA(cudaStreamBeginCapture(gs, cudaStreamCaptureModeRelaxed));
-    cudaError_t e = enqueue_sort(c, pos, radii, gs);
+    cudaError_t e = timed ? cudaEventRecordWithFlags(c->gev[2], gs, cudaEventRecordExternal) : cudaSuccess;
+    if (e == cudaSuccess) e = enqueue_sort(c, pos, radii, dtype, gs);
+    if (e == cudaSuccess && timed) e = cudaEventRecordWithFlags(c->gev[3], gs, cudaEventRecordExternal);
     if (e == cudaSuccess && timed) e = cudaEventRecordWithFlags(c->gev[0], gs, cudaEventRecordExternal);
     if (e == cudaSuccess) e = enqueue_cells(c, cfg, gs);
     if (e == cudaSuccess && timed) e = cudaEventRecordWithFlags(c->gev[1], gs, cudaEventRecordExternal);
@@ -746,10 +772,10 @@ vg_status vg_graph_capture(vg_ctx *c, const int64_t *counts, const double *pos, 
             if (ty != cudaGraphNodeTypeEventRecord) continue;
             cudaEvent_t ev = nullptr;
             VG_CUDA(cudaGraphEventRecordNodeGetEvent(nd, &ev));
-            for (int k = 0; k < 2; k++)
+            for (int k = 0; k < 4; k++)
                 if (ev == c->gev[k]) c->gev_node[k] = nd;
         }
-        if (!c->gev_node[0] || !c->gev_node[1]) {
+        if (!c->gev_node[0] || !c->gev_node[1] || !c->gev_node[2] || !c->gev_node[3]) {
             release_graph(c);
             return fail(c, VG_ERR_CUDA, "graph capture lost its timing events");
         }
@@ -759,6 +785,7 @@ vg_status vg_graph_capture(vg_ctx *c, const int64_t *counts, const double *pos, 
     c->g_counts = keep;
     c->g_pos = pos;
     c->g_rad = radii;
+    c->g_dtype = dtype;
     c->g_cfg = cfg;
     return VG_OK;
 }
@@ -773,6 +800,14 @@ vg_status vg_graph_launch(vg_ctx *c) {
             VG_CUDA(cudaGraphExecEventRecordNodeSetEvent(c->gexec, c->gev_node[k], ev));
         }
         c->nev++;
+    }
+    if (c->graph_timed && c->nsev < vg_ctx::NEV) {
+        for (int k = 0; k < 2; k++) {
+            cudaEvent_t &ev = c->sev[2 * c->nsev + k];
+            if (!ev) VG_CUDA(cudaEventCreate(&ev));
+            VG_CUDA(cudaGraphExecEventRecordNodeSetEvent(c->gexec, c->gev_node[2 + k], ev));
+        }
+        c->nsev++;
     }
     VG_CUDA(cudaGraphLaunch(c->gexec, c->stream));
     c->launches += c->graph_kernels;
@@ -877,6 +912,21 @@ vg_status vg_get_kernel_ms(vg_ctx *c, double *total_ms, int64_t *count) {
     return VG_OK;
 }
 
+vg_status vg_get_sort_ms(vg_ctx *c, double *total_ms, int64_t *count) {
+    if (!c || !total_ms || !count) return VG_ERR_ARG;
+    VG_CUDA(cudaStreamSynchronize(c->stream));
+    double t = 0;
+    for (int k = 0; k < c->nsev; k++) {
+        float ms = 0;
+        VG_CUDA(cudaEventElapsedTime(&ms, c->sev[2 * k], c->sev[2 * k + 1]));
+        t += ms;
+    }
+    *total_ms = t;
+    *count = c->nsev;
+    c->nsev = 0;
+    return VG_OK;
+}
+
 vg_status vg_get_work(vg_ctx *c, int32_t *n_tested, int32_t *n_vtests, int32_t *n_cuts, int32_t *n_newv,
                       int32_t *n_retest, uint8_t *fallback, int32_t *n_prefetch, int on_device) {
     if (!c) return VG_ERR_ARG;
@@ -953,7 +1003,7 @@ const char *vg_last_error(vg_ctx *c) { return c ? c->err.c_str() : "null context
 
 void vg_destroy(vg_ctx *c) {
     if (!c) return;
-    release(c->d_pos); release(c->d_rad); release(c->d_key); release(c->d_slot); release(c->d_tmp);
+    release(c->d_pos); release(c->d_rad); release(c->d_pos32); release(c->d_rad32); release(c->d_key); release(c->d_slot); release(c->d_tmp);
     release(c->d_p32); release(c->d_p64); release(c->d_sid); release(c->d_sblk); release(c->d_ssys);
     release(c->d_count); release(c->d_bstart); release(c->d_err); release(c->d_sys);
     if (c->d_scan) cudaFree(c->d_scan);
@@ -970,11 +1020,13 @@ void vg_destroy(vg_ctx *c) {
     release(c->d_rank); release(c->d_subset); release(c->d_subset_in);
     release(c->d_sys_init);
     release_graph(c);
-    for (int k = 0; k < 2; k++)
+    for (int k = 0; k < 4; k++)
         if (c->gev[k]) cudaEventDestroy(c->gev[k]);
     if (c->gstream) cudaStreamDestroy(c->gstream);
-    for (int k = 0; k < 2 * vg_ctx::NEV; k++)
+    for (int k = 0; k < 2 * vg_ctx::NEV; k++) {
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+        if (c->sev[k]) cudaEventDestroy(c->sev[k]);
+    }
     delete c;
 }
 
@@ -999,7 +1051,7 @@ vg_status graph_check(vg_ctx *c) {
     if ((long long)used <= c->fcap) return VG_OK;
     const std::vector<int64_t> counts = c->g_counts;
     const vg_config cfg = c->g_cfg;
-    return vg_graph_capture(c, counts.data(), c->g_pos, c->g_rad, &cfg);
+    return vg_graph_capture(c, counts.data(), c->g_pos, c->g_rad, c->g_dtype, &cfg);
 }
 
 }  // namespace

@@ -161,6 +161,8 @@ cudaError_t sort_particles(const Sys *sys, int nsys, int dim, long long total_bl
                            int *bstart, int *tmp_id, float4 *p32, D4 *p64, int *sid, int *sblk,
                            int *ssys, int *errflags, void *scan_tmp, cudaStream_t st);
 cudaError_t system_rmax(Sys *sys, int nsys, long long n, const double *radii, cudaStream_t st);
+// FP32 input widened to FP64 (n values), the form every sort kernel reads.
+cudaError_t widen_f32(const float *in, double *out, long long n, cudaStream_t st);
 size_t scan_tmp_bytes_i32(long long n);
 size_t scan_tmp_bytes_i64(long long n);
 cudaError_t exclusive_scan_i32(const int *in, int *out, long long n, void *tmp, cudaStream_t st);
@@ -221,7 +223,8 @@ struct vg_ctx {
     int inserted = 0, computed = 0;
 
     // per-particle device buffers
-    double *d_pos = nullptr, *d_rad = nullptr;   // staged copies of host input
+    double *d_pos = nullptr, *d_rad = nullptr;   // staged copies of host input; FP32 input widened
+    float *d_pos32 = nullptr, *d_rad32 = nullptr; // host FP32 input staged before widening
     int *d_key = nullptr, *d_slot = nullptr, *d_tmp = nullptr, *d_ssys = nullptr;
     float4 *d_p32 = nullptr;
     vg::D4 *d_p64 = nullptr;
@@ -274,13 +277,18 @@ struct vg_ctx {
     cudaStream_t gstream = nullptr;       // capture stream (non-blocking)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    cudaEvent_t gev[2] = {nullptr, nullptr};           // event nodes around the cell kernels
-    cudaGraphNode_t gev_node[2] = {nullptr, nullptr};
+    // event nodes around the cell kernels ([0], [1]) and the sort ([2], [3])
+    cudaEvent_t gev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaGraphNode_t gev_node[4] = {nullptr, nullptr, nullptr, nullptr};
+    // event pairs around the sort of timed graph replays
+    cudaEvent_t sev[2 * NEV] = {};
+    int nsev = 0;
     long long graph_kernels = 0;          // kernels one replay launches
     int graph_timed = 0;
     int graph_unchecked = 0;              // replayed, flags not read yet
     std::vector<int64_t> g_counts;        // capture arguments, for a re-capture
-    const double *g_pos = nullptr, *g_rad = nullptr;
+    const void *g_pos = nullptr, *g_rad = nullptr;
+    int g_dtype = 0;
     vg_config g_cfg{};
 
     // learned preload targets, one per block (valid until the next insert)

@@ -244,6 +244,20 @@ __global__ void k_total(const TI *in, TO *out, long long n) {
 }
 }  // namespace
 
+namespace {
+__global__ void k_widen(const float *__restrict__ in, double *__restrict__ out, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (double)in[i];
+}
+}  // namespace
+
+cudaError_t widen_f32(const float *in, double *out, long long n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    ++g_launch_count;
+    k_widen<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, out, n);
+    return cudaGetLastError();
+}
+
 cudaError_t system_rmax(Sys *sys, int nsys, long long n, const double *radii, cudaStream_t st) {
     if (n <= 0 || !radii) return cudaSuccess;
     ++g_launch_count;

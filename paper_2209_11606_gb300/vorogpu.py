@@ -20,6 +20,8 @@ VG_OK = 0
 STATUS_NAMES = {0: "VG_OK", 1: "VG_ERR_ARG", 2: "VG_ERR_OOM", 3: "VG_ERR_OUT_OF_BOX",
                 4: "VG_ERR_NONFINITE", 5: "VG_ERR_CAP", 6: "VG_ERR_CUDA", 7: "VG_ERR_STATE",
                 8: "VG_ERR_DUP_POINT"}
+STATUS_CODES = {v: k for k, v in STATUS_NAMES.items()}
+VG_F64, VG_F32 = 0, 1
 VG_FP64, VG_FP32_RETEST = 0, 1
 VG_WALK, VG_PREFETCH = 0, 1
 VG_CELL_OK, VG_CELL_EMPTY, VG_CELL_CAP, VG_CELL_DUP, VG_CELL_LIMIT = 0, 1, 2, 3, 4
@@ -27,7 +29,7 @@ VG_CELL_OK, VG_CELL_EMPTY, VG_CELL_CAP, VG_CELL_DUP, VG_CELL_LIMIT = 0, 1, 2, 3,
 EXPORTS = ["vg_config_default", "vg_create", "vg_batch_create", "vg_insert", "vg_batch_insert",
            "vg_compute", "vg_compute_subset", "vg_get_counts", "vg_get_cells", "vg_get_faces", "vg_get_work",
            "vg_get_radius", "vg_get_weinberg", "vg_get_sorted", "vg_get_grid", "vg_get_system_grid", "vg_get_launches",
-           "vg_get_kernel_ms", "vg_graph_capture", "vg_graph_launch", "vg_graph_sync",
+           "vg_get_kernel_ms", "vg_get_sort_ms", "vg_graph_capture", "vg_graph_launch", "vg_graph_sync",
            "vg_sort_blocks_noalloc", "vg_last_error", "vg_destroy",
            "vg_mlp_create", "vg_mlp_destroy", "vg_mlp_last_error", "vg_mlp_set_params",
            "vg_mlp_get_params", "vg_mlp_features", "vg_mlp_labels", "vg_mlp_dataset",
@@ -71,11 +73,11 @@ def load(path: str = LIB_PATH):
         "vg_config_default": (None, [ctypes.POINTER(VgConfig)]),
         "vg_create": (I, [ctypes.POINTER(P), I, P, P, P, P, D, P]),
         "vg_batch_create": (I, [ctypes.POINTER(P), I, I, ctypes.POINTER(VgSystem), P]),
-        "vg_insert": (I, [P, L, P, P, I]),
-        "vg_batch_insert": (I, [P, P, P, P, I]),
+        "vg_insert": (I, [P, L, P, P, I, I]),
+        "vg_batch_insert": (I, [P, P, P, P, I, I]),
         "vg_compute": (I, [P, ctypes.POINTER(VgConfig)]),
         "vg_compute_subset": (I, [P, ctypes.POINTER(VgConfig), P, L, I]),
-        "vg_graph_capture": (I, [P, P, P, P, ctypes.POINTER(VgConfig)]),
+        "vg_graph_capture": (I, [P, P, P, P, I, ctypes.POINTER(VgConfig)]),
         "vg_graph_launch": (I, [P]),
         "vg_graph_sync": (I, [P]),
         "vg_get_counts": (I, [P, ctypes.POINTER(L), ctypes.POINTER(L)]),
@@ -85,6 +87,7 @@ def load(path: str = LIB_PATH):
         "vg_get_radius": (I, [P, P, I]),
         "vg_get_weinberg": (I, [P, P, P, P, I]),
         "vg_get_kernel_ms": (I, [P, ctypes.POINTER(D), ctypes.POINTER(L)]),
+        "vg_get_sort_ms": (I, [P, ctypes.POINTER(D), ctypes.POINTER(L)]),
         "vg_get_sorted": (I, [P, ctypes.POINTER(L), P, P, I]),
         "vg_get_grid": (I, [P, P]),
         "vg_get_system_grid": (I, [P, I, P]),
@@ -131,7 +134,52 @@ def _ptr(x):
     # torch tensor
     if not x.is_contiguous():
         raise ValueError("tensor must be contiguous")
+    if x.is_cuda:
+        import torch
+        if x.device.index != torch.cuda.current_device():
+            raise ValueError(f"tensor is on {x.device}, but the current device is "
+                             f"cuda:{torch.cuda.current_device()}")
     return x.data_ptr(), 1 if x.is_cuda else 0
+
+
+def _dtype_name(x) -> str:
+    """'float64', 'float32', 'int32', ... of a numpy array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        return x.dtype.name
+    return str(x.dtype).replace("torch.", "")
+
+
+def _numel(x) -> int:
+    return int(x.size) if isinstance(x, np.ndarray) else int(x.numel())
+
+
+def _input_dtype(pos, radii, n, dim):
+    """VG_F64 or VG_F32 for positions of shape (n, dim) and radii of shape
+    (n,) of one floating type; anything else raises before the library can
+    read past a buffer."""
+    dt = _dtype_name(pos)
+    if dt not in ("float64", "float32"):
+        raise ValueError(f"positions must be float64 or float32, not {dt}")
+    if tuple(pos.shape) != (n, dim):
+        raise ValueError(f"positions must have shape ({n}, {dim}), not {tuple(pos.shape)}")
+    if radii is not None:
+        if _dtype_name(radii) != dt:
+            raise ValueError("radii must have the positions' dtype")
+        if tuple(radii.shape) != (n,):
+            raise ValueError(f"radii must have shape ({n},), not {tuple(radii.shape)}")
+    return VG_F32 if dt == "float32" else VG_F64
+
+
+# dimension of every live container, by handle value (inputs are checked
+# against it before they reach the library)
+_ctx_dim: dict = {}
+
+
+def _dim_of(ctx) -> int:
+    key = ctx.value if isinstance(ctx, ctypes.c_void_p) else ctx
+    if key not in _ctx_dim:
+        raise ValueError("not a live container")
+    return _ctx_dim[key]
 
 
 def vg_config_default() -> VgConfig:
@@ -154,6 +202,7 @@ def vg_create(dim, lo, hi, periodic, nblocks=None, n_opt=0.0, stream=None):
                          None if nb is None else nb.ctypes.data, float(n_opt), st)
     if code != VG_OK:
         raise VgError(code, "vg_create failed")
+    _ctx_dim[h.value] = int(dim)
     return h
 
 
@@ -179,6 +228,7 @@ def vg_batch_create(dim, systems, stream=None):
     code = lib.vg_batch_create(ctypes.byref(h), int(dim), len(systems), arr, st)
     if code != VG_OK:
         raise VgError(code, "vg_batch_create failed")
+    _ctx_dim[h.value] = int(dim)
     return h
 
 
@@ -192,16 +242,20 @@ def vg_batch_insert(ctx, counts, pos, radii=None):
         raise ValueError("pos and radii must both be host or both device")
     if int(cnt.sum()) != pos.shape[0]:
         raise ValueError("counts do not add up to the rows of pos")
-    _check(ctx, load().vg_batch_insert(ctx, cnt.ctypes.data, p, r, dev))
+    dt = _input_dtype(pos, radii, int(cnt.sum()), _dim_of(ctx))
+    _check(ctx, load().vg_batch_insert(ctx, cnt.ctypes.data, p, r, dt, dev))
 
 
 def vg_insert(ctx, pos, radii=None):
+    """Positions (n, dim) and optional radii (n,), float64 or float32 (one
+    type for both), numpy arrays or CUDA tensors on the current device."""
     p, dev = _ptr(pos)
     r, rdev = _ptr(radii)
     if radii is not None and rdev != dev:
         raise ValueError("pos and radii must both be host or both device")
     n = pos.shape[0]
-    _check(ctx, load().vg_insert(ctx, n, p, r, dev))
+    dt = _input_dtype(pos, radii, n, _dim_of(ctx))
+    _check(ctx, load().vg_insert(ctx, n, p, r, dt, dev))
 
 
 def vg_compute(ctx, cfg: VgConfig | None = None):
@@ -228,7 +282,8 @@ def vg_graph_capture(ctx, counts, pos, radii=None, cfg: VgConfig | None = None):
         raise ValueError("graph inputs must be CUDA tensors")
     if int(cnt.sum()) != pos.shape[0]:
         raise ValueError("counts do not add up to the rows of pos")
-    _check(ctx, load().vg_graph_capture(ctx, cnt.ctypes.data, p, r,
+    dt = _input_dtype(pos, radii, int(cnt.sum()), _dim_of(ctx))
+    _check(ctx, load().vg_graph_capture(ctx, cnt.ctypes.data, p, r, dt,
                                         None if cfg is None else ctypes.byref(cfg)))
 
 
@@ -311,6 +366,12 @@ def vg_get_kernel_ms(ctx):
     return t.value, c.value
 
 
+def vg_get_sort_ms(ctx):
+    t, c = ctypes.c_double(), ctypes.c_int64()
+    _check(ctx, load().vg_get_sort_ms(ctx, ctypes.byref(t), ctypes.byref(c)))
+    return t.value, c.value
+
+
 def vg_get_launches(ctx):
     v = ctypes.c_int64()
     _check(ctx, load().vg_get_launches(ctx, ctypes.byref(v)))
@@ -319,12 +380,26 @@ def vg_get_launches(ctx):
 
 def vg_sort_blocks_noalloc(dim, lo, hi, periodic, nblocks, pos, block_start, order, stream=None):
     """Counting sort into blocks with no device allocation (see vorogpu.h):
-    `pos`, `block_start` and `order` are CUDA tensors; raises VgError with
-    the library's reason on failure."""
+    `pos` (n, dim) float64, `block_start` (>= B + 1) and `order` (>= n)
+    int32, all CUDA tensors on the current device; raises ValueError before
+    the call on any other shape, type or device (the library cannot check
+    the sizes of caller buffers), and VgError with the library's reason on
+    failure."""
     lo = np.ascontiguousarray(lo, dtype=np.float64)
     hi = np.ascontiguousarray(hi, dtype=np.float64)
     per = np.ascontiguousarray([1 if p else 0 for p in periodic], dtype=np.int32)
     nb = np.ascontiguousarray(nblocks, dtype=np.int32)
+    dim = int(dim)
+    if dim not in (2, 3) or lo.shape != (dim,) or hi.shape != (dim,) or per.shape != (dim,) or nb.shape != (dim,):
+        raise ValueError("lo, hi, periodic and nblocks must each hold dim (2 or 3) entries")
+    n = int(pos.shape[0])
+    if _dtype_name(pos) != "float64" or tuple(pos.shape) != (n, dim):
+        raise ValueError(f"pos must be float64 of shape (n, {dim})")
+    nblk = int(np.prod(nb.astype(np.int64)))
+    if _dtype_name(block_start) != "int32" or _numel(block_start) < nblk + 1:
+        raise ValueError(f"block_start must be int32 with at least {nblk + 1} entries")
+    if _dtype_name(order) != "int32" or _numel(order) < n:
+        raise ValueError(f"order must be int32 with at least {n} entries")
     for t in (pos, block_start, order):
         if _ptr(t)[1] != 1:
             raise ValueError("pos, block_start and order must be CUDA tensors")
@@ -332,8 +407,8 @@ def vg_sort_blocks_noalloc(dim, lo, hi, periodic, nblocks, pos, block_start, ord
     if stream is not None:
         st = stream if isinstance(stream, int) else stream.cuda_stream
     buf = ctypes.create_string_buffer(256)
-    code = load().vg_sort_blocks_noalloc(int(dim), lo.ctypes.data, hi.ctypes.data, per.ctypes.data,
-                                         nb.ctypes.data, int(pos.shape[0]), pos.data_ptr(),
+    code = load().vg_sort_blocks_noalloc(dim, lo.ctypes.data, hi.ctypes.data, per.ctypes.data,
+                                         nb.ctypes.data, n, pos.data_ptr(),
                                          block_start.data_ptr(), order.data_ptr(), st, buf, 256)
     if code != VG_OK:
         raise VgError(code, buf.value.decode())
@@ -349,6 +424,7 @@ def vg_mlp_last_error(m) -> str:
 
 def vg_destroy(ctx):
     if ctx:
+        _ctx_dim.pop(ctx.value if isinstance(ctx, ctypes.c_void_p) else ctx, None)
         load().vg_destroy(ctx)
 
 
