@@ -76,13 +76,31 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # three planes), a fan tetrahedron of the statistics (determinant, centroid,
 # vector area)
 FLOP_VTEST, FLOP_CAND, FLOP_NEWV, FLOP_FANTET = 6, 12, 51, 42
-# DRAM bytes (read + write) of one k_cells3<float,2,64> launch over the 1M
-# uniform cells from an ncu capture, or None while the kernel has changed
-# since its counters were taken.  The last capture (172.645 MB read, 289.882
-# MB written, profiles/k_cells3_fp32_uniform1m_ncu.md) predates the FP32
-# safeguards for cells far smaller than a block, so it is not reported.
-CELL_KERNEL_DRAM_BYTES_UNIFORM1M = None
+# Counters of the tier-0 FP32 cell kernel from one ncu capture of the
+# bench's own workload (profiles/), per workload: DRAM bytes (read + write)
+# of one launch, warp instructions per cell, active lanes per instruction,
+# issue-active fraction.  An entry is removed whenever the kernel changes
+# after its capture, so only counters of the timed build are reported.
+CELL_KERNEL_NCU = {}
 MLP_ALPHA, MLP_KMIN, MLP_KMAX = 1.5, 24.0, 1024.0
+# peak warp-instruction issue rate: 152 SMs x 4 schedulers x 1 per cycle x 2.07 GHz
+ISSUE_PEAK = 152 * 4 * 2.07e9
+# algorithmic bytes of the counting sort per particle (FP64 input): read the
+# position (24), the block-count atomic (4), write the FP32 offset + radius
+# (16) and the input index (4); plus 8 per block for the scan
+SORT_BYTES_PER_PARTICLE, SORT_BYTES_PER_BLOCK = 48, 8
+
+
+def hbm_peak():
+    """Measured copy bandwidth of the GB300s (GB/s) and its source."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback (6.8 TB/s)"
+
+
 PKG = os.path.join(ROOT, "paper_2209_11606_gb300")
 MLP_PARAMS = os.path.join(PKG, "mlp_params_gb300.json")
 TUNE_CACHE = os.path.join(PKG, "tuned_gb300.json")
@@ -100,6 +118,10 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the alternative FP32 forms")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 form")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 102.4M-point slabs record of the default run")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the comparison of the GPU outputs with the oracle's")
     ap.add_argument("--weinberg", action="store_true",
                     help="also time the cells with Weinberg codes (Sec. 4), eager calls")
     return ap.parse_args()
@@ -269,6 +291,72 @@ def batched_run(V, torch, stream, flush, mlp, steps: int = 5, seed: int = 5):
         V.vg_destroy(ctx)
 
 
+def large_run(V, torch, stream, flush, mlp, steps: int = 2, with_oracle: bool = True):
+    """The 102.4M-point slabs (perturbed FCC and uniform): the chosen form as
+    graph replays (sort, learned preload targets, cells, faces) against the
+    plain FP64 form (eager insert + compute, CUDA events on the stream), the
+    learned preload's fallback rate, and 2000 sampled cells against the
+    oracle."""
+    s, grid, _, _ = workload("slabs102m", 0)
+    n = s.n
+    pos_d = torch.from_numpy(s.pos).cuda()
+    ctx = V.vg_create(3, s.lo, s.hi, s.periodic, grid, stream=stream)
+    try:
+        V.vg_set_predictor(ctx, mlp, MLP_ALPHA, MLP_KMIN, MLP_KMAX)
+        cfg = V.vg_config_default()
+        cfg.precision, cfg.order, cfg.use_mlp, cfg.time_kernels = V.VG_FP32_RETEST, V.VG_PREFETCH, 1, 1
+        V.vg_graph_capture(ctx, [n], pos_d, None, cfg)
+        V.vg_graph_launch(ctx)
+        V.vg_graph_sync(ctx)
+        V.vg_get_kernel_ms(ctx)
+        V.vg_get_sort_ms(ctx)
+        ms = graph_steps(V, torch, ctx, stream, flush, steps)
+        kern_ms, kern_n = V.vg_get_kernel_ms(ctx)
+        sort_ms, sort_n = V.vg_get_sort_ms(ctx)
+        chosen = n * steps / (sum(ms) / 1000.0)
+        got = V._fetch(ctx, n, 3, False) if with_oracle else None
+        # the learned preload's fallbacks (work counters of an eager compute)
+        c = V.vg_config_default()
+        c.precision, c.order, c.use_mlp, c.collect_stats = V.VG_FP32_RETEST, V.VG_PREFETCH, 1, 1
+        V.vg_insert(ctx, pos_d)
+        V.vg_compute(ctx, c)
+        fb = np.zeros(n, np.uint8)
+        pref = np.zeros(n, np.int32)
+        V.vg_get_work(ctx, fallback=fb, n_prefetch=pref)
+        # the plain FP64 form: sort + cells + faces, eager
+        c64 = V.vg_config_default()
+        c64.precision, c64.order = V.VG_FP64, V.VG_WALK
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        flush.fill_(1)
+        e0.record(stream)
+        V.vg_insert(ctx, pos_d)
+        V.vg_compute(ctx, c64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain = n / (e0.elapsed_time(e1) / 1000.0)
+        rec = {"workload": WORKLOADS["slabs102m"], "cells_per_step": n, "steps": steps,
+               "value": chosen, "unit": "cells/s", "ms_per_step": sum(ms) / steps,
+               "cell_kernel_ms": kern_ms / max(kern_n, 1), "sort_ms": sort_ms / max(sort_n, 1),
+               "plain_fp64": {"value": plain, "unit": "cells/s",
+                              "form": "FP64 everywhere, block walk, eager insert + compute"},
+               "chosen_vs_plain": chosen / plain,
+               "learned_preload": {"fallback_rate": float(fb.mean()), "preload_per_cell": float(pref.mean())},
+               "form": "FP32 cuts + FP64 re-test, learned distance-sorted preload, graph replays"}
+        if with_oracle:
+            import oracle
+            rng = np.random.default_rng(7)
+            cells = np.sort(rng.choice(n, size=2000, replace=False))
+            ref = oracle.compute(s.pos, s.lo, s.hi, s.periodic, nblocks=V.vg_get_grid(ctx, 3), cells=cells,
+                                 threads=os.cpu_count() or 1)
+            rec["accuracy"] = accuracy(got, ref, cells, 1e-5)
+        return rec
+    finally:
+        V.vg_destroy(ctx)
+        del pos_d
+        torch.cuda.empty_cache()
+
+
 def weinberg_run(V, torch, ctx, pos_d, rad_d, cfg, n, reps: int = 3):
     """Cells with and without Weinberg codes (Sec. 4): eager insert + compute,
     host clock around synchronised calls."""
@@ -306,13 +394,28 @@ def cpu_baseline(s, grid, cells: int, seed: int = 0, clip: float = 0.0):
     if grid is None:
         grid = oracle.grid_size(s.n, s.lo, s.hi, 4.6 if s.dim == 3 else 3.4)
     t0 = time.perf_counter()
-    oracle.compute(s.pos, s.lo, s.hi, s.periodic, radii=s.radii, method="grid", nblocks=grid, cells=sample,
-                   threads=threads, clip=clip)
+    ref = oracle.compute(s.pos, s.lo, s.hi, s.periodic, radii=s.radii, method="grid", nblocks=grid,
+                         cells=sample, threads=threads, clip=clip)
     dt = time.perf_counter() - t0
     return {"value": len(sample) / dt, "unit": "cells/s", "cores": threads, "kind": "oracle",
             "sample": f"{len(sample)} random cells of the {s.n}-point workload (FP64 block-grid "
                       f"walk with the radius bound, OpenMP dynamic over cells)",
-            "seconds": dt}
+            "seconds": dt, "cells": sample, "result": ref}
+
+
+def accuracy(got, ref, cells, rtol):
+    """Errors of the GPU outputs against the oracle's on the same cells (the
+    parity tests' comparison): topology mismatches and the max / rms
+    relative error of volume, area and centroid."""
+    from tests.compare import compare
+    rep = compare(got, ref, rtol, cells=cells)
+    topo = (rep["status_mismatch"] + rep["nv_mismatch"] + rep["ne_mismatch"] + rep["nf_mismatch"] +
+            rep["face_mismatch"])
+    return {"cells": int(len(cells)), "topology_mismatches": int(topo),
+            "vol_max_rel": rep["vol_max_rel"], "vol_rms_rel": rep["vol_rms_rel"],
+            "area_max_rel": rep["area_max_rel"], "area_rms_rel": rep["area_rms_rel"],
+            "centroid_max_rel": rep["centroid_max_rel"], "centroid_rms_rel": rep["centroid_rms_rel"],
+            "bar": rtol, "within_bar": bool(rep["topology_ok"] and rep["values_ok"])}
 
 
 def run_reference(args, rank, world):
@@ -408,6 +511,7 @@ def main():
     clk = clocks.stop()
     launches = V.vg_get_launches(ctx) - l0
     kern_ms, kern_n = V.vg_get_kernel_ms(ctx)
+    sort_ms, sort_n = V.vg_get_sort_ms(ctx)
     t_total = sum(step_ms) / 1000.0
     if dist:
         t = torch.tensor([t_total], device="cuda")
@@ -450,12 +554,40 @@ def main():
     achieved = flop / (kern_avg_ms / 1000.0) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP32_PEAK_TFLOPS,
-            "traffic": CELL_KERNEL_DRAM_BYTES_UNIFORM1M if args.workload == "uniform1m" else None,
+            "traffic": None,
             "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
             "kernel": ("k_cells3<float,2,64>" if dim == 3 else "k_cells2<float,8,32>") + " (cell kernel phase, all tiers)",
             "kernel_ms": kern_avg_ms,
             "flop_per_cell": flop / n,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    # the counting sort against HBM bandwidth: its algorithmic bytes (input
+    # positions, block counts, sorted offsets and ids, the scan) over its
+    # device time inside the replays
+    peak_gbs, peak_src = hbm_peak()
+    sort_avg_ms = sort_ms / max(sort_n, 1)
+    grid_used = V.vg_get_grid(ctx, dim)
+    sort_bytes = SORT_BYTES_PER_PARTICLE * n + SORT_BYTES_PER_BLOCK * int(np.prod(grid_used))
+    sort_gbs = sort_bytes / (sort_avg_ms / 1000.0) / 1e9 if sort_avg_ms > 0 else None
+    roof["sort"] = {"bound": "hbm", "ms": sort_avg_ms, "bytes_per_launch": sort_bytes,
+                    "achieved": sort_gbs, "peak": peak_gbs, "unit": "GB/s",
+                    "frac": None if sort_gbs is None else sort_gbs / peak_gbs,
+                    "peak_source": peak_src,
+                    "kernels": "widen (FP32 input), rmax (radical), k_index, scans, k_scatter, k_finalize, "
+                               "k_predict (learned preload)"}
+    roof["work_per_cell"] = {"candidates_tested": float(w["t"].mean()), "vertex_tests": float(w["v"].mean()),
+                             "cuts": float(w["c"].mean()), "new_vertices": float(w["nv"].mean()),
+                             "fp64_retests": float(w["r"].mean())}
+    if CELL_KERNEL_NCU.get(args.workload):
+        prof = CELL_KERNEL_NCU[args.workload]
+        ipc = prof["warp_inst_per_cell"]
+        roof["traffic"] = prof["dram_bytes"]
+        roof["issue"] = {"warp_inst_per_cell": ipc,
+                         "achieved_inst_per_s": ipc * n / (kern_avg_ms / 1000.0),
+                         "peak_inst_per_s": ISSUE_PEAK,
+                         "frac": ipc * n / (kern_avg_ms / 1000.0) / ISSUE_PEAK,
+                         "lanes_active_per_inst": prof["lanes_per_inst"],
+                         "issue_active_ncu": prof["issue_active"],
+                         "source": prof["source"]}
     learned = None
     if learned_on:
         c_fixed = V.vg_config_default()
@@ -537,10 +669,23 @@ def main():
     if not args.no_batched and args.workload == "uniform1m":
         line["batched"] = batched_run(V, torch, stream, flush, mlp)
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = {k: v for k, v in
-                                cpu_baseline(s, grid, n if args.workload == "uniform1m" else 100_000,
-                                             clip=clip).items()
-                                if k != "seconds"}
+        cb = cpu_baseline(s, grid, n if args.workload == "uniform1m" else 100_000, clip=clip)
+        line["cpu_baseline"] = {k: v for k, v in cb.items() if k not in ("seconds", "cells", "result")}
+        if not args.no_accuracy:
+            # every output of the chosen form and of the plain FP64 form against
+            # the oracle, on the cells the CPU baseline computed
+            acc = {}
+            for name, c2, rtol in (("chosen", cfg, 1e-5), ("plain_fp64", None, 1e-12)):
+                if c2 is None:
+                    c2 = V.vg_config_default()
+                    c2.precision, c2.order, c2.clip = V.VG_FP64, V.VG_WALK, clip
+                V.vg_insert(ctx, pos_d, rad_d)
+                V.vg_compute(ctx, c2)
+                got = V._fetch(ctx, n, dim, False)
+                acc[name] = accuracy(got, cb["result"], cb["cells"], rtol)
+            line["accuracy"] = acc
+    if not args.no_large and args.workload == "uniform1m" and world == 1:
+        line["large"] = large_run(V, torch, stream, flush, mlp, with_oracle=not args.no_cpu_baseline)
     V.vg_destroy(ctx)
     V.vg_mlp_destroy(mlp)
     print(json.dumps(line), flush=True)

@@ -23,21 +23,28 @@ def compare(got, ref, rtol, cells=None):
     for k in ("nv", "ne", "nf"):
         rep[k + "_mismatch"] = int((got[k][idx][ok] != ref[k][ok]).sum())
     d = ref["centroid"].shape[1]
-    # faces per cell
-    bad_faces = 0
-    for j, i in enumerate(idx):
-        if not ok[j]:
-            continue
-        a, b = ref["face_off"][j], ref["face_off"][j + 1]
-        ga, gb = got["face_off"][i], got["face_off"][i + 1]
-        if (b - a) != (gb - ga):
-            bad_faces += 1
-            continue
-        if not (np.array_equal(ref["nbr_id"][a:b], got["nbr_id"][ga:gb])
-                and np.array_equal(np.asarray(ref["nbr_img"][a:b])[:, :d],
-                                   np.asarray(got["nbr_img"][ga:gb])[:, :d])
-                and np.array_equal(ref["face_order"][a:b], got["face_order"][ga:gb])):
-            bad_faces += 1
+    # faces per cell, compared for all cells at once: cells whose face counts
+    # agree are compared face by face through index arrays
+    fo_r = np.asarray(ref["face_off"], dtype=np.int64)
+    fo_g = np.asarray(got["face_off"], dtype=np.int64)
+    cnt_r = np.diff(fo_r)
+    cnt_g = (fo_g[1:] - fo_g[:-1])[idx]
+    same = ok & (cnt_r == cnt_g)
+    bad_faces = int((ok & (cnt_r != cnt_g)).sum())
+    sel = np.nonzero(same)[0]
+    c = cnt_r[sel]
+    tot = int(c.sum())
+    if tot:
+        cell = np.repeat(np.arange(len(sel)), c)
+        within = np.arange(tot) - np.repeat(np.cumsum(c) - c, c)
+        fr = fo_r[sel][cell] + within
+        fg = fo_g[idx[sel]][cell] + within
+        img_r = np.asarray(ref["nbr_img"])[:, :d]
+        img_g = np.asarray(got["nbr_img"])[:, :d]
+        diff = ((np.asarray(ref["nbr_id"])[fr] != np.asarray(got["nbr_id"])[fg]) |
+                np.any(img_r[fr] != img_g[fg], axis=1) |
+                (np.asarray(ref["face_order"])[fr] != np.asarray(got["face_order"])[fg]))
+        bad_faces += int(len(np.unique(cell[diff])))
     rep["face_mismatch"] = bad_faces
     vr = ref["vol"][ok]
     vg = got["vol"][idx][ok]
@@ -50,9 +57,11 @@ def compare(got, ref, rtol, cells=None):
     ascale = np.maximum(np.abs(ar), 1e-3 * R ** (d - 1))
     arel = np.abs(got["area"][idx][ok] - ar) / np.maximum(ascale, 1e-300)
     rep["area_max_rel"] = float(arel.max()) if arel.size else 0.0
+    rep["area_rms_rel"] = float(np.sqrt(np.mean(arel ** 2))) if arel.size else 0.0
     size = np.maximum(vscale, 1e-300) ** (1.0 / d)
     cd = np.linalg.norm(got["centroid"][idx][ok] - ref["centroid"][ok], axis=1) / size
     rep["centroid_max_rel"] = float(cd.max()) if cd.size else 0.0
+    rep["centroid_rms_rel"] = float(np.sqrt(np.mean(cd ** 2))) if cd.size else 0.0
     rep["topology_ok"] = (rep["status_mismatch"] == 0 and rep["nv_mismatch"] == 0 and
                           rep["ne_mismatch"] == 0 and rep["nf_mismatch"] == 0 and bad_faces == 0)
     rep["values_ok"] = (rep["vol_max_rel"] <= rtol and rep["area_max_rel"] <= rtol and
