@@ -14,6 +14,10 @@ namespace vg {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Blocks of up to this many particles are ordered inside by a scan over the
+// block; larger ones by an in-place sort of their ids (sort_big_blocks).
+constexpr int VG_SMALL_BLOCK = 64;
+
 // Kernels launched by this host thread (every launch site increments it).
 extern thread_local long long g_launch_count;
 
@@ -161,6 +165,11 @@ cudaError_t sort_particles(const Sys *sys, int nsys, int dim, long long total_bl
                            int *bstart, int *tmp_id, float4 *p32, D4 *p64, int *sid, int *sblk,
                            int *ssys, int *errflags, void *scan_tmp, cudaStream_t st);
 cudaError_t system_rmax(Sys *sys, int nsys, long long n, const double *radii, cudaStream_t st);
+// In-place ascending sort of the particle ids of every block holding more
+// than VG_SMALL_BLOCK particles (scratch: n ints; list: nblk ints; *nlist 0
+// on entry).
+cudaError_t sort_big_blocks(const int *bstart, long long nblk, int *ids, int *scratch, int *list, int *nlist,
+                            int grid, cudaStream_t st);
 // FP32 input widened to FP64 (n values), the form every sort kernel reads.
 cudaError_t widen_f32(const float *in, double *out, long long n, cudaStream_t st);
 size_t scan_tmp_bytes_i32(long long n);

@@ -101,7 +101,8 @@ __global__ void na_scatter(long long n, const int *__restrict__ key, const int *
     if (i < n) tmp[start[key[i]] + slot[i]] = (int)i;
 }
 
-// inside each block, order the particles by input index
+// inside each block, order the particles by input index: a scan over a
+// small block, the position in a large one (sorted in place before)
 __global__ void na_order(long long n, const int *__restrict__ key, const int *__restrict__ start,
                          const int *__restrict__ tmp, int *__restrict__ order) {
     long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -109,7 +110,9 @@ __global__ void na_order(long long n, const int *__restrict__ key, const int *__
     int i = tmp[u];
     int k = key[i];
     int b0 = start[k], b1 = start[k + 1], rank = 0;
-    for (int v = b0; v < b1; v++) rank += tmp[v] < i;
+    if (b1 - b0 > VG_SMALL_BLOCK) rank = (int)(u - b0);
+    else
+        for (int v = b0; v < b1; v++) rank += tmp[v] < i;
     order[b0 + rank] = i;
 }
 
@@ -191,6 +194,9 @@ extern "C" vg_status vg_sort_blocks_noalloc(int dim, const double *lo, const dou
         na_index<<<nb, T, 0, st>>>(g, n, pos, key, slot, count, err);
         na_scan<<<1, NA_SCAN_THREADS, 0, st>>>(count, block_start, g.nblk);
         na_scatter<<<nb, T, 0, st>>>(n, key, slot, block_start, tmp);
+        // large blocks sorted in place: the slots serve as scratch, the block
+        // counts (read by the scan already) as the list, err[2] as its length
+        sort_big_blocks(block_start, g.nblk, tmp, slot, count, err + 2, 304, st);
         na_order<<<nb, T, 0, st>>>(n, key, block_start, tmp, order);
     } else {
         na_scan<<<1, NA_SCAN_THREADS, 0, st>>>(count, block_start, g.nblk);

@@ -94,6 +94,9 @@ __global__ void k_scatter(long long n, const int *__restrict__ key, const int *_
 }
 
 // Step 4: rank inside the block by input index and write the sorted store.
+// A block of up to VG_SMALL_BLOCK particles is ranked by a scan over its
+// entries; a larger one has been sorted in place by sort_big_blocks, so a
+// particle's rank is its position.
 __global__ void k_finalize(const Sys *__restrict__ sys, int nsys, int dim, long long n,
                            const int *__restrict__ key, const int *__restrict__ bstart,
                            const int *__restrict__ tmp_id, const double *__restrict__ pos,
@@ -106,7 +109,9 @@ __global__ void k_finalize(const Sys *__restrict__ sys, int nsys, int dim, long 
     const int k = key[i];
     const int b0 = bstart[k], b1 = bstart[k + 1];
     int rank = 0;
-    for (int v = b0; v < b1; v++) rank += tmp_id[v] < i;
+    if (b1 - b0 > VG_SMALL_BLOCK) rank = (int)(u - b0);
+    else
+        for (int v = b0; v < b1; v++) rank += tmp_id[v] < i;
     const int dst = b0 + rank;
     const int sidx = nsys > 1 ? system_of(sys, nsys, i) : 0;
     const Grid &g = sys[sidx].g;
@@ -131,6 +136,131 @@ __global__ void k_finalize(const Sys *__restrict__ sys, int nsys, int dim, long 
     sid[dst] = i;
     sblk[dst] = k;
     ssys[dst] = sidx;
+}
+
+// ---- in-place sort of the particle ids of large blocks ----------------------
+
+constexpr int BIG_THREADS = 512;
+constexpr int BIG_SMEM = 4096;  // ids sorted in shared memory up to this count
+constexpr int RADIX_BITS = 4;
+constexpr int RADIX = 1 << RADIX_BITS;
+
+// The blocks that hold more than VG_SMALL_BLOCK particles.
+__global__ void k_list_big(const int *__restrict__ bstart, long long nblk, int *__restrict__ list,
+                           int *__restrict__ nlist) {
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k < nblk && bstart[k + 1] - bstart[k] > VG_SMALL_BLOCK) list[atomicAdd(nlist, 1)] = (int)k;
+}
+
+// Exclusive scan of RADIX * BIG_THREADS counters in shared memory (digit-major
+// order), each thread scanning RADIX consecutive entries.
+__device__ void cta_scan_counts(int *cnt, int *part) {
+    const int t = threadIdx.x;
+    int loc[RADIX], sum = 0;
+#pragma unroll
+    for (int d = 0; d < RADIX; d++) {
+        loc[d] = sum;
+        sum += cnt[t * RADIX + d];
+    }
+    part[t] = sum;
+    __syncthreads();
+    for (int off = 1; off < BIG_THREADS; off <<= 1) {
+        const int v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    const int base = part[t] - sum;
+#pragma unroll
+    for (int d = 0; d < RADIX; d++) cnt[t * RADIX + d] = base + loc[d];
+    __syncthreads();
+}
+
+// Sorts the ids of every listed block ascending, in place (a block's ids
+// are distinct input indices).  Up to BIG_SMEM ids: a bitonic sort in shared
+// memory.  Beyond: an LSD radix sort of (id - min) in digits of RADIX_BITS,
+// each thread taking a contiguous chunk so that every pass is stable,
+// ping-ponging between the block's range in `ids` and the same range in
+// `scratch`.
+__global__ void __launch_bounds__(BIG_THREADS) k_sort_big(const int *__restrict__ bstart, const int *__restrict__ list,
+                                                         const int *__restrict__ nlist, int *__restrict__ ids,
+                                                         int *__restrict__ scratch) {
+    __shared__ int sm[RADIX * BIG_THREADS];  // 32 KB: bitonic keys or digit counters
+    __shared__ int part[BIG_THREADS];
+    __shared__ int red[2];
+    const int t = threadIdx.x;
+    const int nl = *nlist;
+    for (int e = blockIdx.x; e < nl; e += gridDim.x) {
+        const int k = list[e];
+        const int b0 = bstart[k], sz = bstart[k + 1] - b0;
+        if (sz <= BIG_SMEM) {
+            int P = 1;
+            while (P < sz) P <<= 1;
+            for (int x = t; x < P; x += BIG_THREADS) sm[x] = x < sz ? ids[b0 + x] : 0x7fffffff;
+            __syncthreads();
+            for (int kk = 2; kk <= P; kk <<= 1) {
+                for (int j = kk >> 1; j > 0; j >>= 1) {
+                    for (int x = t; x < P; x += BIG_THREADS) {
+                        const int y = x ^ j;
+                        if (y > x) {
+                            const int a = sm[x], b = sm[y];
+                            if ((a > b) == ((x & kk) == 0)) { sm[x] = b; sm[y] = a; }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (int x = t; x < sz; x += BIG_THREADS) ids[b0 + x] = sm[x];
+            __syncthreads();
+            continue;
+        }
+        // range of the ids: the passes cover the bits of (max - min)
+        if (t == 0) { red[0] = 0x7fffffff; red[1] = 0; }
+        __syncthreads();
+        int mn = 0x7fffffff, mx = 0;
+        for (int x = t; x < sz; x += BIG_THREADS) {
+            const int v = ids[b0 + x];
+            mn = min(mn, v);
+            mx = max(mx, v);
+        }
+        atomicMin(&red[0], mn);
+        atomicMax(&red[1], mx);
+        __syncthreads();
+        mn = red[0];
+        const unsigned span = (unsigned)(red[1] - mn);
+        const int bits = span ? 32 - __clz(span) : 0;
+        const int passes = (bits + RADIX_BITS - 1) / RADIX_BITS;
+        const int chunk = (sz + BIG_THREADS - 1) / BIG_THREADS;
+        const int c0 = min(sz, t * chunk), c1 = min(sz, c0 + chunk);
+        int *src = ids + b0, *dst = scratch + b0;
+        for (int p = 0; p < passes; p++) {
+            const int shift = p * RADIX_BITS;
+            int h[RADIX];
+#pragma unroll
+            for (int d = 0; d < RADIX; d++) h[d] = 0;
+            for (int x = c0; x < c1; x++) {
+                const int d = (int)(((unsigned)(src[x] - mn) >> shift) & (RADIX - 1));
+#pragma unroll
+                for (int dd = 0; dd < RADIX; dd++) h[dd] += d == dd;
+            }
+            // digit-major: counter (d, t) at d * BIG_THREADS + t, scanned in
+            // that order, so equal digits keep the threads' (input) order
+#pragma unroll
+            for (int d = 0; d < RADIX; d++) sm[d * BIG_THREADS + t] = h[d];
+            __syncthreads();
+            cta_scan_counts(sm, part);
+            for (int x = c0; x < c1; x++) {
+                const int v = src[x];
+                const int d = (int)(((unsigned)(v - mn) >> shift) & (RADIX - 1));
+                dst[sm[d * BIG_THREADS + t]++] = v;
+            }
+            __syncthreads();
+            int *tmp = src; src = dst; dst = tmp;
+        }
+        if (src != ids + b0)
+            for (int x = t; x < sz; x += BIG_THREADS) ids[b0 + x] = src[x];
+        __syncthreads();
+    }
 }
 
 // ---- exclusive scan: tiles, recursive tile sums, add back ------------------
@@ -258,6 +388,19 @@ cudaError_t widen_f32(const float *in, double *out, long long n, cudaStream_t st
     return cudaGetLastError();
 }
 
+// Blocks of more than VG_SMALL_BLOCK particles get their ids sorted in place
+// (ids: the scattered ids, block_start the block CSR; scratch: n ints;
+// list: room for nblk ints; *nlist must be 0 on entry).
+cudaError_t sort_big_blocks(const int *bstart, long long nblk, int *ids, int *scratch, int *list, int *nlist,
+                            int grid, cudaStream_t st) {
+    if (nblk <= 0) return cudaSuccess;
+    ++g_launch_count;
+    k_list_big<<<(unsigned)((nblk + 255) / 256), 256, 0, st>>>(bstart, nblk, list, nlist);
+    ++g_launch_count;
+    k_sort_big<<<grid, BIG_THREADS, 0, st>>>(bstart, list, nlist, ids, scratch);
+    return cudaGetLastError();
+}
+
 cudaError_t system_rmax(Sys *sys, int nsys, long long n, const double *radii, cudaStream_t st) {
     if (n <= 0 || !radii) return cudaSuccess;
     ++g_launch_count;
@@ -272,6 +415,7 @@ cudaError_t sort_particles(const Sys *sys, int nsys, int dim, long long total_bl
     cudaError_t e;
     if ((e = cudaMemsetAsync(count, 0, sizeof(int) * total_blk, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(errflags, 0, sizeof(int) * 2, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(errflags + 3, 0, sizeof(int), st)) != cudaSuccess) return e;
     const int T = 256;
     const unsigned nbk = (unsigned)((n + T - 1) / T);
     if (n > 0) { ++g_launch_count; k_index<<<nbk, T, 0, st>>>(sys, nsys, dim, n, pos, radii, key, slot, count, errflags); }
@@ -281,6 +425,10 @@ cudaError_t sort_particles(const Sys *sys, int nsys, int dim, long long total_bl
     if (n > 0) {
         ++g_launch_count;
         k_scatter<<<nbk, T, 0, st>>>(n, key, slot, bstart, tmp_id);
+        // large blocks: ids sorted in place (slots are free now; the block
+        // counts, read by the scan, hold the list of large blocks)
+        if ((e = sort_big_blocks(bstart, total_blk, tmp_id, slot, count, errflags + 3, 304, st)) != cudaSuccess)
+            return e;
         ++g_launch_count;
         k_finalize<<<nbk, T, 0, st>>>(sys, nsys, dim, n, key, bstart, tmp_id, pos, radii, p32, p64, sid, sblk, ssys);
     }

@@ -138,6 +138,9 @@ SORT_CASES = {
     "clustered": (lambda: W.extreme_clustering(50_000, 3, seed=24), (37, 37, 37)),
     "blobs": (lambda: W.blobs(40_000, 10.0, seed=25), (20, 20, 20)),
     "big_block": (_cluster_big_block, (10, 10, 10)),
+    # blocks of every size class: a scan below 65 particles, a shared-memory
+    # sort up to 4096, a radix sort beyond (5000 in the central blocks)
+    "extreme_1m": (lambda: W.extreme_clustering(1_000_000, 3, seed=28), (50, 50, 50)),
     "2d_walled": (lambda: W.uniform(50_000, 2, 1.0, False, seed=26), (121, 97)),
     "2d_periodic": (lambda: W.uniform(50_000, 2, 3.0, True, seed=27), (130, 130)),
 }
