@@ -214,6 +214,7 @@ vg_status new_context(vg_ctx **made, int dim, void *stream) {
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_ticket, sizeof(unsigned) * 4);
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_capcount, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_capcount2, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_capcount0, sizeof(int));
     if (e != cudaSuccess) {
         cudaGetLastError();
         vg_destroy(c);
@@ -271,6 +272,7 @@ vg_status prepare_insert(vg_ctx *c, const std::vector<long long> &counts, const 
     VG_CUDA(ensure(c, c->d_face_off, n + 1));
     VG_CUDA(ensure(c, c->d_caplist, n));
     VG_CUDA(ensure(c, c->d_caplist2, n));
+    VG_CUDA(ensure(c, c->d_caplist0, n));
     VG_CUDA(ensure(c, c->d_w_tested, n));
     VG_CUDA(ensure(c, c->d_w_vtests, n));
     VG_CUDA(ensure(c, c->d_w_cuts, n));
@@ -426,6 +428,7 @@ cudaError_t enqueue_cells(vg_ctx *c, const vg_config &cfg, cudaStream_t s, const
     o.w_pref = c->d_w_pref;
     o.retry = c->d_caplist; o.retry_count = c->d_capcount;
     o.retry2 = c->d_caplist2; o.retry2_count = c->d_capcount2;
+    o.retry0 = c->d_caplist0; o.retry0_count = c->d_capcount0;
     o.topo = cfg.weinberg ? c->d_topo : nullptr;
     o.topo_n = cfg.weinberg ? c->d_topo_n : nullptr;
     cudaError_t e;
@@ -433,10 +436,23 @@ cudaError_t enqueue_cells(vg_ctx *c, const vg_config &cfg, cudaStream_t s, const
     if ((e = cudaMemsetAsync(c->d_fcount, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->d_capcount, 0, sizeof(int), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->d_capcount2, 0, sizeof(int), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_capcount0, 0, sizeof(int), s)) != cudaSuccess) return e;
     auto launch = c->dim == 3 ? launch_cells3 : launch_cells2;
     const int nc = subset ? nsubset : (int)c->n;
-    if ((e = launch(st, o, pp, off, cfg.precision, c->d_ticket, c->sm_count, cfg.warps_per_cta, subset, nc, 0, s)))
+    // 3D FP32 prefetch: the hot kernel over every cell, then the general one
+    // over the cells it deferred (walk after the preload, FP64 statistics)
+    const bool hot = c->dim == 3 && cfg.precision == VG_FP32_RETEST && cfg.order == VG_PREFETCH && !cfg.weinberg &&
+                     c->n < (1 << 27);
+    if (hot) {
+        if ((e = launch_cells3_hot(st, o, pp, off, c->d_ticket, c->sm_count, cfg.warps_per_cta, subset, nc, s)))
+            return e;
+        if ((e = launch(st, o, pp, off, cfg.precision, c->d_ticket + 3, c->sm_count, cfg.warps_per_cta, c->d_caplist0,
+                        0, 3, s)))
+            return e;
+    } else if ((e = launch(st, o, pp, off, cfg.precision, c->d_ticket, c->sm_count, cfg.warps_per_cta, subset, nc, 0,
+                           s))) {
         return e;
+    }
     if ((e = launch(st, o, pp, off, cfg.precision, c->d_ticket + 1, c->sm_count, 0, c->d_caplist, 0, 1, s))) return e;
     return launch(st, o, pp, off, cfg.precision, c->d_ticket + 2, c->sm_count, 0, c->d_caplist2, 0, 2, s);
 }
@@ -1012,7 +1028,7 @@ void vg_destroy(vg_ctx *c) {
     release(c->d_ticket); release(c->d_face_off); release(c->d_nbr); release(c->d_img); release(c->d_ford);
     release(c->d_w_tested); release(c->d_w_vtests); release(c->d_w_cuts); release(c->d_w_retest);
     release(c->d_w_fallback); release(c->d_caplist); release(c->d_capcount);
-    release(c->d_caplist2); release(c->d_capcount2);
+    release(c->d_caplist2); release(c->d_capcount2); release(c->d_caplist0); release(c->d_capcount0);
     release(c->d_off_code); release(c->d_off_lb); release(c->d_kblock); release(c->d_w_newv);
     release(c->d_w_pref); release(c->d_rfin);
     release(c->d_topo); release(c->d_topo_n); release(c->d_wlen); release(c->d_wsym); release(c->d_whash);

@@ -524,7 +524,14 @@ __device__ __forceinline__ bool resolve(const Grid &g, long long base, const int
 
 // ---- the kernel ------------------------------------------------------------------
 
-template <typename T, int VPL, int MAXP, bool BATCH, int G, bool TOPO = false>
+// HOT: the common path only (FP32, prefetch, tier 0).  A cell that needs
+// anything else -- the walk after its preload, FP64 vertices for its
+// statistics (degenerate, ill-conditioned or thin cells) -- is handed on
+// whole, through the deferred list, to the general kernel (tier 3), which
+// computes it from the start.  The hot kernel's code then holds neither the
+// walk nor the FP64 statistics, which keeps it small in the instruction
+// cache.
+template <typename T, int VPL, int MAXP, bool BATCH, int G, bool TOPO = false, bool HOT = false>
 __global__ void VG_BOUNDS
     k_cells3(const __grid_constant__ Store st, const __grid_constant__ Out o,
              const __grid_constant__ Params pp, const __grid_constant__ Offsets off, unsigned *ticket,
@@ -547,7 +554,11 @@ __global__ void VG_BOUNDS
     __syncwarp(gmask);
     const Sys &SY = sys_ref<BATCH>(st, S.sysc);
     const Grid &g = SY.g;
-    const int total = cells ? (tier == 1 ? *o.retry_count : (tier == 2 ? *o.retry2_count : ncells)) : st.n;
+    // tier 0 takes all cells (or a caller's subset), tier 3 the cells the hot
+    // kernel deferred, tiers 1 and 2 the cells the tier below handed on
+    const int total = cells ? (tier == 1 ? *o.retry_count
+                                         : (tier == 2 ? *o.retry2_count : (tier == 3 ? *o.retry0_count : ncells)))
+                            : st.n;
     const int chunk = pp.chunk > 0 ? pp.chunk : 1;
     // FP32 band factor, converted once (FP64 work is scarce on this part)
     const float tol32f = (float)pp.tol32;
@@ -717,13 +728,18 @@ __global__ void VG_BOUNDS
             // that covers the rounding of R and of candidate distances
             // FP32: the inputs' absolute error eabs moves |q| and R by about
             // eabs and the vertices by kappa eabs; 64 eabs R covers a small cell
+            // (FP32: approximate roots, a few ulps against the 1e-4 margin)
+            auto root = [](T x) -> T {
+                if constexpr (F32) return sqrt_a(x);
+                else return sqrt(x);
+            };
             auto stop2 = [&]() -> T {
                 const T margin = F32 ? (T)1.0001 : (T)(1.0 + 1e-12);
                 const T ea = F32 ? (T)(64.f * eabs) : (T)0;
-                if (!st.radical) return (T)4 * r2 * margin + ea * sqrt(r2);
+                if (!st.radical) return (T)4 * r2 * margin + ea * root(r2);
                 T disc = r2 + (T)(S.cc.rmax * S.cc.rmax) - (T)(S.cc.rp * S.cc.rp);
                 if (disc <= (T)0) return (T)0;
-                T rs = sqrt(r2) + sqrt(disc);
+                T rs = root(r2) + root(disc);
                 return rs * rs * margin + ea * rs;
             };
 
@@ -948,6 +964,10 @@ __global__ void VG_BOUNDS
                         if (pp.collect && gl == 0) S.cnt[5] = count;
                         src.rho2 = rho2;
                         src.rg[0] = rg0; src.rg[1] = rg1; src.rg[2] = rg2;
+                    } else if constexpr (HOT) {
+                        // no preload list: the general kernel walks this cell
+                        src.mode = 3;
+                        flags |= 32;
                     }
                     __syncwarp(gmask);
                 }
@@ -963,8 +983,16 @@ __global__ void VG_BOUNDS
                     if (mode == 0) {
                         const int u = src.u, count = src.count;
                         if (u >= count) {
-                            if ((T)stop <= (T)src.rho2 * (T)0.9999) src.mode = 3;
-                            else { src.mode = 1; src.fell_back = 1; }
+                            if ((T)stop <= (T)src.rho2 * (T)0.9999) {
+                                src.mode = 3;
+                            } else if constexpr (HOT) {
+                                // the bound reaches past the preload: deferred
+                                src.mode = 3;
+                                flags |= 32;
+                            } else {
+                                src.mode = 1;
+                                src.fell_back = 1;
+                            }
                             continue;
                         }
                         const int idx = u + gl;
@@ -1008,6 +1036,9 @@ __global__ void VG_BOUNDS
                         src.u = ((T)lb2 >= stop) ? count : u + G;
                         continue;
                     }
+                    if constexpr (HOT) {
+                        break;  // modes 1 and 2 (the walk) never occur here
+                    } else {
                     const int vp = src.vp, vtot = src.vtot;
                     if (vp < vtot) {
                         // a batch of the current window's particles
@@ -1155,6 +1186,7 @@ __global__ void VG_BOUNDS
                     src.vp = 0;
                     src.vtot = ltot;
                     __syncwarp(gmask);
+                    }  // !HOT
                 }
                 if (want == 0) break;
                 const int srcl = __ffs(want) - 1;
@@ -1470,6 +1502,18 @@ __global__ void VG_BOUNDS
                 const bool anyhk = __any_sync(gmask, hk);
                 degen = degen || anyhk;
             }
+            if constexpr (HOT) {
+                // FP64 statistics or the walk needed: the general kernel
+                // computes the cell (flags are warp-uniform)
+                if (degen || (flags & 32)) {
+                    if (gl == 0) {
+                        const int slot = atomicAdd(o.retry0_count, 1);
+                        o.retry0[slot] = i;
+                    }
+                    __syncwarp(gmask);
+                    continue;
+                }
+            }
             bool fail = flags & 2;
             int status = VG_CELL_OK;
             if (flags & 4) status = VG_CELL_EMPTY;
@@ -1509,7 +1553,7 @@ __global__ void VG_BOUNDS
                 // pass 0 sums the FP32 vertices; a cell thin against its
                 // distance from the particle gets a pass from FP64 vertices
                 for (int pass = 0; pass < 2; pass++) {
-                if (degen) {
+                if (!HOT && degen) {
                     // (vertices read back from the staging arrays: the loop stays rolled)
 #pragma unroll 1
                     for (int s = 0; s < VPL; s++) {
@@ -1526,7 +1570,7 @@ __global__ void VG_BOUNDS
                 }
                 __syncwarp(gmask);
                 double dref[3];
-                if (degen) { dref[0] = S.x.v.dpos[tref][0]; dref[1] = S.x.v.dpos[tref][1]; dref[2] = S.x.v.dpos[tref][2]; }
+                if (!HOT && degen) { dref[0] = S.x.v.dpos[tref][0]; dref[1] = S.x.v.dpos[tref][1]; dref[2] = S.x.v.dpos[tref][2]; }
                 else { dref[0] = (double)rx; dref[1] = (double)ry; dref[2] = (double)rz; }
                 int F = 0;
 #pragma unroll
@@ -1589,7 +1633,7 @@ __global__ void VG_BOUNDS
                         int order = 0;
                         bool keep = true;
                         T farea;
-                        if (!degen) {
+                        if (HOT || !degen) {
                             const T u0x = S.x.v.sx[t0] - rx, u0y = S.x.v.sy[t0] - ry, u0z = S.x.v.sz[t0] - rz;
                             T fv = 0, fcx = 0, fcy = 0, fcz = 0, fax = 0, fay = 0, faz = 0;
 #pragma unroll 1
@@ -1708,13 +1752,22 @@ __global__ void VG_BOUNDS
                     const float thick = (float)vol * rcp_a(2.f * (float)area);
                     const float scale = fmaxf(sqrt_a((float)r2), fmaxf(g.hf[0], fmaxf(g.hf[1], g.hf[2])));
                     if (!(thick * 10.f > scale)) {
+                        if constexpr (HOT) {
+                            // thin: FP64 statistics in the general kernel
+                            if (gl == 0) {
+                                const int slot = atomicAdd(o.retry0_count, 1);
+                                o.retry0[slot] = i;
+                            }
+                            __syncwarp(gmask);
+                            break;
+                        }
                         degen = true;
                         __syncwarp(gmask);
                         continue;
                     }
                 }
                 int nv;
-                if (degen) {
+                if (!HOT && degen) {
                     // distinct vertices: a vertex counts if no earlier one coincides
                     const double eps = pp.merge_rel * g.s, eps2 = eps * eps;
                     int cntv = 0;
@@ -1809,7 +1862,7 @@ __global__ void VG_BOUNDS
                 o.fptr[out_i] = 0;
             }
             if (fail && gl == 0) {
-                if (tier == 0) {
+                if (tier == 0 || tier == 3) {
                     const int slot = atomicAdd(o.retry_count, 1);
                     o.retry[slot] = i;
                 } else if (tier == 1) {
@@ -1835,11 +1888,11 @@ __global__ void VG_BOUNDS
     }
 }
 
-template <typename T, int VPL, int MAXP, bool BATCH, int G, bool TOPO = false>
+template <typename T, int VPL, int MAXP, bool BATCH, int G, bool TOPO = false, bool HOT = false>
 cudaError_t launch_t(const Store &s, const Out &o, const Params &p, const Offsets &off, unsigned *ticket,
                      int sm_count, int warps, const int *cells, int ncells, int tier, cudaStream_t st) {
     const size_t smem = sizeof(Smem<T, VPL, MAXP, G>) * warps * (32 / G);
-    auto kfn = k_cells3<T, VPL, MAXP, BATCH, G, TOPO>;
+    auto kfn = k_cells3<T, VPL, MAXP, BATCH, G, TOPO, HOT>;
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // shared memory before L1: the resident CTAs are bounded by it
@@ -1879,8 +1932,20 @@ cudaError_t launch_cells3(const Store &s, const Out &o, const Params &p, const O
     if (o.topo)  // the cells' triangles are kept for Weinberg codes (FP32 form, tier 0)
         return batch ? launch_t<float, VG_T0_VPL, 64, true, VG_T0_G, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st)
                      : launch_t<float, VG_T0_VPL, 64, false, VG_T0_G, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
-    return batch ? launch_t<float, VG_T0_VPL, 64, true, VG_T0_G>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st)
-                 : launch_t<float, VG_T0_VPL, 64, false, VG_T0_G>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
+    return batch ? launch_t<float, VG_T0_VPL, 64, true, VG_T0_G>(s, o, p, off, ticket, sm_count, w, cells, ncells, tier, st)
+                 : launch_t<float, VG_T0_VPL, 64, false, VG_T0_G>(s, o, p, off, ticket, sm_count, w, cells, ncells, tier, st);
+}
+
+// The hot FP32 prefetch kernel over all cells (or a subset); the cells it
+// defers go to o.retry0 for launch_cells3(..., tier 3).
+cudaError_t launch_cells3_hot(const Store &s, const Out &o, const Params &p, const Offsets &off, unsigned *ticket,
+                              int sm_count, int warps_per_cta, const int *cells, int ncells, cudaStream_t st) {
+    const int w = warps_per_cta > 0 ? min(warps_per_cta, VG_MAXT / 32) : VG_MAXT / 32;
+    return s.nsys > 1
+               ? launch_t<float, VG_T0_VPL, 64, true, VG_T0_G, false, true>(s, o, p, off, ticket, sm_count, w, cells,
+                                                                           ncells, 0, st)
+               : launch_t<float, VG_T0_VPL, 64, false, VG_T0_G, false, true>(s, o, p, off, ticket, sm_count, w, cells,
+                                                                            ncells, 0, st);
 }
 
 }  // namespace vg

@@ -84,6 +84,8 @@ struct Out {
     int *retry_count;
     int *retry2;                  // sorted indices of cells for tier 2
     int *retry2_count;
+    int *retry0;                  // sorted indices of cells the hot kernel deferred (tier 3)
+    int *retry0_count;
     // optional: the final cell's triangles (plane triples, 64 slots a cell)
     // and their count, 0 where the cell has merged vertices or no entry
     unsigned *topo;
@@ -184,6 +186,8 @@ cudaError_t launch_weinberg(const unsigned *topo, const int *topo_n, long long n
 cudaError_t launch_cells3(const Store &s, const Out &o, const Params &p, const Offsets &off,
                           int precision, unsigned *ticket, int sm_count, int warps_per_cta,
                           const int *cells, int ncells, int tier, cudaStream_t st);
+cudaError_t launch_cells3_hot(const Store &s, const Out &o, const Params &p, const Offsets &off, unsigned *ticket,
+                              int sm_count, int warps_per_cta, const int *cells, int ncells, cudaStream_t st);
 cudaError_t launch_cells2(const Store &s, const Out &o, const Params &p, const Offsets &off,
                           int precision, unsigned *ticket, int sm_count, int warps_per_cta,
                           const int *cells, int ncells, int tier, cudaStream_t st);
@@ -271,6 +275,7 @@ struct vg_ctx {
     unsigned char *d_w_fallback = nullptr;
     int *d_caplist = nullptr, *d_capcount = nullptr;
     int *d_caplist2 = nullptr, *d_capcount2 = nullptr;
+    int *d_caplist0 = nullptr, *d_capcount0 = nullptr;   // deferred by the hot 3D kernel
 
     // walk offsets, one slice per distinct block shape (Sys::off_base)
     int *d_off_code = nullptr;
