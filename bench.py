@@ -65,8 +65,17 @@ WORKLOADS = {
     "extreme3d": ("extreme3d: 10^8 points, each coordinate 1/2 + 4 (X - 1/2)^3 (seed 13), walled unit cube, "
                   "584^3 blocks (Table 3, n_opt 0.5); chosen form = FP32 cuts + FP64 re-test, "
                   "distance-sorted preload (72)"),
+    # the same three cases in 2D (Table 3 grids)
+    "homog2d": ("homog2d: 10^8 points uniform in the walled unit square (seed 14), 5423^2 blocks (Table 3, "
+                "n_opt 3.4); chosen form = FP32 cuts + FP64 re-test, block walk"),
+    "local2d": ("local2d: the points of 10^8 uniform ones (seed 15) inside the central square of area 0.1, "
+                "walled unit square, 1825^2 blocks (Table 3, n_opt 30); chosen form = FP32 cuts + FP64 "
+                "re-test, block walk"),
+    "extreme2d": ("extreme2d: 10^8 points, each coordinate 1/2 + 4 (X - 1/2)^3 (seed 16), walled unit square, "
+                  "14142^2 blocks (Table 3, n_opt 0.5); chosen form = FP32 cuts + FP64 re-test, block walk"),
 }
 PAPER3D = ("homog3d", "local3d", "local3d_clip", "extreme3d")
+PAPER2D = ("homog2d", "local2d", "extreme2d")
 METRIC_2D = "2D Voronoi cells/s, 1 GB300, chosen vs plain FP64 form; % of roofline"
 # FP32 peak derived from unit counts and clock: 152 SMs x 128 FP32 lanes x
 # 2 FLOP (FMA) x 2.07 GHz
@@ -141,6 +150,12 @@ def workload(name: str, rank: int):
         return W.localized(100_000_000, 3, 0.1, seed=12 + rank), (126,) * 3, "prefetch", False
     if name == "extreme3d":
         return W.extreme_clustering(100_000_000, 3, seed=13 + rank), (584,) * 3, "prefetch", False
+    if name == "homog2d":
+        return W.uniform(100_000_000, 2, 1.0, False, seed=14 + rank), (5423,) * 2, "walk", False
+    if name == "local2d":
+        return W.localized(100_000_000, 2, 0.1, seed=15 + rank), (1825,) * 2, "walk", False
+    if name == "extreme2d":
+        return W.extreme_clustering(100_000_000, 2, seed=16 + rank), (14142,) * 2, "walk", False
     if name == "uniform1m":
         return W.uniform(1_000_000, 3, 100.0, True, seed=1 + rank), (58, 58, 58), "prefetch", True
     if name == "slabs102m":
@@ -250,7 +265,7 @@ def batched_run(V, torch, stream, flush, mlp, steps: int = 5, seed: int = 5):
     systems = W.batched_systems(256, 1000, 200_000, seed=seed)
     t0 = time.perf_counter()
     cache = A.Cache(TUNE_CACHE)
-    key = "batched256-seed%d" % seed
+    key = "batched256-seed%d-split" % seed
     tb = cache.get(key)
     if tb is None:
         tb = A.tune_batch(systems, torch, cache, predictor=mlp, mlp_args=(MLP_ALPHA, MLP_KMIN, MLP_KMAX))
@@ -277,10 +292,29 @@ def batched_run(V, torch, stream, flush, mlp, steps: int = 5, seed: int = 5):
         per_class = {}
         for c, v in zip(tb["classes"], tb["n_opt"]):
             per_class[c] = v
+        # the same launch on each distribution's systems alone: where the
+        # batch's time goes
+        by_tag = {}
+        for tag in sorted(mix):
+            idx = [k for k, x in enumerate(systems) if x.tag == tag]
+            sub = V.vg_batch_create(3, [descs[k] for k in idx], stream=stream)
+            try:
+                pos_t = torch.from_numpy(np.concatenate([systems[k].pos for k in idx])).cuda()
+                if cfg.use_mlp:
+                    V.vg_set_predictor(sub, mlp, MLP_ALPHA, MLP_KMIN, MLP_KMAX)
+                V.vg_graph_capture(sub, [counts[k] for k in idx], pos_t, None, cfg)
+                V.vg_graph_launch(sub)
+                V.vg_graph_sync(sub)
+                ms_t = graph_steps(V, torch, sub, stream, flush, 3)
+                n_t = int(sum(counts[k] for k in idx))
+                by_tag[tag] = {"systems": len(idx), "cells": n_t, "ms_per_step": sum(ms_t) / 3,
+                               "cells_per_s": n_t * 3 / (sum(ms_t) / 1000.0)}
+            finally:
+                V.vg_destroy(sub)
         return {"value": n * steps / (sum(ms) / 1000.0), "unit": "cells/s", "steps": steps,
                 "ms_per_step": sum(ms) / steps, "cells_per_step": n, "systems": len(systems),
-                "mix": mix, "n_opt_by_class": per_class,
-                "launch": {k: tb["launch"].get(k, 0) for k in ("order", "warps_per_cta", "chunk", "use_mlp")},
+                "mix": mix, "n_opt_by_class": per_class, "by_distribution": by_tag,
+                "launch": {k: tb["launch"].get(k, 0) for k in ("order", "warps_per_cta", "chunk", "use_mlp", "split")},
                 "tuning_seconds": tune_s,
                 "form": "FP32 cuts + FP64 re-test, autotuned N_opt, launch and preload (fixed or learned), "
                         "one graph replay",
@@ -465,7 +499,7 @@ def main():
     B.build()
     from paper_2209_11606_gb300 import predictor as P, vorogpu as V
 
-    big = args.workload in ("slabs102m",) + PAPER3D
+    big = args.workload in ("slabs102m",) + PAPER3D + PAPER2D
     s, grid, chosen_order, learned_on = workload(args.workload, rank)
     n, dim = s.n, s.dim
     order_code = V.VG_PREFETCH if chosen_order == "prefetch" else V.VG_WALK

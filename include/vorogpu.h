@@ -112,6 +112,14 @@ typedef struct {
     int weinberg;      /* 1 = also the Weinberg code of every 3D cell's edge
                           graph (Sec. 4), read with vg_get_weinberg(); FP32
                           form, eager vg_compute only.  Default 0 */
+    int split;         /* 3D FP32 prefetch only.  1 (default): a kernel built
+                          for the common path alone computes every cell it
+                          can, and hands each cell that needs the walk after
+                          its preload or FP64 statistics to the general
+                          kernel, which computes that cell from the start.
+                          0: the general kernel computes every cell (better
+                          where many cells outgrow their preload, as in
+                          clustered sets).  Results are the same */
 } vg_config;
 
 /* Fills `cfg` with the defaults listed above (FP32_RETEST, PREFETCH). */

@@ -89,12 +89,13 @@ class Cache:
         os.replace(tmp, self.path)
 
 
-def _cfg(order: str, warps: int, chunk: int, use_mlp: int = 0):
+def _cfg(order: str, warps: int, chunk: int, use_mlp: int = 0, split: int = 1):
     cfg = V.vg_config_default()
     cfg.order = V.VG_WALK if order == "walk" else V.VG_PREFETCH
     cfg.warps_per_cta = warps
     cfg.chunk = chunk
     cfg.use_mlp = int(use_mlp)
+    cfg.split = int(split)
     return cfg
 
 
@@ -162,15 +163,17 @@ def tuned(s, torch, cache: Cache | None = None, cls: str | None = None, **kw) ->
 
 def config_from(best: dict):
     """vg_config of a tuned entry."""
-    return _cfg(best["order"], int(best["warps_per_cta"]), int(best["chunk"]), int(best.get("use_mlp", 0)))
+    return _cfg(best["order"], int(best["warps_per_cta"]), int(best["chunk"]), int(best.get("use_mlp", 0)),
+                int(best.get("split", 1)))
 
 
 def tune_batch(systems, torch, cache: Cache | None = None, sample_frac: float = 0.05, seed: int = 0,
                reps: int = 2, predictor=None, mlp_args=(1.5, 24.0, 1024.0)) -> dict:
     """Parameters for a batch of systems: N_opt per distribution class (tuned
     on the class's largest system with the default launch), then the launch
-    parameters (order, warps per CTA, chunk, and with a `predictor` handle
-    fixed or learned preload targets, `mlp_args` = (alpha, kmin, kmax)) on a
+    parameters (order, warps per CTA, chunk, the hot/general kernel split of
+    the prefetch form, and with a `predictor` handle fixed or learned preload
+    targets, `mlp_args` = (alpha, kmin, kmax)) on a
     sample of the whole batch with those grids.  Returns {"n_opt": [...],
     "launch": {...}, "classes": [...]}."""
     classes = [distribution_class(x.pos, x.lo, x.hi) for x in systems]
@@ -206,11 +209,14 @@ def tune_batch(systems, torch, cache: Cache | None = None, sample_frac: float = 
             if order == "prefetch" and systems[0].dim != 3:
                 continue
             mlps = (0, 1) if order == "prefetch" and predictor is not None else (0,)
+            splits = (1, 0) if order == "prefetch" and systems[0].dim == 3 else (1,)
             for w in WARPS:
                 for ch in CHUNKS:
                     for um in mlps:
-                        ms = _time_subset(ctx, sample, _cfg(order, w, ch, um), reps)
-                        table.append({"order": order, "warps_per_cta": w, "chunk": ch, "use_mlp": um, "ms": ms})
+                        for sp in splits:
+                            ms = _time_subset(ctx, sample, _cfg(order, w, ch, um, sp), reps)
+                            table.append({"order": order, "warps_per_cta": w, "chunk": ch, "use_mlp": um,
+                                          "split": sp, "ms": ms})
     finally:
         V.vg_destroy(ctx)
     launch = min(table, key=lambda r: r["ms"])

@@ -441,8 +441,8 @@ cudaError_t enqueue_cells(vg_ctx *c, const vg_config &cfg, cudaStream_t s, const
     const int nc = subset ? nsubset : (int)c->n;
     // 3D FP32 prefetch: the hot kernel over every cell, then the general one
     // over the cells it deferred (walk after the preload, FP64 statistics)
-    const bool hot = c->dim == 3 && cfg.precision == VG_FP32_RETEST && cfg.order == VG_PREFETCH && !cfg.weinberg &&
-                     c->n < (1 << 27);
+    const bool hot = cfg.split && c->dim == 3 && cfg.precision == VG_FP32_RETEST && cfg.order == VG_PREFETCH &&
+                     !cfg.weinberg && c->n < (1 << 27);
     if (hot) {
         if ((e = launch_cells3_hot(st, o, pp, off, c->d_ticket, c->sm_count, cfg.warps_per_cta, subset, nc, s)))
             return e;
@@ -492,6 +492,7 @@ void vg_config_default(vg_config *cfg) {
     cfg->warps_per_cta = 0;
     cfg->collect_stats = 0;
     cfg->time_kernels = 0;
+    cfg->split = 1;
 }
 
 vg_status vg_create(vg_ctx **out, int dim, const double *lo, const double *hi, const int *periodic,

@@ -48,16 +48,20 @@ namespace {
 
 constexpr unsigned TRI_EMPTY = 0xffffffffu;
 constexpr int KMAX = 128;         // prefetch list capacity
-constexpr int NRUN = 128;         // prefetch gather: runs of contiguous blocks
+constexpr int NRUN = 64;          // prefetch gather: runs of contiguous blocks
 constexpr int RGMAX = 3;          // prefetch gather: largest block reach per axis
 constexpr int NBIN = 8;           // prefetch: radial buckets
 constexpr float KAP0 = 4.0f;      // condition number covered by the base FP32 band
 constexpr float KAP_MAX2 = 1e8f;  // condition number^2 beyond which a new vertex is solved in FP64
 constexpr int MAX_SHELL_EXTRA = 4;
-// resident CTAs per SM the register budget is sized for: tier 0 (64-vertex
-// cells) five (96 registers a thread, 20 warps an SM), the larger tiers four
+// resident CTAs per SM the register budget is sized for: the hot kernel six
+// (80 registers a thread, 9.3 KB of shared memory a warp: 24 warps an SM),
+// the general tier-0 kernel five (96 registers), the larger tiers four
 #ifndef VG_MINB
 #define VG_MINB 5
+#endif
+#ifndef VG_MINB_HOT
+#define VG_MINB_HOT 6
 #endif
 #ifndef VG_MAXT
 #define VG_MAXT 128
@@ -72,7 +76,7 @@ constexpr int MAX_SHELL_EXTRA = 4;
 #ifdef VG_MAXREG
 #define VG_BOUNDS __maxnreg__(VG_MAXREG)
 #else
-#define VG_BOUNDS __launch_bounds__(VG_MAXT, MAXP == 64 ? VG_MINB : 4)
+#define VG_BOUNDS __launch_bounds__(VG_MAXT, MAXP == 64 ? (HOT ? VG_MINB_HOT : VG_MINB) : 4)
 #endif
 
 template <typename T> struct V4T;
@@ -116,7 +120,7 @@ struct Src {
     int rg[3];         // prefetch reach in blocks per axis
 };
 
-template <typename T, int VPL, int MAXP, int G>
+template <typename T, int VPL, int MAXP, int G, bool HOT>
 struct Smem {
     // slot indices in the face walk tables: a byte up to 256 vertices
     using FT = typename std::conditional<(G * VPL > 256), unsigned short, unsigned char>::type;
@@ -126,7 +130,6 @@ struct Smem {
     float4 v4[G * VPL];                     // FP32 form: the cell's vertices (x, y, z, kappa); free slots 0
     unsigned E[MAXP][MAXP / 32];  // removed directed edges of one cut (32-bit words: native shared atomics)
     union {
-        FT ftab[G][MAXP];              // face walk tables, one row per face of a round
         struct {
             int start[NRUN], j0[NRUN], oxb[NRUN], oyz[NRUN];
         } run;                         // prefetch gather: runs of contiguous blocks
@@ -143,7 +146,8 @@ struct Smem {
         struct {
             unsigned stri[G * VPL];            // the cell's triangles, by slot
             T sx[G * VPL], sy[G * VPL], sz[G * VPL];
-            double dpos[G * VPL][3];           // FP64 vertices (degenerate cells)
+            FT ftab[G][MAXP];                  // face walk tables, one row per face of a round
+            double dpos[HOT ? 1 : G * VPL][3]; // FP64 vertices (degenerate cells; not in the hot kernel)
         } v;                                   // statistics: the finished cell
     } x;
     FT sfirst[G];              // a triangle of each face of a round
@@ -540,7 +544,7 @@ __global__ void VG_BOUNDS
     constexpr int CAP = G * VPL;
     constexpr int NW = MAXP / 64;
     constexpr int R = MAXP / G;
-    using S_t = Smem<T, VPL, MAXP, G>;
+    using S_t = Smem<T, VPL, MAXP, G, HOT>;
     extern __shared__ __align__(32) unsigned char smem_raw[];
     // G lanes per cell: gl is the lane within the cell's group
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1303,7 +1307,9 @@ __global__ void VG_BOUNDS
                     const bool have = gl < 3 * R;
                     const int e = have ? S.elist[gl] : 0;
                     const int ex = e & 0xff, ey = e >> 8;
-                    const unsigned key = have ? (unsigned)(min(ex, ey) | (max(ex, ey) << 8)) : 0x10000u + gl;
+                    // idle lanes share one key: the match's cost grows with
+                    // the number of distinct keys
+                    const unsigned key = have ? (unsigned)(min(ex, ey) | (max(ex, ey) << 8)) : 0xffffffffu;
                     // every lane of the group takes part in the match (not behind &&)
                     const unsigned same = __match_any_sync(gmask, key);
                     const bool bd = have && __popc(same) == 1;
@@ -1619,7 +1625,7 @@ __global__ void VG_BOUNDS
                                     else if (pl_ > lo64) rk += __popcll(live[w2] & ((1ull << (pl_ - lo64)) - 1));
                                 }
                                 if (rk / G == rnd) {
-                                    S.w.ftab[rk % G][xx] = (typename S_t::FT)t;
+                                    S.x.v.ftab[rk % G][xx] = (typename S_t::FT)t;
                                     S.sfirst[rk % G] = (typename S_t::FT)t;
                                 }
                             }
@@ -1642,7 +1648,7 @@ __global__ void VG_BOUNDS
                                 const int p0 = tri_a(tr), p1 = tri_b(tr), p2 = tri_c(tr);
                                 const int yy = p0 == a ? p2 : (p1 == a ? p0 : (p2 == a ? p1 : -1));
                                 if (yy < 0) { bad = true; break; }
-                                const int nx = S.w.ftab[gl][yy];
+                                const int nx = S.x.v.ftab[gl][yy];
                                 if (nx >= CAP || S.x.v.stri[nx] == TRI_EMPTY) { bad = true; break; }
                                 if (nx == t0) { steps++; closed = true; break; }
                                 if (cur != t0) {
@@ -1681,7 +1687,7 @@ __global__ void VG_BOUNDS
                                 const int p0 = tri_a(tr), p1 = tri_b(tr), p2 = tri_c(tr);
                                 const int yy = p0 == a ? p2 : (p1 == a ? p0 : (p2 == a ? p1 : -1));
                                 if (yy < 0) { bad = true; break; }
-                                const int nx = S.w.ftab[gl][yy];
+                                const int nx = S.x.v.ftab[gl][yy];
                                 if (nx >= CAP || S.x.v.stri[nx] == TRI_EMPTY) { bad = true; break; }
                                 if (nx == t0) { steps++; closed = true; break; }
                                 const double A[3] = {S.x.v.dpos[cur][0] - dref[0], S.x.v.dpos[cur][1] - dref[1],
@@ -1736,6 +1742,11 @@ __global__ void VG_BOUNDS
 #pragma unroll
                             for (int r = 0; r < R; r++)
                                 if (r == rnd) key[r] = k;
+                        } else if (order >= 3) {
+                            // a face dropped for its width (a sliver of distinct
+                            // vertices) keeps its edges: they stay edges of the
+                            // cell, held by the neighbouring faces
+                            order_sum += order;
                         }
                     }
                     __syncwarp(gmask);
@@ -1891,7 +1902,7 @@ __global__ void VG_BOUNDS
 template <typename T, int VPL, int MAXP, bool BATCH, int G, bool TOPO = false, bool HOT = false>
 cudaError_t launch_t(const Store &s, const Out &o, const Params &p, const Offsets &off, unsigned *ticket,
                      int sm_count, int warps, const int *cells, int ncells, int tier, cudaStream_t st) {
-    const size_t smem = sizeof(Smem<T, VPL, MAXP, G>) * warps * (32 / G);
+    const size_t smem = sizeof(Smem<T, VPL, MAXP, G, HOT>) * warps * (32 / G);
     auto kfn = k_cells3<T, VPL, MAXP, BATCH, G, TOPO, HOT>;
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

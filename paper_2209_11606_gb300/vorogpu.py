@@ -42,7 +42,8 @@ class VgConfig(ctypes.Structure):
                 ("tau_rel", ctypes.c_double), ("merge_rel", ctypes.c_double),
                 ("prefetch_k", ctypes.c_int), ("use_mlp", ctypes.c_int), ("chunk", ctypes.c_int),
                 ("warps_per_cta", ctypes.c_int), ("collect_stats", ctypes.c_int),
-                ("time_kernels", ctypes.c_int), ("clip", ctypes.c_double), ("weinberg", ctypes.c_int)]
+                ("time_kernels", ctypes.c_int), ("clip", ctypes.c_double), ("weinberg", ctypes.c_int),
+                ("split", ctypes.c_int)]
 
 
 class VgSystem(ctypes.Structure):
