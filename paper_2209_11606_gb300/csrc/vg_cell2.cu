@@ -353,55 +353,96 @@ __global__ void __launch_bounds__(128, VG2_MINB) k_cells2(const __grid_constant_
         const int maxs = min(16000, SY.off_shell + 4 + 2 * max(g.nb[0], g.nb[1]));
         const int ocount = SY.off_count, obase = SY.off_base;
         int e = 0, shell = 0, sidx = 0, mode = 1;  // 1 list, 2 shells, 3 done
+        // blocks are taken G at a time, one per lane of the group (a window):
+        // each lane resolves its block and loads its particle range, so the
+        // loads of a window are in flight together; the blocks that hold
+        // particles are then cut one after another
         for (int guard = 0; guard < (1 << 30) && mode != 3 && !(flags & 6); guard++) {
-            int ox = 0, oy = 0;
+            int wox = 0, woy = 0;
+            bool cand = false, last = false;
             if (mode == 1) {
                 if (e >= ocount) { mode = 2; shell = 1; sidx = 0; continue; }
-                const float lbv = __ldg(&off.lb[obase + e]);
-                if ((T)(lbv * lbv) * (T)0.99998 >= stop) { mode = 3; continue; }
-                const int code = __ldg(&off.code[obase + e]);
-                e++;
-                ox = imgc2(code, 0);
-                oy = imgc2(code, 1);
+                const int ei = e + gl;
+                bool beyond = true;
+                if (ei < ocount) {
+                    const float lbv = __ldg(&off.lb[obase + ei]);
+                    beyond = (T)(lbv * lbv) * (T)0.99998 >= stop;
+                    const int code = __ldg(&off.code[obase + ei]);
+                    wox = imgc2(code, 0);
+                    woy = imgc2(code, 1);
+                }
+                // the list is sorted by its bound: entries past the first one
+                // beyond the stop radius are all beyond it
+                const unsigned bb = gballot<G>(gmask, gbase, beyond);
+                const int first = bb ? __ffs(bb) - 1 : G;
+                cand = gl < first;
+                last = first < G && e + first < ocount;
+                e += G;
             } else {
                 const float sb = (float)(shell - 1) * hmin;
                 if ((T)(sb * sb) * (T)0.99998 >= stop) { mode = 3; continue; }
                 if (shell > maxs) { limit = 1; mode = 3; continue; }
                 // the shell's surface only: two rows of wd, two columns of wd - 2
-                const int wd = 2 * shell + 1;
-                if (sidx >= 4 * wd - 4) { shell++; sidx = 0; continue; }
-                if (sidx < 2 * wd) {
-                    const int r = sidx < wd ? sidx : sidx - wd;
-                    ox = r - shell;
-                    oy = sidx < wd ? -shell : shell;
-                } else {
-                    const int t = sidx - 2 * wd, r = t < wd - 2 ? t : t - (wd - 2);
-                    ox = t < wd - 2 ? -shell : shell;
-                    oy = r - (shell - 1);
+                const int wd = 2 * shell + 1, ns = 4 * wd - 4;
+                if (sidx >= ns) { shell++; sidx = 0; continue; }
+                const int si = sidx + gl;
+                if (si < ns) {
+                    if (si < 2 * wd) {
+                        const int r = si < wd ? si : si - wd;
+                        wox = r - shell;
+                        woy = si < wd ? -shell : shell;
+                    } else {
+                        const int t = si - 2 * wd, r = t < wd - 2 ? t : t - (wd - 2);
+                        wox = t < wd - 2 ? -shell : shell;
+                        woy = r - (shell - 1);
+                    }
+                    // shell members that the offset list did not hold (its bound is
+                    // below off_shell * h_min, in FP32, exactly as the list was cut)
+                    const float lbmax = (float)SY.off_shell * hmin;
+                    const float lbx = fmaxf(0.f, (float)(abs(wox) - 1)) * g.hf[0];
+                    const float lby = fmaxf(0.f, (float)(abs(woy) - 1)) * g.hf[1];
+                    cand = !(lbx * lbx + lby * lby < lbmax * lbmax);
                 }
-                sidx++;
-                // shell members that the offset list did not hold (its bound is
-                // below off_shell * h_min, in FP32, exactly as the list was cut)
-                const float lbmax = (float)SY.off_shell * hmin;
-                const float lbx = fmaxf(0.f, (float)(abs(ox) - 1)) * g.hf[0];
-                const float lby = fmaxf(0.f, (float)(abs(oy) - 1)) * g.hf[1];
-                if (lbx * lbx + lby * lby < lbmax * lbmax) continue;
+                sidx += G;
             }
-            // the block: resolve, distance bound, particles
-            int t0 = b0 + ox, t1 = b1 + oy, m0 = 0, m1 = 0;
-            if (g.per[0]) { m0 = floordiv_near(t0, g.nb[0]); t0 -= m0 * g.nb[0]; }
-            else if (t0 < 0 || t0 >= g.nb[0]) continue;
-            if (g.per[1]) { m1 = floordiv_near(t1, g.nb[1]); t1 -= m1 * g.nb[1]; }
-            else if (t1 < 0 || t1 >= g.nb[1]) continue;
-            {
-                float lo0 = (float)ox * g.hf[0] - o0, lo1 = (float)oy * g.hf[1] - o1;
-                float gx = lo0 > 0.f ? lo0 : (lo0 + g.hf[0] < 0.f ? -(lo0 + g.hf[0]) : 0.f);
-                float gy = lo1 > 0.f ? lo1 : (lo1 + g.hf[1] < 0.f ? -(lo1 + g.hf[1]) : 0.f);
-                if ((T)(gx * gx + gy * gy) * (T)0.99998 >= stop) continue;
+            // each lane's block: resolve, distance bound, particle range
+            int wj0 = 0, wj1 = 0, wimg = 0;
+            if (cand) {
+                int t0 = b0 + wox, t1 = b1 + woy, m0 = 0, m1 = 0;
+                if (g.per[0]) { m0 = floordiv_near(t0, g.nb[0]); t0 -= m0 * g.nb[0]; }
+                else if (t0 < 0 || t0 >= g.nb[0]) cand = false;
+                if (g.per[1]) { m1 = floordiv_near(t1, g.nb[1]); t1 -= m1 * g.nb[1]; }
+                else if (t1 < 0 || t1 >= g.nb[1]) cand = false;
+                if (cand) {
+                    const float lo0 = (float)wox * g.hf[0] - o0, lo1 = (float)woy * g.hf[1] - o1;
+                    const float gx = lo0 > 0.f ? lo0 : (lo0 + g.hf[0] < 0.f ? -(lo0 + g.hf[0]) : 0.f);
+                    const float gy = lo1 > 0.f ? lo1 : (lo1 + g.hf[1] < 0.f ? -(lo1 + g.hf[1]) : 0.f);
+                    cand = !((T)(gx * gx + gy * gy) * (T)0.99998 >= stop);
+                }
+                if (cand) {
+                    const int kb = (int)SY.blk_base + t0 + g.nb[0] * t1;
+                    wj0 = __ldg(&st.bstart[kb]);
+                    wj1 = __ldg(&st.bstart[kb + 1]);
+                    wimg = pack2(m0, m1);
+                    cand = wj1 > wj0;
+                }
             }
-            const int kb = (int)SY.blk_base + t0 + g.nb[0] * t1;
-            const int j0 = __ldg(&st.bstart[kb]), j1 = __ldg(&st.bstart[kb + 1]);
-            const int img = pack2(m0, m1);
+            if (last) mode = 3;  // after this window
+            unsigned blocks = gballot<G>(gmask, gbase, cand);
+            while (blocks && !(flags & 6)) {
+                const int bl = __ffs(blocks) - 1;
+                blocks &= blocks - 1;
+                const int ox = __shfl_sync(gmask, wox, bl, G), oy = __shfl_sync(gmask, woy, bl, G);
+                const int j0 = __shfl_sync(gmask, wj0, bl, G), j1 = __shfl_sync(gmask, wj1, bl, G);
+                const int img = __shfl_sync(gmask, wimg, bl, G);
+                const int m0 = imgc2(img, 0), m1 = imgc2(img, 1);
+                {
+                    // cuts of earlier blocks may have brought the bound closer
+                    const float lo0 = (float)ox * g.hf[0] - o0, lo1 = (float)oy * g.hf[1] - o1;
+                    const float gx = lo0 > 0.f ? lo0 : (lo0 + g.hf[0] < 0.f ? -(lo0 + g.hf[0]) : 0.f);
+                    const float gy = lo1 > 0.f ? lo1 : (lo1 + g.hf[1] < 0.f ? -(lo1 + g.hf[1]) : 0.f);
+                    if ((T)(gx * gx + gy * gy) * (T)0.99998 >= stop) continue;
+                }
             for (int jb = j0; jb < j1 && !(flags & 6); jb += G) {
                 const int j = jb + gl;
                 T qx = 0, qy = 0, qq = 0, rj = 0;
@@ -569,6 +610,7 @@ __global__ void __launch_bounds__(128, VG2_MINB) k_cells2(const __grid_constant_
                     stop = stop2();
                 }
             }
+            }  // blocks of the window
         }
 
         if (mode != 3 && !(flags & 6)) limit = 1;  // the guard ran out

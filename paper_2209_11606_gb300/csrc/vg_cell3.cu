@@ -1020,7 +1020,7 @@ __global__ void VG_BOUNDS
                             if constexpr (F32) {
                                 if (filt && ok && q4.w >= 1e-30f) {
                                     const float cc = st.radical ? 0.5f * (q4.w + rp32 * rp32 - crj * crj) : 0.5f * q4.w;
-                                    ok = may_cut(S.v4, G * (32 - __clz(rows)), q4.x, q4.y, q4.z, cc,
+                                    ok = may_cut(S.v4, ((ntri + 7) & ~7), q4.x, q4.y, q4.z, cc,
                                                  VG_RARE(q4.w < qabs2) ? band_close(tol32f, r2, q4.w, eabs)
                                                                        : tol32f * sqrt_a(r2 * q4.w));
                                 }
@@ -1079,7 +1079,7 @@ __global__ void VG_BOUNDS
                             if constexpr (F32) {
                                 if (filt && ok && cqq >= 1e-30f) {
                                     const float cc = st.radical ? 0.5f * (cqq + rp32 * rp32 - crj * crj) : 0.5f * cqq;
-                                    ok = may_cut(S.v4, G * (32 - __clz(rows)), cqx, cqy, cqz, cc,
+                                    ok = may_cut(S.v4, ((ntri + 7) & ~7), cqx, cqy, cqz, cc,
                                                  VG_RARE(cqq < qabs2) ? band_close(tol32f, r2, cqq, eabs)
                                                                       : tol32f * sqrt_a(r2 * cqq));
                                 }
@@ -1163,7 +1163,7 @@ __global__ void VG_BOUNDS
                                                 bl2 = (float)oz * g.hf[2] - o2;
                                     const float ex = st.radical ? (float)(S.cc.rmax * S.cc.rmax - S.cc.rp * S.cc.rp) : 0.f;
                                     const float sl = 1e-5f * (sqrt_a((float)r2) + fmaxf(g.hf[0], fmaxf(g.hf[1], g.hf[2])));
-                                    cand = block_touches(S.v4, G * (32 - __clz(rows)), bl0, bl1, bl2, bl0 + g.hf[0],
+                                    cand = block_touches(S.v4, ((ntri + 7) & ~7), bl0, bl1, bl2, bl0 + g.hf[0],
                                                          bl1 + g.hf[1], bl2 + g.hf[2], fmaxf(ex, 0.f), sl);
                                 }
                             }
@@ -1476,6 +1476,8 @@ __global__ void VG_BOUNDS
                 // carries it through the group maximum to every lane)
                 const T r2lim = r2 * (T)1.01;
                 bool wild = false;
+                // the mirror holds the vertices packed in (slot, lane) order
+                int mpos = 0;
 #pragma unroll
                 for (int s = 0; s < VPL; s++) {
                     if (tri[s] != TRI_EMPTY) {
@@ -1484,10 +1486,15 @@ __global__ void VG_BOUNDS
                         if constexpr (F32) q2 *= 1.f + 4e-6f * kap[s];  // allowance for FP32 error
                         rr = rr > q2 ? rr : q2;
                     }
+                    const unsigned oc = gballot<G>(gmask, gbase, tri[s] != TRI_EMPTY);
                     if constexpr (F32)
-                        S.v4[s * G + gl] = tri[s] != TRI_EMPTY ? make_float4(vx[s], vy[s], vz[s], kap[s])
-                                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (__any_sync(gmask, tri[s] != TRI_EMPTY)) rows |= 1u << s;
+                        if (tri[s] != TRI_EMPTY) S.v4[mpos + __popc(oc & lt)] = make_float4(vx[s], vy[s], vz[s], kap[s]);
+                    if (oc) rows |= 1u << s;
+                    mpos += __popc(oc);
+                }
+                if constexpr (F32) {
+                    // entries up to the next multiple of 8 are read too: free ones
+                    if (gl < ((ntri + 7) & ~7) - ntri) S.v4[ntri + gl] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
                 if (VG_RARE(wild)) rr = (T)INFINITY;
                 r2 = gmax<G>(gmask, rr);
@@ -1606,6 +1613,13 @@ __global__ void VG_BOUNDS
                             }
                             cntw += pc;
                         }
+                    }
+                    // the neighbour's input index, asked for before the walk so that
+                    // the load's round trip overlaps it
+                    int nid_pre = 0;
+                    if (a >= 0) {
+                        const int ref0 = S.pref[a];
+                        nid_pre = ref0 >= 0 ? __ldg(&st.sid[ref0]) : ref0;
                     }
                     // every vertex enters itself in the walk tables of its faces
 #pragma unroll 1
@@ -1730,8 +1744,7 @@ __global__ void VG_BOUNDS
                             area += farea;
                             order_sum += order;
                             faces_kept++;
-                            const int ref = S.pref[a];
-                            const int nid = ref >= 0 ? __ldg(&st.sid[ref]) : ref;
+                            const int nid = nid_pre;
                             const int img = S.pimg[a];
                             const unsigned ib = ((unsigned)(imgc(img, 0) + 128) << 16) |
                                                 ((unsigned)(imgc(img, 1) + 128) << 8) | (unsigned)(imgc(img, 2) + 128);
