@@ -131,6 +131,10 @@ def parse():
                     help="skip the 102.4M-point slabs record of the default run")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the comparison of the GPU outputs with the oracle's")
+    ap.add_argument("--grid", type=int, default=0,
+                    help="blocks per axis instead of the workload's grid (e.g. a tuned grid)")
+    ap.add_argument("--split", type=int, default=1, choices=[0, 1],
+                    help="3D FP32 prefetch: 1 = the hot kernel with deferral, 0 = the general kernel alone")
     ap.add_argument("--weinberg", action="store_true",
                     help="also time the cells with Weinberg codes (Sec. 4), eager calls")
     return ap.parse_args()
@@ -501,6 +505,8 @@ def main():
 
     big = args.workload in ("slabs102m",) + PAPER3D + PAPER2D
     s, grid, chosen_order, learned_on = workload(args.workload, rank)
+    if args.grid > 0:
+        grid = (args.grid,) * s.dim
     n, dim = s.n, s.dim
     order_code = V.VG_PREFETCH if chosen_order == "prefetch" else V.VG_WALK
     stream = torch.cuda.current_stream()
@@ -516,6 +522,7 @@ def main():
     cfg = V.vg_config_default()
     cfg.precision, cfg.order, cfg.use_mlp = V.VG_FP32_RETEST, order_code, int(learned_on)
     cfg.clip = clip
+    cfg.split = args.split
 
     # warm-up through the eager calls, then the step as one graph: sort ->
     # learned preload targets -> cells -> faces, the cell kernels timed by
@@ -527,6 +534,7 @@ def main():
     gcfg = V.vg_config_default()
     gcfg.clip = clip
     gcfg.precision, gcfg.order, gcfg.use_mlp, gcfg.time_kernels = cfg.precision, cfg.order, cfg.use_mlp, 1
+    gcfg.split = cfg.split
     V.vg_graph_capture(ctx, [n], pos_d, rad_d, gcfg)
     for _ in range(max(args.warmup, 3)):
         V.vg_graph_launch(ctx)
@@ -687,6 +695,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "cells_per_step": n * world,
+                       "kernel_split": args.split, "grid": list(V.vg_get_grid(ctx, dim)),
                        "l2": "flushed between steps (256 MB write outside the timed events)",
                        "parallelism": f"replicas{world}"},
             "step": "one CUDA graph replay: counting sort, learned preload targets, cell kernels "
