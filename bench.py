@@ -91,7 +91,7 @@ FLOP_VTEST, FLOP_CAND, FLOP_NEWV, FLOP_FANTET = 6, 12, 51, 42
 # issue-active fraction.  An entry is removed whenever the kernel changes
 # after its capture, so only counters of the timed build are reported.
 CELL_KERNEL_NCU = {}
-MLP_ALPHA, MLP_KMIN, MLP_KMAX = 1.5, 24.0, 1024.0
+MLP_ALPHA, MLP_KMIN, MLP_KMAX = 1.2, 24.0, 1024.0
 # peak warp-instruction issue rate: 152 SMs x 4 schedulers x 1 per cycle x 2.07 GHz
 ISSUE_PEAK = 152 * 4 * 2.07e9
 # algorithmic bytes of the counting sort per particle (FP64 input): read the
@@ -379,7 +379,8 @@ def large_run(V, torch, stream, flush, mlp, steps: int = 2, with_oracle: bool = 
                "plain_fp64": {"value": plain, "unit": "cells/s",
                               "form": "FP64 everywhere, block walk, eager insert + compute"},
                "chosen_vs_plain": chosen / plain,
-               "learned_preload": {"fallback_rate": float(fb.mean()), "preload_per_cell": float(pref.mean())},
+               "learned_preload": {"shortfall_rate": float((fb > 0).mean()), "walk_rate": float((fb == 1).mean()),
+                                   "preload_per_cell": float(pref.mean())},
                "form": "FP32 cuts + FP64 re-test, learned distance-sorted preload, graph replays"}
         if with_oracle:
             import oracle
@@ -635,8 +636,10 @@ def main():
         c_fixed = V.vg_config_default()
         c_fixed.clip = clip
         w_fixed, fb_fixed = work(c_fixed)
-        learned = {"fallback_rate": float(fb.mean()), "preload_per_cell": float(w["p"].mean()),
-                   "fixed_k_fallback_rate": float(fb_fixed.mean()),
+        learned = {"shortfall_rate": float((fb > 0).mean()), "walk_rate": float((fb == 1).mean()),
+                   "preload_per_cell": float(w["p"].mean()),
+                   "fixed_k_shortfall_rate": float((fb_fixed > 0).mean()),
+                   "fixed_k_walk_rate": float((fb_fixed == 1).mean()),
                    "fixed_k_preload_per_cell": float(w_fixed["p"].mean()),
                    "alpha": MLP_ALPHA, "trained": mlp_meta}
 

@@ -110,7 +110,7 @@ typedef struct {
                           faces are reported as walls (ids -1..-6 by axis and
                           side).  0 (default): plain cells */
     int weinberg;      /* 1 = also the Weinberg code of every 3D cell's edge
-                          graph (Sec. 4), read with vg_get_weinberg(); FP32
+                          graph (Sec. 4), read with vg_get_weinberg(); either
                           form, eager vg_compute only.  Default 0 */
     int split;         /* 3D FP32 prefetch only.  1 (default): a kernel built
                           for the common path alone computes every cell it
@@ -278,8 +278,9 @@ vg_status vg_get_faces(vg_ctx *ctx, int64_t *face_off, int32_t *nbr_id, int8_t *
  * Per-cell work counters of the last vg_compute() with collect_stats = 1,
  * n entries each (any may be NULL): candidates offered to the cut routine,
  * vertex-plane tests, cuts that removed something, vertices those cuts
- * created, FP64 re-tests, whether the prefetch form fell back to the walk
- * (0/1), and how many candidates the prefetch preloaded (0 for the walk).
+ * created, FP64 re-tests, how the prefetch form met a shortfall of its
+ * preload (0 none, 1 the walk, 2 a second, wider preload), and how many
+ * candidates the prefetch preloaded (both preloads; 0 for the walk).
  */
 vg_status vg_get_work(vg_ctx *ctx, int32_t *n_tested, int32_t *n_vtests, int32_t *n_cuts,
                       int32_t *n_newv, int32_t *n_retest, uint8_t *fallback, int32_t *n_prefetch,
@@ -361,9 +362,11 @@ vg_status vg_get_system_grid(vg_ctx *ctx, int k, int *nblocks);
  * train and run a small network that predicts k per block from the 27 block
  * counts:
  *
- *   features  x_j = log(1 + c_j) / 4, c_j the count of block b + (dx,dy,dz),
+ *   features  x_j = c_j / m - 1, c_j the count of block b + (dx,dy,dz),
  *             j = (dx+1) + 3 (dy+1) + 9 (dz+1), wrapped on periodic axes,
- *             0 past a wall;
+ *             0 past a wall, m the mean count of those of the 27 blocks
+ *             inside the box (x = 0 where m = 0): counts relative to their
+ *             local mean, the same at any density or block size;
  *   network   y = W3 . relu(W2 relu(W1 x + b1) + b2) + b3, hidden widths 32
  *             and 32, W1 W2 W3 in FP16, biases FP32, FP32 accumulation;
  *             predicted count exp(y);

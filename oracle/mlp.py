@@ -14,7 +14,12 @@ contains every candidate within 2R.  Definitions:
 
 * Features of block b: the particle counts c_j of the 27 blocks b + (dx, dy,
   dz), dx, dy, dz in {-1, 0, 1}, j = (dx+1) + 3 (dy+1) + 9 (dz+1), wrapped on
-  periodic axes and 0 outside a walled box; x_j = log(1 + c_j) / 4.
+  periodic axes and 0 outside a walled box, relative to their mean:
+  x_j = c_j / m - 1 with m = (sum_j c_j) / v, v the number of those blocks
+  inside the box (x = 0 where m = 0).  The features do not change with the
+  density or the block size, only with how the particles are spread over
+  the 27 blocks; the cell kernel turns a count into a radius with the same
+  local density m / h^d.
 * Label of cell i: k*_i = the number of candidates (particle j and periodic
   image m, excluding i itself with m = 0) at distance < 2 R_i.  Cutting those
   in distance order leaves the final cell, and the radius bound then stops.
@@ -31,7 +36,8 @@ contains every candidate within 2R.  Definitions:
 
 Every function is pinned by tests/test_oracle_mlp.py: central finite
 differences of the loss, the closed-form first Adam step, the BCC neighbour
-count 14, count invariants of the features, and a k-d tree count.
+count 14, count invariants and density invariance of the features, and a
+k-d tree count.
 """
 from __future__ import annotations
 
@@ -107,21 +113,37 @@ def _neighbour(c, d, axis, periodic):
     return out
 
 
-def block_features(pos, lo, hi, periodic, nblocks):
-    """(B, 27) features of every block, block k = i + n_x (j + n_y l)."""
+def block_counts27(pos, lo, hi, periodic, nblocks):
+    """(B, 27) counts c_j of the blocks b + (dx, dy, dz) of every block b =
+    i + n_x (j + n_y l) (0 past a wall), and (B,) the number of those 27
+    blocks that lie inside the box."""
     c = block_counts(pos, lo, hi, periodic, nblocks).astype(np.float64)
+    one = np.ones_like(c)
     per = list(periodic) + [False] * (3 - len(periodic))
     out = np.zeros((c.size, NIN))
+    inside = np.zeros(c.size)
     for dz in (-1, 0, 1):
         for dy in (-1, 0, 1):
             for dx in (-1, 0, 1):
                 j = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)
                 # array axes are (z, y, x)
-                sh = _neighbour(c, dz, 0, per[2])
-                sh = _neighbour(sh, dy, 1, per[1])
-                sh = _neighbour(sh, dx, 2, per[0])
+                sh, e = c, one
+                for d, ax, p in ((dz, 0, per[2]), (dy, 1, per[1]), (dx, 2, per[0])):
+                    sh = _neighbour(sh, d, ax, p)
+                    e = _neighbour(e, d, ax, p)
                 out[:, j] = sh.reshape(-1)
-    return np.log1p(out) / 4.0
+                inside += e.reshape(-1)
+    return out, inside
+
+
+def block_features(pos, lo, hi, periodic, nblocks):
+    """(B, 27) features of every block: counts over their mean."""
+    c, v = block_counts27(pos, lo, hi, periodic, nblocks)
+    m = c.sum(axis=1) / np.maximum(v, 1.0)
+    x = np.zeros_like(c)
+    ok = m > 0
+    x[ok] = c[ok] / m[ok, None] - 1.0
+    return x
 
 
 def kstar(pos, lo, hi, periodic, rmax, cells=None):

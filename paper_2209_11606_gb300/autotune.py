@@ -168,7 +168,7 @@ def config_from(best: dict):
 
 
 def tune_batch(systems, torch, cache: Cache | None = None, sample_frac: float = 0.05, seed: int = 0,
-               reps: int = 2, predictor=None, mlp_args=(1.5, 24.0, 1024.0)) -> dict:
+               reps: int = 2, predictor=None, mlp_args=(1.2, 24.0, 1024.0)) -> dict:
     """Parameters for a batch of systems: N_opt per distribution class (tuned
     on the class's largest system with the default launch), then the launch
     parameters (order, warps per CTA, chunk, the hot/general kernel split of

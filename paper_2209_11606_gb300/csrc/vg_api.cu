@@ -302,6 +302,7 @@ vg_status prepare_insert(vg_ctx *c, const std::vector<long long> &counts, const 
         }
     }
     VG_CUDA(ensure(c, c->d_bstart, c->total_blk + 1));
+    VG_CUDA(ensure(c, c->d_rho, c->total_blk));
     const size_t need_scan = std::max(scan_tmp_bytes_i32(c->total_blk + 1),
                                       (((size_t)n * sizeof(int) + 255) & ~(size_t)255) + scan_tmp_bytes_i64(n + 1));
     if (need_scan > c->scan_bytes) {
@@ -393,8 +394,7 @@ vg_status check_config(vg_ctx *c, const vg_config &cfg, bool inserts = false) {
     if (cfg.order != VG_WALK && cfg.order != VG_PREFETCH) return fail(c, VG_ERR_ARG, "order");
     if (!(cfg.tol32 > 0) || !(cfg.tau_rel > 0) || !(cfg.merge_rel > 0)) return fail(c, VG_ERR_ARG, "tolerances");
     if (!(cfg.clip >= 0) || !(cfg.clip < 1e300)) return fail(c, VG_ERR_ARG, "clip must be finite and >= 0");
-    if (cfg.weinberg && (c->dim != 3 || cfg.precision != VG_FP32_RETEST))
-        return fail(c, VG_ERR_ARG, "Weinberg codes: 3D cells in the FP32 form");
+    if (cfg.weinberg && c->dim != 3) return fail(c, VG_ERR_ARG, "Weinberg codes: 3D cells");
     if (cfg.weinberg && inserts) return fail(c, VG_ERR_ARG, "Weinberg codes: eager vg_compute only");
     if (cfg.warps_per_cta > 4) return fail(c, VG_ERR_ARG, "warps_per_cta above 4 (CTAs of at most 128 threads)");
     if (cfg.use_mlp && !c->kblock_valid && !(inserts && c->pred))
@@ -414,9 +414,10 @@ cudaError_t enqueue_cells(vg_ctx *c, const vg_config &cfg, cudaStream_t s, const
     pp.tol32 = cfg.tol32; pp.tau_rel = cfg.tau_rel; pp.merge_rel = cfg.merge_rel;
     pp.clip = cfg.clip;
     pp.prefetch_k = cfg.prefetch_k; pp.order = cfg.order;
-    pp.chunk = cfg.chunk > 0 ? cfg.chunk : 2;
+    pp.chunk = cfg.chunk > 0 ? cfg.chunk : 1;
     pp.collect = cfg.collect_stats ? 1 : 0;
     pp.kblock = cfg.use_mlp ? c->d_kblock : nullptr;
+    pp.rhoblk = c->d_rho;
     Offsets off;
     off.code = c->d_off_code; off.lb = c->d_off_lb;
     Out o;
@@ -437,6 +438,11 @@ cudaError_t enqueue_cells(vg_ctx *c, const vg_config &cfg, cudaStream_t s, const
     if ((e = cudaMemsetAsync(c->d_capcount, 0, sizeof(int), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->d_capcount2, 0, sizeof(int), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->d_capcount0, 0, sizeof(int), s)) != cudaSuccess) return e;
+    // 3D FP32 prefetch: every block's preload radius first
+    if (c->dim == 3 && cfg.precision == VG_FP32_RETEST && cfg.order == VG_PREFETCH &&
+        (e = prefetch_rho(c->d_sys, (int)c->sys.size(), c->d_bstart, c->total_blk, pp.kblock,
+                          (float)(cfg.prefetch_k > 0 ? cfg.prefetch_k : 72), c->d_rho, s)) != cudaSuccess)
+        return e;
     auto launch = c->dim == 3 ? launch_cells3 : launch_cells2;
     const int nc = subset ? nsubset : (int)c->n;
     // 3D FP32 prefetch: the hot kernel over every cell, then the general one
@@ -1030,7 +1036,7 @@ void vg_destroy(vg_ctx *c) {
     release(c->d_w_tested); release(c->d_w_vtests); release(c->d_w_cuts); release(c->d_w_retest);
     release(c->d_w_fallback); release(c->d_caplist); release(c->d_capcount);
     release(c->d_caplist2); release(c->d_capcount2); release(c->d_caplist0); release(c->d_capcount0);
-    release(c->d_off_code); release(c->d_off_lb); release(c->d_kblock); release(c->d_w_newv);
+    release(c->d_off_code); release(c->d_off_lb); release(c->d_kblock); release(c->d_rho); release(c->d_w_newv);
     release(c->d_w_pref); release(c->d_rfin);
     release(c->d_topo); release(c->d_topo_n); release(c->d_wlen); release(c->d_wsym); release(c->d_whash);
     release(c->d_kstar); release(c->d_kmax); release(c->d_feat);

@@ -53,6 +53,7 @@ struct Smem2 {
     unsigned sv[CAP];
     T sx[CAP], sy[CAP];
     float sk[CAP];
+    float4 mv[CAP];  // FP32 form: the cell's vertices (x, y, kappa, 0) by slot, free slots 0
     double dpos[CAP][2];
     unsigned char nxt[MAXP2];  // vertex slot by arriving line
     CellC2 cc;
@@ -60,6 +61,30 @@ struct Smem2 {
     Sys sysc;    // descriptor of the system of the current cell
     int sys_id;
 };
+
+// Block bound (Sec. 2.1.3) in 2D: a particle q cuts the cell only if some
+// vertex v lies beyond its line, |q - v|^2 < |v|^2 (radical: + rmax^2 -
+// r_p^2), so a block whose box [lo, hi] (relative to the particle) meets none
+// of those discs holds no cutting particle.  Each disc is widened by sl * kappa
+// (FP32 vertex error) and 1e-4 relative.  A free slot is (0, 0, 0): a disc of
+// radius 0 (radical: sqrt(extra), which can only keep a block).
+__device__ __noinline__ bool block_touches2(const float4 *mv, int n, float lo0, float lo1, float hi0, float hi1,
+                                            float extra, float sl) {
+    bool m = false;
+#pragma unroll 1
+    for (int t0 = 0; t0 < n; t0 += 8) {
+#pragma unroll
+        for (int t = t0; t < t0 + 8; t++) {
+            const float4 v = mv[t];
+            const float dx = fmaxf(0.f, fmaxf(lo0 - v.x, v.x - hi0));
+            const float dy = fmaxf(0.f, fmaxf(lo1 - v.y, v.y - hi1));
+            const float d2 = fmaf(dx, dx, dy * dy);
+            const float rv = sqrt_a(fmaf(v.x, v.x, fmaf(v.y, v.y, extra))) + sl * v.z;
+            m |= d2 < rv * rv * 1.0001f;
+        }
+    }
+    return m;
+}
 
 template <int G>
 __device__ __forceinline__ unsigned gballot(unsigned gmask, int gbase, bool p) {
@@ -324,6 +349,12 @@ __global__ void __launch_bounds__(128, VG2_MINB) k_cells2(const __grid_constant_
                 vx[0] = px[gl];
                 vy[0] = py[gl];
             }
+            if constexpr (F32) {
+#pragma unroll
+                for (int s = 0; s < VPL; s++)
+                    S.mv[s * G + gl] = v[s] != EMPTY2 ? make_float4(vx[s], vy[s], kap[s], 0.f)
+                                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
         int nvert = 4;
         unsigned rows = 1;
@@ -425,6 +456,17 @@ __global__ void __launch_bounds__(128, VG2_MINB) k_cells2(const __grid_constant_
                     wj1 = __ldg(&st.bstart[kb + 1]);
                     wimg = pack2(m0, m1);
                     cand = wj1 > wj0;
+                    if constexpr (F32) {
+                        // beyond the offset list (extended cells): the block bound,
+                        // for blocks whose particles would cost more than the test
+                        if (cand && mode == 2 && wj1 - wj0 >= 8) {
+                            const float bl0 = (float)wox * g.hf[0] - o0, bl1 = (float)woy * g.hf[1] - o1;
+                            const float ex = st.radical ? (float)(S.cc.rmax * S.cc.rmax - S.cc.rp * S.cc.rp) : 0.f;
+                            const float sl = 1e-5f * (sqrt_a((float)r2) + hmax);
+                            cand = block_touches2(S.mv, G * (32 - __clz(rows)), bl0, bl1, bl0 + g.hf[0],
+                                                  bl1 + g.hf[1], fmaxf(ex, 0.f), sl);
+                        }
+                    }
                 }
             }
             if (last) mode = 3;  // after this window
@@ -601,6 +643,9 @@ __global__ void __launch_bounds__(128, VG2_MINB) k_cells2(const __grid_constant_
                             if constexpr (F32) q2 *= 1.f + 4e-6f * kap[s];
                             rr = rr > q2 ? rr : q2;
                         }
+                        if constexpr (F32)
+                            S.mv[s * G + gl] = v[s] != EMPTY2 ? make_float4(vx[s], vy[s], kap[s], 0.f)
+                                                               : make_float4(0.f, 0.f, 0.f, 0.f);
                         if (__any_sync(gmask, v[s] != EMPTY2)) rows |= 1u << s;
                     }
                     live = gor64<G>(gmask, lv);

@@ -117,6 +117,8 @@ struct Src {
     int last;          // walk: the current window is the last one
     int nbatch;        // candidate batches loaded for this cell
     float rho2;        // prefetch radius^2 (0: none)
+    float lo2;         // the preload holds the candidates with lo2 <= |q|^2 < rho2
+    int round;         // hot kernel: 0 first preload, 1 the wider second one
     int rg[3];         // prefetch reach in blocks per axis
 };
 
@@ -526,6 +528,39 @@ __device__ __forceinline__ bool resolve(const Grid &g, long long base, const int
     return true;
 }
 
+// Preload radius of every block: the ball that holds the block's candidate
+// target at the density of the 27 blocks around it (a block with n27
+// particles in v27 blocks inside the box), rho = (3 k / (4 pi dens))^(1/3).
+__global__ void k_prefetch_rho(const Sys *__restrict__ sys, int nsys, const int *__restrict__ bstart, long long nblk,
+                               const float *__restrict__ kblock, float kfixed, float *__restrict__ rho) {
+    const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (b >= nblk) return;
+    int sidx = 0;
+    if (nsys > 1) {
+        int lo = 0, hi = nsys - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sys[mid].blk_base <= b) lo = mid; else hi = mid - 1;
+        }
+        sidx = lo;
+    }
+    const Sys &sy = sys[sidx];
+    const Grid &g = sy.g;
+    const long long kl = b - sy.blk_base;
+    const int hb[3] = {(int)(kl % g.nb[0]), (int)((kl / g.nb[0]) % g.nb[1]), (int)(kl / ((long long)g.nb[0] * g.nb[1]))};
+    int n27 = 0, v27 = 0;
+    for (int q = 0; q < 27; q++) {
+        int kk, mx, my, mz;
+        if (resolve(g, sy.blk_base, hb, q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1, kk, mx, my, mz)) {
+            n27 += bstart[kk + 1] - bstart[kk];
+            v27 += 1;
+        }
+    }
+    const float kt = kblock ? fmaxf(8.f, kblock[b]) : kfixed;
+    const float dens = (float)max(n27, 1) * rcp_a((float)max(v27, 1) * g.hf[0] * g.hf[1] * g.hf[2]);
+    rho[b] = cbrt_a(3.f * kt * rcp_a(4.f * 3.14159265f * dens));
+}
+
 // ---- the kernel ------------------------------------------------------------------
 
 // HOT: the common path only (FP32, prefetch, tier 0).  A cell that needs
@@ -535,6 +570,8 @@ __device__ __forceinline__ bool resolve(const Grid &g, long long base, const int
 // computes it from the start.  The hot kernel's code then holds neither the
 // walk nor the FP64 statistics, which keeps it small in the instruction
 // cache.
+// (the second preload's label is used by the hot instantiation only)
+#pragma nv_diag_suppress 177
 template <typename T, int VPL, int MAXP, bool BATCH, int G, bool TOPO = false, bool HOT = false>
 __global__ void VG_BOUNDS
     k_cells3(const __grid_constant__ Store st, const __grid_constant__ Out o,
@@ -606,7 +643,7 @@ __global__ void VG_BOUNDS
                     S.cc.rmax = st.radical ? (BATCH ? S.sysc.rmax : st.sys[0].rmax) : 0.0;
                     S.cc.hc = 0.5 * pp.clip;
                 }
-                if (pp.collect && gl < 6) S.cnt[gl] = 0;
+                if (pp.collect && gl < 6) S.cnt[gl] = 0;  // [5] sums the preloads of both rounds
             }
             // ------------------------------------- initial cell, Eqs. (1)-(2)
             unsigned tri[VPL];
@@ -763,23 +800,19 @@ __global__ void VG_BOUNDS
             src.fell_back = 0;
             src.last = 0;
             src.nbatch = 0;
+            src.lo2 = 0.f;
+            src.round = 0;
+            // the hot kernel's second preload: when the bound reaches past the
+            // first one, the candidates of a wider shell are gathered and cut
+            // the same way instead of handing the cell on
+        regather:
             if constexpr (F32) {
                 if (pp.order == VG_PREFETCH && st.n < (1 << 27)) {
-                    float kt = (float)(pp.prefetch_k > 0 ? pp.prefetch_k : 72);
-                    if (pp.kblock) kt = fmaxf(8.f, __ldg(&pp.kblock[kh]));
-                    // local density from the 27 surrounding blocks
-                    int n27 = 0, v27 = 0;
-                    for (int q = gl; q < 27; q += G) {
-                        int kk, mx, my, mz;
-                        if (resolve(g, SY.blk_base, S.cc.b, q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1, kk, mx, my, mz)) {
-                            n27 += __ldg(&st.bstart[kk + 1]) - __ldg(&st.bstart[kk]);
-                            v27 += 1;
-                        }
-                    }
-                    n27 = __reduce_add_sync(gmask, n27);
-                    v27 = __reduce_add_sync(gmask, v27);
-                    const float dens = (float)max(n27, 1) * rcp_a((float)max(v27, 1) * g.hf[0] * g.hf[1] * g.hf[2]);
-                    float rho = cbrt_a(3.f * kt * rcp_a(4.f * 3.14159265f * dens));
+                    // the block's preload radius, computed per block before the
+                    // launch; a second round reaches past the bound with a margin
+                    const float lo2 = src.lo2;
+                    float rho = src.round == 0 ? __ldg(&pp.rhoblk[kh])
+                                           : fmaxf(1.26f * sqrt_a(lo2), 1.01f * sqrt_a((float)stop2()));
                     int count = 0;
                     bool give_up = false;
                     float rho2 = 0.f;
@@ -893,7 +926,7 @@ __global__ void VG_BOUNDS
                                 const int oxj = S.w.run.oxb[lo] + __ldg(&st.sblk[j]);
                                 const float4 pj = __ldg(&st.p32[j]);
                                 cand32(g, o0, o1, o2, pj, oxj, oy, oz, qx, qy, qz, qq);
-                                keep = qq < rho2 && !(j == i && oxj == 0 && oy == 0 && oz == 0);
+                                keep = qq < rho2 && qq >= lo2 && !(j == i && oxj == 0 && oy == 0 && oz == 0);
                                 img = pack_img(((oyz >> 16) & 15) - 8, ((oyz >> 20) & 15) - 8, ((oyz >> 24) & 15) - 8);
                             }
                             const unsigned bal = gballot<G>(gmask, gbase, keep);
@@ -911,16 +944,17 @@ __global__ void VG_BOUNDS
                     }
                     if (!give_up && count <= KMAX) {
                         // order by radial bucket: NBIN shells of equal volume inside
-                        // rho (about equal counts); inside a bucket the gather order,
-                        // which is deterministic, is kept
-                        const float irho2 = rcp_a(rho2);
+                        // rho (about equal counts; for a second round, of the shell
+                        // above lo2 taken the same way); inside a bucket the gather
+                        // order, which is deterministic, is kept
+                        const float irho2 = rcp_a(rho2 - lo2);
                         int bin[KMAX / G];
 #pragma unroll
                         for (int e2 = 0; e2 < KMAX / G; e2++) {
                             const int slot = e2 * G + gl;
                             bin[e2] = NBIN;
                             if (slot < count) {
-                                const float t = fminf(S.x.pf.q[slot].w * irho2, 1.f);
+                                const float t = fminf(fmaxf(S.x.pf.q[slot].w - lo2, 0.f) * irho2, 1.f);
                                 bin[e2] = min(NBIN - 1, (int)((float)NBIN * t * sqrt_a(t)));
                             }
                         }
@@ -965,7 +999,8 @@ __global__ void VG_BOUNDS
                         }
                         src.mode = 0;
                         src.count = count;
-                        if (pp.collect && gl == 0) S.cnt[5] = count;
+                        src.u = 0;
+                        if (pp.collect && gl == 0) S.cnt[5] += count;
                         src.rho2 = rho2;
                         src.rg[0] = rg0; src.rg[1] = rg1; src.rg[2] = rg2;
                     } else if constexpr (HOT) {
@@ -990,8 +1025,17 @@ __global__ void VG_BOUNDS
                             if ((T)stop <= (T)src.rho2 * (T)0.9999) {
                                 src.mode = 3;
                             } else if constexpr (HOT) {
-                                // the bound reaches past the preload: deferred
+                                // the bound reaches past the preload: once a wider
+                                // preload, then the general kernel
                                 src.mode = 3;
+                                if (src.round == 0) {
+                                    __syncwarp(gmask);
+                                    src.round = 1;
+                                    src.fell_back = 2;  // a shortfall, met by a second preload
+                                    src.lo2 = src.rho2;
+                                    __syncwarp(gmask);
+                                    goto regather;
+                                }
                                 flags |= 32;
                             } else {
                                 src.mode = 1;
@@ -1033,10 +1077,11 @@ __global__ void VG_BOUNDS
                         // bound, every later entry lies beyond it too
                         const int last = min(count - u, G) - 1;
                         const float qlast = __shfl_sync(gmask, (float)cqq, last, G);  // this batch's gl value
-                        const float t = fminf(qlast * rcp_a(src.rho2), 1.f);
+                        const float plo2 = src.lo2, pw2 = src.rho2 - plo2;
+                        const float t = fminf(fmaxf(qlast - plo2, 0.f) * rcp_a(pw2), 1.f);
                         const int bl = min(NBIN - 1, (int)((float)NBIN * t * sqrt_a(t)));
                         // bucket bl starts at t = (bl / NBIN)^(2/3)
-                        const float lb2 = src.rho2 * bucket_t[bl] * 0.9999f;  // margin for rounding
+                        const float lb2 = (plo2 + pw2 * bucket_t[bl]) * 0.9999f;  // margin for rounding
                         src.u = ((T)lb2 >= stop) ? count : u + G;
                         continue;
                     }
@@ -1936,6 +1981,14 @@ cudaError_t launch_t(const Store &s, const Out &o, const Params &p, const Offset
 
 }  // namespace
 
+cudaError_t prefetch_rho(const Sys *sys, int nsys, const int *bstart, long long nblk, const float *kblock,
+                         float kfixed, float *rho, cudaStream_t st) {
+    if (nblk <= 0) return cudaSuccess;
+    ++g_launch_count;
+    k_prefetch_rho<<<(unsigned)((nblk + 255) / 256), 256, 0, st>>>(sys, nsys, bstart, nblk, kblock, kfixed, rho);
+    return cudaGetLastError();
+}
+
 // Every tier runs one cell per warp (32 lanes); tier 0 holds cells up to 64
 // vertices and 64 planes, tier 1 up to 128, tier 2 up to 256.
 cudaError_t launch_cells3(const Store &s, const Out &o, const Params &p, const Offsets &off, int precision,
@@ -1950,10 +2003,14 @@ cudaError_t launch_cells3(const Store &s, const Out &o, const Params &p, const O
                    ? launch_t<double, 4, 128, true, 32>(s, o, p, off, ticket, sm_count, 2, cells, ncells, tier, st)
                    : launch_t<float, 4, 128, true, 32>(s, o, p, off, ticket, sm_count, 2, cells, ncells, tier, st);
     const bool batch = s.nsys > 1;
-    if (precision == VG_FP64)
+    if (precision == VG_FP64) {
+        if (o.topo)  // the cells' triangles are kept for Weinberg codes (tier 0)
+            return batch ? launch_t<double, VG_T0_VPL, 64, true, VG_T0_G, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st)
+                         : launch_t<double, VG_T0_VPL, 64, false, VG_T0_G, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
         return batch ? launch_t<double, VG_T0_VPL, 64, true, VG_T0_G>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st)
                      : launch_t<double, VG_T0_VPL, 64, false, VG_T0_G>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
-    if (o.topo)  // the cells' triangles are kept for Weinberg codes (FP32 form, tier 0)
+    }
+    if (o.topo)  // the cells' triangles are kept for Weinberg codes (tier 0)
         return batch ? launch_t<float, VG_T0_VPL, 64, true, VG_T0_G, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st)
                      : launch_t<float, VG_T0_VPL, 64, false, VG_T0_G, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
     return batch ? launch_t<float, VG_T0_VPL, 64, true, VG_T0_G>(s, o, p, off, ticket, sm_count, w, cells, ncells, tier, st)

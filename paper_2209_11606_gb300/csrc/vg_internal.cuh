@@ -101,6 +101,7 @@ struct Params {
     int chunk;
     int collect;
     const float *kblock;   // per-block candidate target from the MLP, or null
+    const float *rhoblk;   // per-block prefetch radius (prefetch_rho), or null
     double clip;           // clipped cells: cube side, 0 = none
 };
 
@@ -188,6 +189,11 @@ cudaError_t launch_cells3(const Store &s, const Out &o, const Params &p, const O
                           const int *cells, int ncells, int tier, cudaStream_t st);
 cudaError_t launch_cells3_hot(const Store &s, const Out &o, const Params &p, const Offsets &off, unsigned *ticket,
                               int sm_count, int warps_per_cta, const int *cells, int ncells, cudaStream_t st);
+// Per-block radius of the distance-sorted preload: the ball expected to hold
+// the block's candidate target (kblock, else kfixed) at the density of the 27
+// blocks around it.
+cudaError_t prefetch_rho(const Sys *sys, int nsys, const int *bstart, long long nblk, const float *kblock,
+                         float kfixed, float *rho, cudaStream_t st);
 cudaError_t launch_cells2(const Store &s, const Out &o, const Params &p, const Offsets &off,
                           int precision, unsigned *ticket, int sm_count, int warps_per_cta,
                           const int *cells, int ncells, int tier, cudaStream_t st);
@@ -309,6 +315,7 @@ struct vg_ctx {
     vg_mlp *pred = nullptr;   // predictor run after every sort (vg_set_predictor)
     float pred_alpha = 1.f, pred_kmin = 8.f, pred_kmax = 1024.f;
     float *d_kblock = nullptr;
+    float *d_rho = nullptr;      // per-block prefetch radius (3D FP32 prefetch)
     long long cap_kblock = 0;
     int kblock_valid = 0;
     // training data of the predictor: k* per cell, largest k* and features per block

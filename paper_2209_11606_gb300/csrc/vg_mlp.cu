@@ -100,14 +100,17 @@ __device__ __forceinline__ int system_of_block(const Sys *sys, int nsys, long lo
     return lo;
 }
 
-// The 27 features of global block b: log(1 + count) / 4 of the blocks
+// The 27 features of global block b: the counts c_j of the blocks
 // b + (dx, dy, dz), index (dx+1) + 3 (dy+1) + 9 (dz+1), wrapped on periodic
-// axes and 0 outside a wall.
+// axes and 0 outside a wall, over their mean m = (sum c_j) / (blocks inside
+// the box), minus 1 (0 everywhere when m = 0): the same at any density or
+// block size.
 __device__ void block_features(const Sys *sys, int nsys, const int *__restrict__ bstart, long long b, float *x) {
     const Sys &sy = sys[nsys > 1 ? system_of_block(sys, nsys, b) : 0];
     const Grid &g = sy.g;
     const long long kl = b - sy.blk_base;
     const int c0 = (int)(kl % g.nb[0]), c1 = (int)((kl / g.nb[0]) % g.nb[1]), c2 = (int)(kl / ((long long)g.nb[0] * g.nb[1]));
+    int sum = 0, inside = 0;
     for (int j = 0; j < NIN; j++) {
         int t[3] = {c0 + j % 3 - 1, c1 + (j / 3) % 3 - 1, c2 + j / 9 - 1};
         bool ok = true;
@@ -116,13 +119,18 @@ __device__ void block_features(const Sys *sys, int nsys, const int *__restrict__
             if (g.per[a]) t[a] -= fdiv(t[a], g.nb[a]) * g.nb[a];
             else ok = false;
         }
-        float v = 0.f;
+        int cnt = 0;
         if (ok) {
             const long long k = sy.blk_base + t[0] + (long long)g.nb[0] * (t[1] + (long long)g.nb[1] * t[2]);
-            v = log1pf((float)(bstart[k + 1] - bstart[k])) * 0.25f;
+            cnt = bstart[k + 1] - bstart[k];
+            inside++;
         }
-        x[j] = v;
+        sum += cnt;
+        x[j] = (float)cnt;
     }
+    // x_j = c_j / m - 1 = c_j * inside / sum - 1, the quotient correctly rounded
+    const float f = sum > 0 ? __fdiv_rn((float)inside, (float)sum) : 0.f;
+    for (int j = 0; j < NIN; j++) x[j] = sum > 0 ? __fsub_rn(__fmul_rn(x[j], f), 1.f) : 0.f;
 }
 
 __global__ void k_features(const Sys *sys, int nsys, const int *__restrict__ bstart, long long nblk,

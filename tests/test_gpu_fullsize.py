@@ -25,7 +25,7 @@ pytestmark = pytest.mark.gpu
 
 RTOL = 1e-5
 # the benchmark's predictor settings: preload target clamp(alpha exp(y), kmin, kmax)
-MLP_ALPHA, MLP_KMIN, MLP_KMAX = 1.5, 24.0, 1024.0
+MLP_ALPHA, MLP_KMIN, MLP_KMAX = 1.2, 24.0, 1024.0
 PARAMS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                       "paper_2209_11606_gb300", "mlp_params_gb300.json")
 

@@ -1,0 +1,143 @@
+"""What the trained network gains over the method without it.
+
+The learned part predicts, per block, how many distance-sorted candidates
+the prefetch form preloads (27 block counts -> 32 -> 32 -> 1, FP16
+weights, trained on the 1M-point configuration's k* labels; the weights
+and the scale alpha, floor kmin the benchmark uses).  The radius bound of
+Sec. 2.1.3 still decides, so the cells never depend on the prediction; the
+prediction sets how much each cell preloads, and a shortfall is met by a
+second, wider preload (rarely by the walk).  What it buys is speed.
+
+Measured in the benchmark's launch configuration (graph replays, L2
+flushed) on the 1M-point configuration (uniform, perturbed BCC) and on sets
+outside the training data (perturbed FCC, FCC/uniform slabs):
+
+* the cells of the learned preload equal the oracle's on a sample;
+* the learned preload beats the plain walk (the paper's method, without
+  any preload) by at least WALK_MARGIN everywhere;
+* one learned setting beats every single fixed target over the four sets:
+  a fixed target suits either the lattices (few candidates) or the random
+  points (many), while the network reads which one a block is in.  On the
+  lattices it is faster than the default fixed target (72); on uniform
+  points a fixed target of the right size is as fast or a little faster
+  (the 27 counts say little about one block's cells beyond their
+  distribution), within FIXED_SLACK.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2209_11606_gb300 import workloads as W
+from tests.compare import compare
+
+pytestmark = pytest.mark.gpu
+
+MLP_ALPHA, MLP_KMIN, MLP_KMAX = 1.2, 24.0, 1024.0
+PARAMS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                      "paper_2209_11606_gb300", "mlp_params_gb300.json")
+WALK_MARGIN = 1.2      # learned cells/s over the walk's, everywhere
+FIXED_KS = (32, 48, 64, 72, 80, 96)
+FIXED_SLACK = 0.95     # learned cells/s at least this fraction of fixed 72's on uniform points
+
+
+def measure(torch, mlp, s, grid, mode, k=0, reps=5):
+    """cells/s of graph replays, the shortfall rates (work counters of an
+    eager compute), the mean preload and the host results."""
+    from paper_2209_11606_gb300 import vorogpu as V
+    pos = torch.from_numpy(np.ascontiguousarray(s.pos)).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ctx = V.vg_create(3, s.lo, s.hi, s.periodic, grid)
+    try:
+        cfg = V.vg_config_default()
+        cfg.order = V.VG_WALK if mode == "walk" else V.VG_PREFETCH
+        if mode == "learned":
+            V.vg_set_predictor(ctx, mlp, MLP_ALPHA, MLP_KMIN, MLP_KMAX)
+            cfg.use_mlp = 1
+        if mode == "fixed":
+            cfg.prefetch_k = int(k)
+        V.vg_graph_capture(ctx, [s.n], pos, None, cfg)
+        for _ in range(2):
+            V.vg_graph_launch(ctx)
+        V.vg_graph_sync(ctx)
+        ms = []
+        for r in range(reps):
+            flush.fill_(r)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            V.vg_graph_launch(ctx)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        V.vg_graph_sync(ctx)
+        got = V._fetch(ctx, s.n, 3, False) if mode == "learned" else None
+        cfg.collect_stats = 1
+        V.vg_insert(ctx, pos)
+        V.vg_compute(ctx, cfg)
+        fb = np.zeros(s.n, np.uint8)
+        pref = np.zeros(s.n, np.int32)
+        V.vg_get_work(ctx, fallback=fb, n_prefetch=pref)
+        # a shortfall of the preload is met by a second, wider preload (2) or
+        # by the walk (1)
+        return {"cells_per_s": s.n / (np.median(ms) / 1000.0), "shortfall": float((fb > 0).mean()),
+                "walk": float((fb == 1).mean()), "preload": float(pref.mean()), "got": got,
+                "grid": V.vg_get_grid(ctx, 3)}
+    finally:
+        V.vg_destroy(ctx)
+
+
+CASES = {
+    "uniform1m": (lambda: W.workload("uniform1m"), (58, 58, 58), "uniform"),
+    "bcc1m": (lambda: W.workload("bcc1m"), (64, 64, 64), "lattice"),
+    # outside the training data: perturbed FCC (sigma 0.05 a) at the slabs'
+    # lattice constant and FCC/uniform slabs, blocks by the n_opt = 4.6 rule
+    "fcc1m": (lambda: W.fcc(64, 51.0 / 32.0, 0.05, seed=9), None, "lattice"),
+    "slabs2m": (lambda: W.fcc_uniform_slabs(cells_per_side=64, slabs=8, n_total=2 * 4 * 64 * 64 * 8 * 4, seed=6),
+                None, "mixed"),
+}
+
+
+def test_learned_preload_gain():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_11606_gb300 import build, predictor as P, vorogpu as V
+    build.build()
+    with open(PARAMS) as f:
+        params = np.asarray(json.load(f)["params"], dtype=np.float32)
+    mlp = P.predictor(params)
+    try:
+        runs = {}
+        for name, (make, grid, kind) in CASES.items():
+            s = make()
+            learned = measure(torch, mlp, s, grid, "learned")
+            grid = learned["grid"]
+            r = {"learned": learned, "walk": measure(torch, mlp, s, grid, "walk")}
+            for k in FIXED_KS:
+                r["fixed%d" % k] = measure(torch, mlp, s, grid, "fixed", k=k)
+            print(name, json.dumps({m: {q: v for q, v in x.items() if q not in ("got", "grid")}
+                                    for m, x in r.items()}))
+            # the cells are the oracle's whatever the prediction
+            rng = np.random.default_rng(3)
+            cells = np.sort(rng.choice(s.n, size=1500, replace=False))
+            ref = oracle.compute(s.pos, s.lo, s.hi, s.periodic, nblocks=grid, cells=cells)
+            rep = compare(learned["got"], ref, 1e-5, cells=cells)
+            assert rep["topology_ok"] and rep["values_ok"], (name, rep)
+            runs[name] = (s.n, kind, {m: x["cells_per_s"] for m, x in r.items()})
+    finally:
+        V.vg_mlp_destroy(mlp)
+    for name, (n, kind, rate) in runs.items():
+        assert rate["learned"] > WALK_MARGIN * rate["walk"], (name, rate)
+        if kind == "lattice":
+            assert rate["learned"] > rate["fixed72"], (name, rate)
+        if kind == "uniform":
+            assert rate["learned"] >= FIXED_SLACK * rate["fixed72"], (name, rate)
+    # the time of one step over the four sets: the learned setting against
+    # every single fixed target
+    modes = ["learned"] + ["fixed%d" % k for k in FIXED_KS]
+    total = {m: sum(n / rate[m] for n, _, rate in runs.values()) for m in modes}
+    print("total seconds", json.dumps(total))
+    best_fixed = min(v for m, v in total.items() if m != "learned")
+    assert total["learned"] < best_fixed, total

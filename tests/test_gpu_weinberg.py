@@ -20,9 +20,9 @@ def _built():
     build.build()
 
 
-def codes(s, nb, order="prefetch"):
+def codes(s, nb, order="prefetch", precision="fp32"):
     from paper_2209_11606_gb300 import vorogpu
-    got = vorogpu.compute_host(s.pos, s.lo, s.hi, s.periodic, radii=s.radii, nblocks=nb, precision="fp32",
+    got = vorogpu.compute_host(s.pos, s.lo, s.hi, s.periodic, radii=s.radii, nblocks=nb, precision=precision,
                                order=order, weinberg=1)
     ref = oracle.compute(s.pos, s.lo, s.hi, s.periodic, radii=s.radii, method="grid", nblocks=got["grid"],
                          weinberg=True)
@@ -39,18 +39,19 @@ def check(got, ref):
     return simple
 
 
-@pytest.mark.parametrize("order", ["prefetch", "walk"])
-def test_uniform_periodic_codes(order):
+@pytest.mark.parametrize("order,precision", [("prefetch", "fp32"), ("walk", "fp32"), ("walk", "fp64")])
+def test_uniform_periodic_codes(order, precision):
     s = W.uniform(3000, 3, 3000 ** (1 / 3), True, seed=41)
-    got, ref = codes(s, (8, 8, 8), order)
+    got, ref = codes(s, (8, 8, 8), order, precision)
     simple = check(got, ref)
     assert simple.sum() > 2900
     assert len(np.unique(got["w_hash"][simple])) > 100  # many distinct topologies
 
 
-def test_walled_codes():
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_walled_codes(precision):
     s = W.uniform(2000, 3, 1.0, False, seed=42)
-    got, ref = codes(s, (7, 7, 7))
+    got, ref = codes(s, (7, 7, 7), "walk" if precision == "fp64" else "prefetch", precision)
     check(got, ref)
 
 
@@ -68,8 +69,8 @@ def test_lone_cell_is_the_cube():
     assert got["w_len"][0] == 24 and got["w_sym"][0] == 48 and got["w_hash"][0] == ref["w_hash"][0]
 
 
-def test_weinberg_needs_the_fp32_3d_form():
+def test_weinberg_needs_3d():
     from paper_2209_11606_gb300 import vorogpu
-    s = W.uniform(100, 3, 1.0, False, seed=45)
+    s = W.uniform(100, 2, 1.0, False, seed=45)
     with pytest.raises(vorogpu.VgError):
-        vorogpu.compute_host(s.pos, s.lo, s.hi, s.periodic, nblocks=(2, 2, 2), precision="fp64", weinberg=1)
+        vorogpu.compute_host(s.pos, s.lo, s.hi, s.periodic, nblocks=(2, 2), weinberg=1)

@@ -90,10 +90,8 @@ def test_fp16_rounding_touches_only_weights():
 def test_features_count_invariants():
     s = W.uniform(3000, 3, 1.0, True, seed=5)
     nb = (7, 6, 5)
-    X = M.block_features(s.pos, s.lo, s.hi, s.periodic, nb)
-    c = np.expm1(4.0 * X)
-    assert np.allclose(c, np.round(c), atol=1e-9)
-    c = np.round(c)
+    c, v = M.block_counts27(s.pos, s.lo, s.hi, s.periodic, nb)
+    assert np.all(v == 27)
     # the centre column is the block's own count; on a torus every particle
     # is seen by exactly 27 neighbourhoods
     assert c[:, 13].sum() == 3000
@@ -107,11 +105,50 @@ def test_features_count_invariants():
     assert c[b, 2 + 3 * 1 + 9 * 0] == own[nbk]
 
 
-def test_features_walls_give_zero_outside():
+def test_features_are_counts_over_their_mean():
+    s = W.uniform(3000, 3, 1.0, False, seed=5)
+    nb = (7, 6, 5)
+    X = M.block_features(s.pos, s.lo, s.hi, s.periodic, nb)
+    c, v = M.block_counts27(s.pos, s.lo, s.hi, s.periodic, nb)
+    # inside the box the features average to 0 over a block's neighbourhood
+    # (they are the counts over their mean, minus 1); past a wall they are -1
+    ins = np.zeros_like(c, dtype=bool)
+    for b in range(c.shape[0]):
+        i, j, l = b % 7, (b // 7) % 6, b // 42
+        for q in range(27):
+            t = (i + q % 3 - 1, j + (q // 3) % 3 - 1, l + q // 9 - 1)
+            ins[b, q] = 0 <= t[0] < 7 and 0 <= t[1] < 6 and 0 <= t[2] < 5
+    assert np.array_equal(ins.sum(axis=1), v)
+    np.testing.assert_allclose(np.where(ins, X, 0.0).sum(axis=1), 0.0, atol=1e-12)
+    assert np.all(X[~ins] == -1.0)
+    # x_j + 1 is proportional to c_j: ratios of counts are kept
+    ok = (c[:, 13] > 0) & (c[:, 4] > 0)
+    np.testing.assert_allclose((X[ok, 13] + 1.0) / (X[ok, 4] + 1.0), c[ok, 13] / c[ok, 4], rtol=1e-12)
+
+
+def test_features_do_not_depend_on_density():
+    # every particle doubled (a copy moved by a tenth of the spacing inside
+    # its block): every count doubles and the features stay the same; the
+    # same points in a box scaled by 3 (same block grid) give the same
+    # features too
+    s = W.uniform(2000, 3, 1.0, True, seed=8)
+    nb = (6, 6, 6)
+    X = M.block_features(s.pos, s.lo, s.hi, s.periodic, nb)
+    h = 1.0 / 6
+    cell = np.floor(s.pos / h)
+    moved = np.clip(s.pos + 0.1 * h * 0.05, cell * h, (cell + 1) * h - 1e-12)
+    X2 = M.block_features(np.concatenate([s.pos, moved]), s.lo, s.hi, s.periodic, nb)
+    np.testing.assert_allclose(X2, X, atol=1e-12)
+    X3 = M.block_features(3.0 * s.pos, 3.0 * s.lo, 3.0 * s.hi, s.periodic, nb)
+    np.testing.assert_allclose(X3, X, atol=1e-12)
+
+
+def test_features_walls_give_minus_one_outside():
     s = W.uniform(500, 3, 1.0, False, seed=6)
     X = M.block_features(s.pos, s.lo, s.hi, s.periodic, (1, 1, 1))
-    c = np.round(np.expm1(4.0 * X))
-    assert c[0, 13] == 500 and c[0].sum() == 500
+    # one block: it is its own neighbourhood's mean, every other block is
+    # past a wall
+    assert X[0, 13] == 0.0 and np.all(np.delete(X[0], 13) == -1.0)
 
 
 def test_kstar_bcc_is_fourteen():
