@@ -65,6 +65,9 @@ WORKLOADS = {
     "extreme3d": ("extreme3d: 10^8 points, each coordinate 1/2 + 4 (X - 1/2)^3 (seed 13), walled unit cube, "
                   "584^3 blocks (Table 3, n_opt 0.5); chosen form = FP32 cuts + FP64 re-test, "
                   "distance-sorted preload (72)"),
+    # VoroTop's case (Sec. 4): cells with Weinberg codes (run with --weinberg)
+    "vorotop102m": ("vorotop102m: 102,400,000 points uniform in the periodic unit cube (seed 17), blocks by the "
+                    "n_opt = 4.6 rule; chosen form = FP32 cuts + FP64 re-test, distance-sorted preload (72)"),
     # the same three cases in 2D (Table 3 grids)
     "homog2d": ("homog2d: 10^8 points uniform in the walled unit square (seed 14), 5423^2 blocks (Table 3, "
                 "n_opt 3.4); chosen form = FP32 cuts + FP64 re-test, block walk"),
@@ -90,7 +93,11 @@ FLOP_VTEST, FLOP_CAND, FLOP_NEWV, FLOP_FANTET = 6, 12, 51, 42
 # of one launch, warp instructions per cell, active lanes per instruction,
 # issue-active fraction.  An entry is removed whenever the kernel changes
 # after its capture, so only counters of the timed build are reported.
-CELL_KERNEL_NCU = {}
+CELL_KERNEL_NCU = {
+    "uniform1m": {"dram_bytes": 193917184 + 290388480, "warp_inst_per_cell": 12837.0, "lanes_per_inst": 23.54,
+                  "issue_active": 0.592, "kernel": "k_cells3<float,2,64,...,HOT> (hot kernel)",
+                  "source": "profiles/k_cells3_hot_fp32_uniform1m_ncu.md"},
+}
 MLP_ALPHA, MLP_KMIN, MLP_KMAX = 1.2, 24.0, 1024.0
 # peak warp-instruction issue rate: 152 SMs x 4 schedulers x 1 per cycle x 2.07 GHz
 ISSUE_PEAK = 152 * 4 * 2.07e9
@@ -154,6 +161,8 @@ def workload(name: str, rank: int):
         return W.localized(100_000_000, 3, 0.1, seed=12 + rank), (126,) * 3, "prefetch", False
     if name == "extreme3d":
         return W.extreme_clustering(100_000_000, 3, seed=13 + rank), (584,) * 3, "prefetch", False
+    if name == "vorotop102m":
+        return W.uniform(102_400_000, 3, 1.0, True, seed=17 + rank), None, "prefetch", False
     if name == "homog2d":
         return W.uniform(100_000_000, 2, 1.0, False, seed=14 + rank), (5423,) * 2, "walk", False
     if name == "local2d":
@@ -269,7 +278,7 @@ def batched_run(V, torch, stream, flush, mlp, steps: int = 5, seed: int = 5):
     systems = W.batched_systems(256, 1000, 200_000, seed=seed)
     t0 = time.perf_counter()
     cache = A.Cache(TUNE_CACHE)
-    key = "batched256-seed%d-split" % seed
+    key = "batched256-seed%d-split2" % seed
     tb = cache.get(key)
     if tb is None:
         tb = A.tune_batch(systems, torch, cache, predictor=mlp, mlp_args=(MLP_ALPHA, MLP_KMIN, MLP_KMAX))
@@ -504,7 +513,7 @@ def main():
     B.build()
     from paper_2209_11606_gb300 import predictor as P, vorogpu as V
 
-    big = args.workload in ("slabs102m",) + PAPER3D + PAPER2D
+    big = args.workload in ("slabs102m", "vorotop102m") + PAPER3D + PAPER2D
     s, grid, chosen_order, learned_on = workload(args.workload, rank)
     if args.grid > 0:
         grid = (args.grid,) * s.dim
@@ -624,6 +633,7 @@ def main():
         prof = CELL_KERNEL_NCU[args.workload]
         ipc = prof["warp_inst_per_cell"]
         roof["traffic"] = prof["dram_bytes"]
+        roof["traffic_kernel"] = prof["kernel"]
         roof["issue"] = {"warp_inst_per_cell": ipc,
                          "achieved_inst_per_s": ipc * n / (kern_avg_ms / 1000.0),
                          "peak_inst_per_s": ISSUE_PEAK,

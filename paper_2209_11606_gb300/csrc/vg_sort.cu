@@ -487,22 +487,47 @@ __global__ void k_nf_ok(long long n, const int *nf, const unsigned char *status,
     nf_ok[i] = ok ? nf[i] : 0;
 }
 
-// one warp per 32 cells: each lane copies its cell's faces
-__global__ void k_compact(long long n, const int *__restrict__ nf_ok,
-                          const long long *__restrict__ fptr, const int2 *__restrict__ faces,
-                          const long long *__restrict__ face_off, int *__restrict__ nbr_id,
-                          signed char *__restrict__ nbr_img, unsigned char *__restrict__ face_order) {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int k = nf_ok[i];
-    long long src = fptr[i], dst = face_off[i];
-    for (int f = 0; f < k; f++) {
-        int2 e = faces[src + f];
-        nbr_id[dst + f] = e.x;
-        nbr_img[(dst + f) * 3 + 0] = (signed char)(e.y & 0xff);
-        nbr_img[(dst + f) * 3 + 1] = (signed char)((e.y >> 8) & 0xff);
-        nbr_img[(dst + f) * 3 + 2] = (signed char)((e.y >> 16) & 0xff);
-        face_order[dst + f] = (unsigned char)((unsigned)e.y >> 24);
+// One warp per 32 consecutive cells: their faces are contiguous in the CSR
+// ([face_off[c0], face_off[c0 + 32])), so the warp walks that output range 32
+// faces at a time with coalesced stores.  In each window of 32 outputs every
+// lane (one per cell) marks in shared memory the outputs its cell owns; each
+// lane then copies the one face it writes.
+constexpr int COMPACT_THREADS = 256;
+__global__ void __launch_bounds__(COMPACT_THREADS) k_compact(long long n, const int *__restrict__ nf_ok,
+                                                            const long long *__restrict__ fptr,
+                                                            const int2 *__restrict__ faces,
+                                                            const long long *__restrict__ face_off,
+                                                            int *__restrict__ nbr_id, signed char *__restrict__ nbr_img,
+                                                            unsigned char *__restrict__ face_order) {
+    __shared__ unsigned char owner[COMPACT_THREADS / 32][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long c0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) - lane;
+    if (c0 >= n) return;  // whole warps leave together
+    const long long c = c0 + lane;
+    const bool in = c < n;
+    const long long off = in ? face_off[c] : face_off[n];
+    const int cnt = in ? nf_ok[c] : 0;
+    const long long src = in ? fptr[c] : 0;
+    const long long base = __shfl_sync(FULL, off, 0);
+    const long long end = __shfl_sync(FULL, off + cnt, 31);
+    for (long long w0 = base; w0 < end; w0 += 32) {
+        // this lane's cell covers outputs [off, off + cnt) of the window [w0, w0 + 32)
+        const long long a = off > w0 ? off : w0, b = off + cnt < w0 + 32 ? off + cnt : w0 + 32;
+        for (long long f = a; f < b; f++) owner[wib][f - w0] = (unsigned char)lane;
+        __syncwarp();
+        const long long f = w0 + lane;
+        const int o = f < end ? (int)owner[wib][lane] : 0;
+        const long long s_o = __shfl_sync(FULL, src, o);
+        const long long off_o = __shfl_sync(FULL, off, o);
+        if (f < end) {
+            const int2 e = faces[s_o + (f - off_o)];
+            nbr_id[f] = e.x;
+            nbr_img[f * 3 + 0] = (signed char)(e.y & 0xff);
+            nbr_img[f * 3 + 1] = (signed char)((e.y >> 8) & 0xff);
+            nbr_img[f * 3 + 2] = (signed char)((e.y >> 16) & 0xff);
+            face_order[f] = (unsigned char)((unsigned)e.y >> 24);
+        }
+        __syncwarp();
     }
 }
 
@@ -525,7 +550,8 @@ cudaError_t compact_faces(long long n, const int *nf, const unsigned char *statu
     k_total<int, long long><<<1, 1, 0, st>>>(nf_ok, face_off, n);
     if (n > 0) {
         ++g_launch_count;
-        k_compact<<<nbk, T, 0, st>>>(n, nf_ok, fptr, faces, face_off, nbr_id, nbr_img, face_order);
+        k_compact<<<(unsigned)((n + COMPACT_THREADS - 1) / COMPACT_THREADS), COMPACT_THREADS, 0, st>>>(
+            n, nf_ok, fptr, faces, face_off, nbr_id, nbr_img, face_order);
     }
     return cudaGetLastError();
 }
