@@ -93,11 +93,7 @@ FLOP_VTEST, FLOP_CAND, FLOP_NEWV, FLOP_FANTET = 6, 12, 51, 42
 # of one launch, warp instructions per cell, active lanes per instruction,
 # issue-active fraction.  An entry is removed whenever the kernel changes
 # after its capture, so only counters of the timed build are reported.
-CELL_KERNEL_NCU = {
-    "uniform1m": {"dram_bytes": 193917184 + 290388480, "warp_inst_per_cell": 12837.0, "lanes_per_inst": 23.54,
-                  "issue_active": 0.592, "kernel": "k_cells3<float,2,64,...,HOT> (hot kernel)",
-                  "source": "profiles/k_cells3_hot_fp32_uniform1m_ncu.md"},
-}
+CELL_KERNEL_NCU = {}
 MLP_ALPHA, MLP_KMIN, MLP_KMAX = 1.2, 24.0, 1024.0
 # peak warp-instruction issue rate: 152 SMs x 4 schedulers x 1 per cycle x 2.07 GHz
 ISSUE_PEAK = 152 * 4 * 2.07e9
@@ -405,22 +401,18 @@ def large_run(V, torch, stream, flush, mlp, steps: int = 2, with_oracle: bool = 
         torch.cuda.empty_cache()
 
 
-def weinberg_run(V, torch, ctx, pos_d, rad_d, cfg, n, reps: int = 3):
-    """Cells with and without Weinberg codes (Sec. 4): eager insert + compute,
-    host clock around synchronised calls."""
+def weinberg_run(V, torch, ctx, pos_d, rad_d, cfg, n, stream, flush, reps: int = 3):
+    """Cells with and without Weinberg codes (Sec. 4): graph replays of sort,
+    cells, codes and face CSR, CUDA events, L2 flushed before each."""
     def timed(weinberg):
         c = V.vg_config_default()
         c.precision, c.order, c.use_mlp, c.clip = cfg.precision, cfg.order, cfg.use_mlp, cfg.clip
         c.weinberg = int(weinberg)
-        V.vg_insert(ctx, pos_d, rad_d)
-        V.vg_compute(ctx, c)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            V.vg_insert(ctx, pos_d, rad_d)
-            V.vg_compute(ctx, c)
-        torch.cuda.synchronize()
-        return n * reps / (time.perf_counter() - t0)
+        V.vg_graph_capture(ctx, [n], pos_d, rad_d, c)
+        V.vg_graph_launch(ctx)
+        V.vg_graph_sync(ctx)
+        ms = graph_steps(V, torch, ctx, stream, flush, reps)
+        return n * reps / (sum(ms) / 1000.0)
     base = timed(False)
     with_codes = timed(True)
     wl, wh, ws = np.zeros(n, np.int32), np.zeros(n, np.uint64), np.zeros(n, np.int32)
@@ -428,8 +420,8 @@ def weinberg_run(V, torch, ctx, pos_d, rad_d, cfg, n, reps: int = 3):
     coded = wl > 0
     return {"cells_per_s": with_codes, "without_codes_cells_per_s": base, "unit": "cells/s",
             "coded_fraction": float(coded.mean()), "distinct_codes": int(len(np.unique(wh[coded]))),
-            "form": "eager vg_insert + vg_compute with cfg.weinberg = 1 (cells, then a warp per cell "
-                    "for its Weinberg code), host clock"}
+            "form": "graph replays with cfg.weinberg = 1 (sort, cells keeping their triangles, a warp per "
+                    "cell for its Weinberg code, face CSR), CUDA events, L2 flushed"}
 
 
 def cpu_baseline(s, grid, cells: int, seed: int = 0, clip: float = 0.0):
@@ -588,6 +580,7 @@ def main():
         w = {k: np.zeros(n, np.int32) for k in ("t", "v", "c", "nv", "r", "p")}
         fb = np.zeros(n, np.uint8)
         V.vg_get_work(ctx, w["t"], w["v"], w["c"], w["nv"], w["r"], fb, w["p"])
+        w["deferred"] = V.vg_get_deferred(ctx)
         return w, fb
 
     w, fb = work(cfg)
@@ -651,6 +644,7 @@ def main():
                    "fixed_k_shortfall_rate": float((fb_fixed > 0).mean()),
                    "fixed_k_walk_rate": float((fb_fixed == 1).mean()),
                    "fixed_k_preload_per_cell": float(w_fixed["p"].mean()),
+                   "deferred_rate": w["deferred"] / n, "fixed_k_deferred_rate": w_fixed["deferred"] / n,
                    "alpha": MLP_ALPHA, "trained": mlp_meta}
 
     # ---- the same step in other forms (graph replays) ---------------------------
@@ -721,7 +715,7 @@ def main():
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "retest_per_cell": float(w["r"].mean())}
     if args.weinberg and dim == 3:
-        line["weinberg"] = weinberg_run(V, torch, ctx, pos_d, rad_d, cfg, n)
+        line["weinberg"] = weinberg_run(V, torch, ctx, pos_d, rad_d, cfg, n, stream, flush)
     if not args.no_batched and args.workload == "uniform1m":
         line["batched"] = batched_run(V, torch, stream, flush, mlp)
     if not args.no_cpu_baseline and world == 1:

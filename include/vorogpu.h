@@ -111,12 +111,14 @@ typedef struct {
                           side).  0 (default): plain cells */
     int weinberg;      /* 1 = also the Weinberg code of every 3D cell's edge
                           graph (Sec. 4), read with vg_get_weinberg(); either
-                          form, eager vg_compute only.  Default 0 */
+                          form, vg_compute or a captured graph.  Default 0 */
     int split;         /* 3D FP32 prefetch only.  1 (default): a kernel built
                           for the common path alone computes every cell it
                           can, and hands each cell that needs the walk after
-                          its preload or FP64 statistics to the general
-                          kernel, which computes that cell from the start.
+                          its preloads, FP64 statistics, more than 64 planes
+                          or more than 32 faces to the general kernel, which
+                          computes that cell from the start (vg_get_deferred
+                          counts them).
                           0: the general kernel computes every cell (better
                           where many cells outgrow their preload, as in
                           clustered sets).  Results are the same */
@@ -294,11 +296,13 @@ vg_status vg_get_work(vg_ctx *ctx, int32_t *n_tested, int32_t *n_vtests, int32_t
 vg_status vg_get_radius(vg_ctx *ctx, float *rmax, int on_device);
 
 /*
- * Weinberg codes (Sec. 4) from the last vg_compute() with cfg.weinberg = 1,
+ * Weinberg codes (Sec. 4) from the last vg_compute() or graph replay with
+ * cfg.weinberg = 1,
  * per cell in input order (n entries each, host or device memory):
- *   len  darts traversed, 2E (E edges of the cell); 0 = no code: the cell
- *        is not OK, has vertices of degree above 3 (merged on an exact
- *        lattice) or more than 64 vertices (a larger capacity tier)
+ *   len  darts traversed, 2E (E edges of the cell's edge graph, coincident
+ *        vertices merged: on an exact lattice four or more faces meet at
+ *        a vertex); 0 = no code: the cell is not OK or has more than 64
+ *        vertices before merging (a larger capacity tier)
  *   hash FNV-1a 64 over the 2E+1 vertex labels of the minimal code (order of
  *        first visit from 1, each label as two little-endian bytes); two
  *        cells are topologically equal iff their codes are, so equal
@@ -330,6 +334,16 @@ vg_status vg_get_kernel_ms(vg_ctx *ctx, double *total_ms, int64_t *count);
  * milliseconds and the number of replays.  Synchronises the stream.
  */
 vg_status vg_get_sort_ms(vg_ctx *ctx, double *total_ms, int64_t *count);
+
+/*
+ * Diagnostics of the 3D FP32 prefetch form with vg_config.split = 1: the
+ * number of cells that the last vg_compute() or graph replay handed from
+ * the kernel built for the common path to the general kernel (the walk
+ * after both preloads, FP64 statistics, plane slots used up, more than 32
+ * faces); 0 for every other form.  Synchronises the stream.
+ * VG_ERR_STATE before the first compute.
+ */
+vg_status vg_get_deferred(vg_ctx *ctx, int64_t *count);
 
 /*
  * The sorted container: block_start has B+1 entries (B = product of the

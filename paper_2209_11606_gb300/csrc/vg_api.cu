@@ -395,7 +395,6 @@ vg_status check_config(vg_ctx *c, const vg_config &cfg, bool inserts = false) {
     if (!(cfg.tol32 > 0) || !(cfg.tau_rel > 0) || !(cfg.merge_rel > 0)) return fail(c, VG_ERR_ARG, "tolerances");
     if (!(cfg.clip >= 0) || !(cfg.clip < 1e300)) return fail(c, VG_ERR_ARG, "clip must be finite and >= 0");
     if (cfg.weinberg && c->dim != 3) return fail(c, VG_ERR_ARG, "Weinberg codes: 3D cells");
-    if (cfg.weinberg && inserts) return fail(c, VG_ERR_ARG, "Weinberg codes: eager vg_compute only");
     if (cfg.warps_per_cta > 4) return fail(c, VG_ERR_ARG, "warps_per_cta above 4 (CTAs of at most 128 threads)");
     if (cfg.use_mlp && !c->kblock_valid && !(inserts && c->pred))
         return fail(c, VG_ERR_STATE, "use_mlp without vg_mlp_predict after the insert");
@@ -769,6 +768,8 @@ vg_status vg_graph_capture(vg_ctx *c, const int64_t *counts, const void *pos, co
     if (e == cudaSuccess && timed) e = cudaEventRecordWithFlags(c->gev[0], gs, cudaEventRecordExternal);
     if (e == cudaSuccess) e = enqueue_cells(c, cfg, gs);
     if (e == cudaSuccess && timed) e = cudaEventRecordWithFlags(c->gev[1], gs, cudaEventRecordExternal);
+    if (e == cudaSuccess && cfg.weinberg)
+        e = launch_weinberg(c->d_topo, c->d_topo_n, c->n, c->d_wlen, c->d_whash, c->d_wsym, c->sm_count, gs);
     if (e == cudaSuccess) e = enqueue_compact(c, gs);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(gs, &g);
@@ -836,7 +837,7 @@ vg_status vg_graph_launch(vg_ctx *c) {
     c->launches += c->graph_kernels;
     c->inserted = 1;
     c->computed = 1;
-    c->wb_valid = 0;
+    c->wb_valid = c->g_cfg.weinberg ? 1 : 0;
     c->subset = 0;
     c->graph_unchecked = 1;
     if (c->pred) c->kblock_valid = 1;
@@ -950,6 +951,16 @@ vg_status vg_get_sort_ms(vg_ctx *c, double *total_ms, int64_t *count) {
     return VG_OK;
 }
 
+vg_status vg_get_deferred(vg_ctx *c, int64_t *count) {
+    if (!c || !count) return VG_ERR_ARG;
+    if (!c->computed) return fail(c, VG_ERR_STATE, "no computed cells");
+    int k = 0;
+    VG_CUDA(cudaMemcpyAsync(&k, c->d_capcount0, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    VG_CUDA(cudaStreamSynchronize(c->stream));
+    *count = k;
+    return VG_OK;
+}
+
 vg_status vg_get_work(vg_ctx *c, int32_t *n_tested, int32_t *n_vtests, int32_t *n_cuts, int32_t *n_newv,
                       int32_t *n_retest, uint8_t *fallback, int32_t *n_prefetch, int on_device) {
     if (!c) return VG_ERR_ARG;
@@ -982,6 +993,10 @@ vg_status vg_get_radius(vg_ctx *c, float *rmax, int on_device) {
 
 vg_status vg_get_weinberg(vg_ctx *c, int32_t *len, uint64_t *hash, int32_t *sym, int on_device) {
     if (!c) return VG_ERR_ARG;
+    if (c->graph_unchecked) {
+        vg_status gs = graph_check(c);
+        if (gs != VG_OK) return gs;
+    }
     if (!c->computed) return fail(c, VG_ERR_STATE, "no computed cells");
     if (!c->wb_valid) return fail(c, VG_ERR_STATE, "no Weinberg codes: compute with cfg.weinberg = 1");
     vg_status s;

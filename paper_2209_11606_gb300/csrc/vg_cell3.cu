@@ -1316,6 +1316,9 @@ __global__ void VG_BOUNDS
                 int np = -1;
                 if (nplane < MAXP) {
                     np = nplane++;
+                } else if constexpr (HOT) {
+                    flags |= 32;  // plane slots used up: the general kernel
+                    break;
                 } else {
                     live_planes();
 #pragma unroll
@@ -1561,9 +1564,12 @@ __global__ void VG_BOUNDS
                 degen = degen || anyhk;
             }
             if constexpr (HOT) {
-                // FP64 statistics or the walk needed: the general kernel
-                // computes the cell (flags are warp-uniform)
-                if (degen || (flags & 32)) {
+                // FP64 statistics, the walk or a second round of faces needed:
+                // the general kernel computes the cell (flags are warp-uniform)
+                int nlive = 0;
+#pragma unroll
+                for (int w2 = 0; w2 < NW; w2++) nlive += __popcll(live[w2]);
+                if (degen || (flags & 32) || nlive > G) {
                     if (gl == 0) {
                         const int slot = atomicAdd(o.retry0_count, 1);
                         o.retry0[slot] = i;
@@ -1836,6 +1842,9 @@ __global__ void VG_BOUNDS
                     }
                 }
                 int nv;
+                // Weinberg codes: per slot s, byte s holds 1 + the slot of the
+                // first earlier vertex this one coincides with (0: none)
+                unsigned merged_into = 0;
                 if (!HOT && degen) {
                     // distinct vertices: a vertex counts if no earlier one coincides
                     const double eps = pp.merge_rel * g.s, eps2 = eps * eps;
@@ -1845,11 +1854,16 @@ __global__ void VG_BOUNDS
                         const int t = s * G + gl;
                         if (S.x.v.stri[t] != TRI_EMPTY) {
                             bool first = true;
-                            for (int q = 0; q < t && first; q++) {
+                            int q = 0;
+                            for (; q < t && first; q++) {
                                 if (S.x.v.stri[q] == TRI_EMPTY) continue;
                                 const double dx = S.x.v.dpos[q][0] - S.x.v.dpos[t][0], dy = S.x.v.dpos[q][1] - S.x.v.dpos[t][1],
                                              dz = S.x.v.dpos[q][2] - S.x.v.dpos[t][2];
                                 if (dx * dx + dy * dy + dz * dz <= eps2) first = false;
+                            }
+                            if constexpr (TOPO) {
+                                static_assert(VPL <= 4, "one byte a slot");
+                                if (!first) merged_into |= (unsigned)q << (8 * s);  // q = match + 1
                             }
                             cntv += first;
                         }
@@ -1867,7 +1881,7 @@ __global__ void VG_BOUNDS
                     long long fbase = 0;
                     if (gl == 0) fbase = (long long)atomicAdd(o.fcount, (unsigned long long)nfk);
                     // one round of faces: one key per lane, a shorter network
-                    const bool one = F <= G;
+                    const bool one = HOT || F <= G;  // the hot kernel defers F > G
                     if (one) {
                         key[0] = bitonic1<G>(key[0], gl, gmask);
                     } else if constexpr (R == 2) {
@@ -1895,9 +1909,14 @@ __global__ void VG_BOUNDS
                         }
                     }
                     if constexpr (TOPO) {
-                        // the triangles by slot, for the Weinberg codes (tier 0: 64 slots)
+                        // the triangles by slot, for the Weinberg codes (tier 0: 64
+                        // slots); the top byte names the vertex it merges into
 #pragma unroll
-                        for (int s = 0; s < VPL; s++) o.topo[(long long)out_i * (G * VPL) + s * G + gl] = tri[s];
+                        for (int s = 0; s < VPL; s++) {
+                            unsigned t = tri[s];
+                            if (t != TRI_EMPTY) t = (t & 0xffffffu) | (((merged_into >> (8 * s)) & 0xffu) << 24);
+                            o.topo[(long long)out_i * (G * VPL) + s * G + gl] = t;
+                        }
                     }
                     if (gl == 0) {
                         const double v6 = vol;
@@ -1914,7 +1933,7 @@ __global__ void VG_BOUNDS
                         o.ne[out_i] = osum / 2;
                         o.nf[out_i] = nfk;
                         o.status[out_i] = overflow ? (unsigned char)VG_CELL_CAP : (unsigned char)VG_CELL_OK;
-                        if constexpr (TOPO) o.topo_n[out_i] = (nv == T_ && !overflow) ? T_ : 0;
+                        if constexpr (TOPO) o.topo_n[out_i] = overflow ? 0 : T_;
                         o.fptr[out_i] = fbase;
                     }
                 }

@@ -1,10 +1,21 @@
 // Weinberg codes (Sec. 4) of the cells' edge graphs, one warp per cell.
 //
-// The cell kernel keeps each simple cell's triangles (plane triples, one per
-// vertex, consistently oriented).  Darts: vertex v with planes (a, b, c)
-// leaves along its three edges, dart 3v + k for the plane pairs (a, b),
-// (b, c), (c, a); the edge (x, y) leads to the vertex holding the reverse
-// pair (y, x).  Rotation: dart 3v + k is followed by 3v + (k + 1) mod 3.
+// The cell kernel keeps each cell's triangles (plane triples, one per
+// vertex, consistently oriented); the top byte of a triangle names the
+// earlier slot whose vertex it coincides with (cells of an exact lattice,
+// where four or more planes meet at a point, hold several triangles at one
+// point).  Darts of the triangulation: vertex v with planes (a, b, c) leaves
+// along its three edges, dart 3v + k for the plane pairs (a, b), (b, c),
+// (c, a); the edge (x, y) leads to the vertex holding the reverse pair
+// (y, x), and dart 3v + k is followed by 3v + (k + 1) mod 3 around v.
+//
+// The edge graph of the cell merges coincident vertices: a dart between two
+// of them has length zero and is contracted.  Around a merged vertex the
+// rotation passes a contracted dart by continuing after its reverse, at the
+// vertex on its other end (the two rotations are spliced).  A face left
+// with two edges (a plane that touches the finished cell along one edge)
+// is removed: its two edges become one, whose darts are the reverses of the
+// removed face's darts, and the removed darts leave the rotations.
 //
 // Weinberg's traversal from a start dart: at a new vertex leave by the dart
 // after the reverse of the arriving one; at an old vertex return along the
@@ -26,16 +37,30 @@ namespace {
 constexpr int WB_V = 64;            // vertices of a tier-0 cell
 constexpr int WB_D = 3 * WB_V;      // darts
 constexpr int WB_WARPS = 4;
+constexpr unsigned WB_EMPTY = 0xffffffffu;
 
 struct WbSmem {
     unsigned char pair[WB_V][WB_V];  // vertex holding the directed plane pair (x, y)
-    unsigned tri[WB_V];              // compacted triangles
+    unsigned tri[WB_V];              // compacted triangles (plane ids only)
+    unsigned char cmap[WB_V];        // slot -> compacted index
+    unsigned char cl[WB_V];          // merged vertex of each vertex (its first vertex)
     unsigned char dto[WB_D];         // head vertex of each dart
     unsigned char drev[WB_D];        // reverse dart
-    unsigned char lab[32][WB_V];     // per lane: vertex labels of its traversal
+    unsigned char rotn[WB_D];        // next dart around the merged tail vertex
+    unsigned char rotp[WB_D];        // previous dart around it
+    unsigned char mlist[WB_D];       // the darts that are not contracted
+    unsigned char dead[WB_D];        // darts of a removed two-edge face
+    unsigned char frev[WB_D];        // reverse, rotations and list after the removal
+    unsigned char frotn[WB_D];
+    unsigned char frotp[WB_D];
+    unsigned char flist[WB_D];
+    unsigned char lab[32][WB_V];     // per lane: labels of merged vertices
     unsigned used[32][WB_D / 32];    // per lane: darts traversed
     unsigned short best[WB_D + 1];   // best code so far
 };
+
+__device__ __forceinline__ int dnext(int e) { return e - e % 3 + (e % 3 + 1) % 3; }
+__device__ __forceinline__ int dprev(int e) { return e - e % 3 + (e % 3 + 2) % 3; }
 
 __global__ void __launch_bounds__(32 * WB_WARPS) k_weinberg(const unsigned *__restrict__ topo,
                                                             const int *__restrict__ topo_n, long long n,
@@ -44,25 +69,66 @@ __global__ void __launch_bounds__(32 * WB_WARPS) k_weinberg(const unsigned *__re
                                                             int *__restrict__ wsym) {
     extern __shared__ __align__(16) unsigned char wb_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1;
     WbSmem &S = reinterpret_cast<WbSmem *>(wb_raw)[warp];
     const long long stride = (long long)gridDim.x * WB_WARPS;
     for (long long cell = (long long)blockIdx.x * WB_WARPS + warp; cell < n; cell += stride) {
         const int nt = topo_n[cell];
-        int D = 0, sym = 0;
+        int Dm = 0, sym = 0;
         bool ok = nt > 0 && nt <= WB_V;
         int V = 0;
         if (ok) {
             // compact the occupied slots
+            unsigned traw[WB_V / 32];
+            int tidx[WB_V / 32];
 #pragma unroll
             for (int r = 0; r < WB_V / 32; r++) {
                 const unsigned t = topo[cell * WB_V + r * 32 + lane];
-                const bool occ = t != 0xffffffffu;
+                const bool occ = t != WB_EMPTY;
                 const unsigned m = __ballot_sync(FULL, occ);
-                if (occ) S.tri[V + __popc(m & ((1u << lane) - 1))] = t;
+                traw[r] = t;
+                tidx[r] = V + __popc(m & lt);
+                if (occ) {
+                    S.tri[tidx[r]] = t & 0xffffffu;
+                    S.cmap[r * 32 + lane] = (unsigned char)tidx[r];
+                }
                 V += __popc(m);
             }
             ok = V == nt;
             __syncwarp();
+            // merged vertices: each vertex points at the earlier one it
+            // coincides with; pointer jumping reaches the first of its group
+            bool bad = false;
+#pragma unroll
+            for (int r = 0; r < WB_V / 32; r++) {
+                if (traw[r] != WB_EMPTY) {
+                    const int into = (int)(traw[r] >> 24);  // 1 + slot, 0 = none
+                    int par = tidx[r];
+                    if (into > 0) {
+                        const int slot = into - 1;
+                        if (slot < r * 32 + lane && topo[cell * WB_V + slot] != WB_EMPTY) par = S.cmap[slot];
+                        else bad = true;
+                    }
+                    S.cl[tidx[r]] = (unsigned char)par;
+                }
+            }
+            __syncwarp();
+#pragma unroll 1
+            for (int it = 0; it < 6; it++) {
+                int c2[WB_V / 32];
+#pragma unroll
+                for (int r = 0; r < WB_V / 32; r++) {
+                    const int v = r * 32 + lane;
+                    c2[r] = v < V ? S.cl[S.cl[v]] : 0;
+                }
+                __syncwarp();
+#pragma unroll
+                for (int r = 0; r < WB_V / 32; r++) {
+                    const int v = r * 32 + lane;
+                    if (v < V) S.cl[v] = (unsigned char)c2[r];
+                }
+                __syncwarp();
+            }
             // plane pairs -> vertex; every pair of a valid cell is written once
             for (int v = lane; v < V; v += 32) {
                 const unsigned t = S.tri[v];
@@ -71,11 +137,12 @@ __global__ void __launch_bounds__(32 * WB_WARPS) k_weinberg(const unsigned *__re
                     S.pair[a][b] = (unsigned char)v;
                     S.pair[b][c] = (unsigned char)v;
                     S.pair[c][a] = (unsigned char)v;
+                } else {
+                    bad = true;
                 }
             }
             __syncwarp();
-            D = 3 * V;
-            bool bad = false;
+            const int D = 3 * V;
             for (int d = lane; d < D; d += 32) {
                 const unsigned t = S.tri[d / 3];
                 const int p[3] = {(int)(t & 0xff), (int)((t >> 8) & 0xff), (int)((t >> 16) & 0xff)};
@@ -96,46 +163,116 @@ __global__ void __launch_bounds__(32 * WB_WARPS) k_weinberg(const unsigned *__re
             }
             ok = ok && !__any_sync(FULL, bad);
             __syncwarp();
+            if (ok) {
+                // the darts that join two merged vertices
+                for (int d0 = 0; d0 < D; d0 += 32) {
+                    const int d = d0 + lane;
+                    const bool keep = d < D && S.cl[S.dto[d]] != S.cl[d / 3];
+                    const unsigned m = __ballot_sync(FULL, keep);
+                    if (keep) S.mlist[Dm + __popc(m & lt)] = (unsigned char)d;
+                    Dm += __popc(m);
+                }
+                __syncwarp();
+                // rotations around merged vertices: pass each contracted dart
+                // by continuing after its reverse
+                for (int j = lane; j < Dm; j += 32) {
+                    const int d = S.mlist[j];
+                    int e = dnext(d), steps = 0;
+                    while (S.cl[S.dto[e]] == S.cl[e / 3] && steps < D) { e = dnext(S.drev[e]); steps++; }
+                    int f = dprev(d), fsteps = 0;
+                    while (S.cl[S.dto[f]] == S.cl[f / 3] && fsteps < D) { f = dprev(S.drev[f]); fsteps++; }
+                    if (steps >= D || fsteps >= D) bad = true;
+                    S.rotn[d] = (unsigned char)e;
+                    S.rotp[d] = (unsigned char)f;
+                }
+                __syncwarp();
+                ok = Dm > 0 && !__any_sync(FULL, bad);
+                // faces of two edges: the successor along a face (rotn of the
+                // reverse) returns to the dart in two steps
+                if (ok) {
+                    for (int j = lane; j < Dm; j += 32) {
+                        const int d = S.mlist[j];
+                        const int f1 = S.rotn[S.drev[d]];
+                        S.dead[d] = S.rotn[S.drev[f1]] == d ? 1 : 0;
+                    }
+                    __syncwarp();
+                    int nlive = 0;
+                    for (int j0 = 0; j0 < Dm; j0 += 32) {
+                        const int j = j0 + lane;
+                        const int d = j < Dm ? S.mlist[j] : 0;
+                        const bool live = j < Dm && !S.dead[d];
+                        if (live) {
+                            // the reverse across removed faces, the rotations
+                            // without their darts
+                            int r = S.drev[d], g1 = 0;
+                            while (S.dead[r] && g1 < Dm) { r = S.drev[S.rotn[S.drev[r]]]; g1++; }
+                            int e = S.rotn[d], g2 = 0;
+                            while (S.dead[e] && g2 < Dm) { e = S.rotn[e]; g2++; }
+                            int f = S.rotp[d], g3 = 0;
+                            while (S.dead[f] && g3 < Dm) { f = S.rotp[f]; g3++; }
+                            if (g1 >= Dm || g2 >= Dm || g3 >= Dm) bad = true;
+                            S.frev[d] = (unsigned char)r;
+                            S.frotn[d] = (unsigned char)e;
+                            S.frotp[d] = (unsigned char)f;
+                        }
+                        const unsigned m = __ballot_sync(FULL, live);
+                        if (live) S.flist[nlive + __popc(m & lt)] = (unsigned char)d;
+                        nlive += __popc(m);
+                    }
+                    Dm = nlive;
+                    __syncwarp();
+                    ok = Dm > 0 && !__any_sync(FULL, bad);
+                    // none left after the removal
+                    if (ok) {
+                        for (int j = lane; j < Dm; j += 32) {
+                            const int d = S.flist[j];
+                            const int f1 = S.frotn[S.frev[d]];
+                            if (S.frotn[S.frev[f1]] == d) bad = true;
+                        }
+                        ok = !__any_sync(FULL, bad);
+                    }
+                }
+            }
         }
         if (ok) {
             bool have = false, stuck = false;
-            const int NT = 2 * D;
+            const int NT = 2 * Dm;
             for (int r0 = 0; r0 < NT; r0 += 32) {
                 const int q = r0 + lane;
                 bool active = q < NT;
-                const int o = q >= D ? 1 : 0;  // rotation direction
-                int d = active ? q % D : 0;
+                const int o = q >= Dm ? 1 : 0;  // rotation direction
+                int d = S.flist[active ? q % Dm : 0];
                 for (int v = 0; v < WB_V; v += 4) *reinterpret_cast<unsigned *>(&S.lab[lane][v]) = 0u;
 #pragma unroll
                 for (int w = 0; w < WB_D / 32; w++) S.used[lane][w] = 0u;
                 int nl = 1;
-                S.lab[lane][d / 3] = 1;
+                S.lab[lane][S.cl[d / 3]] = 1;
                 int cmp = have ? 0 : -1;  // 0: equal to the best so far, -1: below it
                 if (!have && lane == 0) S.best[0] = 1;
                 __syncwarp();
-                for (int k = 0; k < D; k++) {
+                for (int k = 0; k < Dm; k++) {
                     int L = 0xffff, nd = -1;
                     if (active) {
                         S.used[lane][d >> 5] |= 1u << (d & 31);
-                        const int y = S.dto[d], rv = S.drev[d];
-                        // the darts leaving y are base .. base + 2, in rotation order
-                        const int base = 3 * (rv / 3);
-                        auto R = [&](int e) { return base + (o ? (e - base + 2) % 3 : (e - base + 1) % 3); };
+                        const int y = S.cl[S.dto[d]], rv = S.frev[d];
+                        const unsigned char *rot = o ? S.frotp : S.frotn;
                         if (!S.lab[lane][y]) {
                             S.lab[lane][y] = (unsigned char)(++nl);
                             L = nl;
-                            nd = R(rv);
+                            nd = rot[rv];
                         } else {
                             L = S.lab[lane][y];
                             if (!((S.used[lane][rv >> 5] >> (rv & 31)) & 1)) {
                                 nd = rv;
                             } else {
-                                int e = R(rv);
-                                while (((S.used[lane][e >> 5] >> (e & 31)) & 1) && e != rv) e = R(e);
+                                int e = rot[rv];
+                                for (int guard = 0; ((S.used[lane][e >> 5] >> (e & 31)) & 1) && e != rv && guard < Dm;
+                                     guard++)
+                                    e = rot[e];
                                 if (!((S.used[lane][e >> 5] >> (e & 31)) & 1)) nd = e;
                             }
                         }
-                        if (k + 1 < D && nd < 0) stuck = true;
+                        if (k + 1 < Dm && nd < 0) stuck = true;
                     }
                     const unsigned m = __reduce_min_sync(FULL, (unsigned)L);
                     const unsigned bk = cmp == 0 ? S.best[k + 1] : 0u;
@@ -162,13 +299,13 @@ __global__ void __launch_bounds__(32 * WB_WARPS) k_weinberg(const unsigned *__re
         if (lane == 0) {
             if (ok) {
                 unsigned long long h = 14695981039346656037ull;
-                for (int k = 0; k <= D; k++) {
+                for (int k = 0; k <= Dm; k++) {
                     h ^= (unsigned long long)(S.best[k] & 0xff);
                     h *= 1099511628211ull;
                     h ^= (unsigned long long)(S.best[k] >> 8);
                     h *= 1099511628211ull;
                 }
-                wlen[cell] = D; whash[cell] = h; wsym[cell] = sym;
+                wlen[cell] = Dm; whash[cell] = h; wsym[cell] = sym;
             } else {
                 wlen[cell] = 0; whash[cell] = 0ull; wsym[cell] = 0;
             }
