@@ -93,11 +93,7 @@ FLOP_VTEST, FLOP_CAND, FLOP_NEWV, FLOP_FANTET = 6, 12, 51, 42
 # of one launch, warp instructions per cell, active lanes per instruction,
 # issue-active fraction.  An entry is removed whenever the kernel changes
 # after its capture, so only counters of the timed build are reported.
-CELL_KERNEL_NCU = {
-    "uniform1m": {"dram_bytes": 194683136 + 290834176, "warp_inst_per_cell": 12697.5, "lanes_per_inst": 23.47,
-                  "issue_active": 0.612, "kernel": "k_cells3<float,2,64,...,HOT> (hot kernel)",
-                  "source": "profiles/k_cells3_hot_fp32_uniform1m_ncu.md"},
-}
+CELL_KERNEL_NCU = {}
 MLP_ALPHA, MLP_KMIN, MLP_KMAX = 1.2, 24.0, 1024.0
 # peak warp-instruction issue rate: 152 SMs x 4 schedulers x 1 per cycle x 2.07 GHz
 ISSUE_PEAK = 152 * 4 * 2.07e9

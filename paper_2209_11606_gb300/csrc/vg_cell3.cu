@@ -731,6 +731,9 @@ __global__ void VG_BOUNDS
             }
             int ntri = 8;        // vertices
             unsigned rows = 1;   // register slots (rows of G lanes) that hold any vertex
+            // FP32: the vertex mirror is rebuilt before the next batch reads it,
+            // not after every cut (warp-uniform)
+            bool mdirty = false;
             // planes in use: a counter hands out plane slots; the exact set of
             // live planes (those some vertex still lies on) is rebuilt from the
             // vertices only when the counter runs out and for the statistics
@@ -1019,6 +1022,23 @@ __global__ void VG_BOUNDS
                 while (want == 0) {
                     const int mode = src.mode;
                     if (mode == 3) break;
+                    if constexpr (F32) {
+                        if (mdirty) {
+                            // packed in (slot, lane) order, zeros up to the next
+                            // multiple of 8
+                            int mpos = 0;
+#pragma unroll
+                            for (int s = 0; s < VPL; s++) {
+                                const unsigned oc = gballot<G>(gmask, gbase, tri[s] != TRI_EMPTY);
+                                if (tri[s] != TRI_EMPTY)
+                                    S.v4[mpos + __popc(oc & ((1u << gl) - 1))] = make_float4(vx[s], vy[s], vz[s], kap[s]);
+                                mpos += __popc(oc);
+                            }
+                            if (gl < ((ntri + 7) & ~7) - ntri) S.v4[ntri + gl] = make_float4(0.f, 0.f, 0.f, 0.f);
+                            mdirty = false;
+                            __syncwarp(gmask);
+                        }
+                    }
                     if (mode == 0) {
                         const int u = src.u, count = src.count;
                         if (u >= count) {
@@ -1524,8 +1544,6 @@ __global__ void VG_BOUNDS
                 // carries it through the group maximum to every lane)
                 const T r2lim = r2 * (T)1.01;
                 bool wild = false;
-                // the mirror holds the vertices packed in (slot, lane) order
-                int mpos = 0;
 #pragma unroll
                 for (int s = 0; s < VPL; s++) {
                     if (tri[s] != TRI_EMPTY) {
@@ -1534,16 +1552,9 @@ __global__ void VG_BOUNDS
                         if constexpr (F32) q2 *= 1.f + 4e-6f * kap[s];  // allowance for FP32 error
                         rr = rr > q2 ? rr : q2;
                     }
-                    const unsigned oc = gballot<G>(gmask, gbase, tri[s] != TRI_EMPTY);
-                    if constexpr (F32)
-                        if (tri[s] != TRI_EMPTY) S.v4[mpos + __popc(oc & lt)] = make_float4(vx[s], vy[s], vz[s], kap[s]);
-                    if (oc) rows |= 1u << s;
-                    mpos += __popc(oc);
+                    if (__any_sync(gmask, tri[s] != TRI_EMPTY)) rows |= 1u << s;
                 }
-                if constexpr (F32) {
-                    // entries up to the next multiple of 8 are read too: free ones
-                    if (gl < ((ntri + 7) & ~7) - ntri) S.v4[ntri + gl] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
+                if constexpr (F32) mdirty = true;
                 if (VG_RARE(wild)) rr = (T)INFINITY;
                 r2 = gmax<G>(gmask, rr);
                 if (VG_RARE(!(r2 < (T)INFINITY))) { flags |= 2; break; }
