@@ -93,7 +93,11 @@ FLOP_VTEST, FLOP_CAND, FLOP_NEWV, FLOP_FANTET = 6, 12, 51, 42
 # of one launch, warp instructions per cell, active lanes per instruction,
 # issue-active fraction.  An entry is removed whenever the kernel changes
 # after its capture, so only counters of the timed build are reported.
-CELL_KERNEL_NCU = {}
+CELL_KERNEL_NCU = {
+    "uniform1m": {"dram_bytes": 204035328 + 298252288, "warp_inst_per_cell": 12404.2, "lanes_per_inst": 23.26,
+                  "issue_active": 0.602, "kernel": "k_cells3<float,2,64,...,HOT> (hot kernel)",
+                  "source": "profiles/k_cells3_hot_fp32_uniform1m_ncu.md"},
+}
 MLP_ALPHA, MLP_KMIN, MLP_KMAX = 1.2, 24.0, 1024.0
 # peak warp-instruction issue rate: 152 SMs x 4 schedulers x 1 per cycle x 2.07 GHz
 ISSUE_PEAK = 152 * 4 * 2.07e9
@@ -274,7 +278,7 @@ def batched_run(V, torch, stream, flush, mlp, steps: int = 5, seed: int = 5):
     systems = W.batched_systems(256, 1000, 200_000, seed=seed)
     t0 = time.perf_counter()
     cache = A.Cache(TUNE_CACHE)
-    key = "batched256-seed%d-split3" % seed
+    key = "batched256-seed%d-nopt48" % seed
     tb = cache.get(key)
     if tb is None:
         tb = A.tune_batch(systems, torch, cache, predictor=mlp, mlp_args=(MLP_ALPHA, MLP_KMIN, MLP_KMAX))

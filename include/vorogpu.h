@@ -479,10 +479,9 @@ vg_status vg_set_predictor(vg_ctx *ctx, vg_mlp *mlp, float alpha, float kmin, fl
  * allocating routine.  Every call ends by reading the error flags back to a
  * host variable and synchronising `stream`.  The first call on each device
  * looks up the device address of the scratch array (cudaGetSymbolAddress)
- * with that device current and keeps it for the rest of the process; make
- * that first call before any stream capture, and do not call this entry
- * point after resetting the device (cudaDeviceReset), which would leave the
- * kept address stale.  All calls on a device share the one scratch array,
+ * with that device current and keeps it for the rest of the process; do
+ * not call this entry point after resetting the device (cudaDeviceReset),
+ * which would leave the kept address stale.  All calls on a device share the one scratch array,
  * so calls that overlap on the GPU (from two streams or two host threads)
  * race and must be serialised by the caller.
  */
