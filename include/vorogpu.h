@@ -439,7 +439,8 @@ vg_status vg_mlp_infer(vg_mlp *mlp, const float *X, int64_t M, float *y);
 /*
  * Per-block preload targets for the inserted container: clamp(alpha exp(y),
  * kmin, kmax) for every block, used by vg_compute() with use_mlp = 1 until
- * the next insert.  VG_ERR_STATE before an insert.
+ * the next insert (each block preloads the geometric mean of the targets
+ * of its 27 blocks, at least 8).  VG_ERR_STATE before an insert.
  */
 vg_status vg_mlp_predict(vg_ctx *ctx, vg_mlp *mlp, float alpha, float kmin, float kmax);
 

@@ -30,7 +30,7 @@ import numpy as np
 
 from . import vorogpu as V
 
-N_OPT = (1.0, 2.0, 3.0, 4.6, 6.0, 8.0, 12.0, 16.0)
+N_OPT = (1.0, 2.0, 3.0, 4.6, 6.0, 8.0, 12.0, 16.0, 24.0, 32.0, 48.0)
 WARPS = (1, 2, 4)
 ORDERS = ("prefetch", "walk")
 CHUNKS = (1, 2, 4)

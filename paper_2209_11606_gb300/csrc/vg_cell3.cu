@@ -549,14 +549,17 @@ __global__ void k_prefetch_rho(const Sys *__restrict__ sys, int nsys, const int 
     const long long kl = b - sy.blk_base;
     const int hb[3] = {(int)(kl % g.nb[0]), (int)((kl / g.nb[0]) % g.nb[1]), (int)(kl / ((long long)g.nb[0] * g.nb[1]))};
     int n27 = 0, v27 = 0;
+    float lk = 0.f;
     for (int q = 0; q < 27; q++) {
         int kk, mx, my, mz;
         if (resolve(g, sy.blk_base, hb, q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1, kk, mx, my, mz)) {
             n27 += bstart[kk + 1] - bstart[kk];
             v27 += 1;
+            if (kblock) lk += logf(fmaxf(8.f, kblock[kk]));
         }
     }
-    const float kt = kblock ? fmaxf(8.f, kblock[b]) : kfixed;
+    // learned targets: the geometric mean over the 27 blocks
+    const float kt = kblock ? expf(lk / (float)max(v27, 1)) : kfixed;
     const float dens = (float)max(n27, 1) * rcp_a((float)max(v27, 1) * g.hf[0] * g.hf[1] * g.hf[2]);
     rho[b] = cbrt_a(3.f * kt * rcp_a(4.f * 3.14159265f * dens));
 }

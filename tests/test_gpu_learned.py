@@ -5,8 +5,9 @@ the prefetch form preloads (27 block counts -> 32 -> 32 -> 1, FP16
 weights, trained on the 1M-point configuration's k* labels; the weights
 and the scale alpha, floor kmin the benchmark uses).  The radius bound of
 Sec. 2.1.3 still decides, so the cells never depend on the prediction; the
-prediction sets how much each cell preloads, and a shortfall is met by a
-second, wider preload (rarely by the walk).  What it buys is speed.
+prediction (the geometric mean over a block's 27 blocks) sets how much each
+cell preloads, and a shortfall is met by a second, wider preload (rarely by
+the walk).  What it buys is speed.
 
 Measured in the benchmark's launch configuration (graph replays, L2
 flushed) on the 1M-point configuration (uniform, perturbed BCC) and on sets
