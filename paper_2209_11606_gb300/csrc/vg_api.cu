@@ -447,7 +447,7 @@ cudaError_t enqueue_cells(vg_ctx *c, const vg_config &cfg, cudaStream_t s, const
     // 3D FP32 prefetch: the hot kernel over every cell, then the general one
     // over the cells it deferred (walk after the preload, FP64 statistics)
     const bool hot = cfg.split && c->dim == 3 && cfg.precision == VG_FP32_RETEST && cfg.order == VG_PREFETCH &&
-                     !cfg.weinberg && c->n < (1 << 27);
+                     (!cfg.weinberg || c->sys.size() == 1) && c->n < (1 << 27);
     if (hot) {
         if ((e = launch_cells3_hot(st, o, pp, off, c->d_ticket, c->sm_count, cfg.warps_per_cta, subset, nc, s)))
             return e;

@@ -2038,14 +2038,14 @@ cudaError_t launch_cells3(const Store &s, const Out &o, const Params &p, const O
     const bool batch = s.nsys > 1;
     if (precision == VG_FP64) {
         if (o.topo)  // the cells' triangles are kept for Weinberg codes (tier 0)
-            return batch ? launch_t<double, VG_T0_VPL, 64, true, VG_T0_G, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st)
-                         : launch_t<double, VG_T0_VPL, 64, false, VG_T0_G, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
+            return batch ? launch_t<double, VG_T0_VPL, 64, true, VG_T0_G, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, tier, st)
+                         : launch_t<double, VG_T0_VPL, 64, false, VG_T0_G, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, tier, st);
         return batch ? launch_t<double, VG_T0_VPL, 64, true, VG_T0_G>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st)
                      : launch_t<double, VG_T0_VPL, 64, false, VG_T0_G>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
     }
-    if (o.topo)  // the cells' triangles are kept for Weinberg codes (tier 0)
-        return batch ? launch_t<float, VG_T0_VPL, 64, true, VG_T0_G, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st)
-                     : launch_t<float, VG_T0_VPL, 64, false, VG_T0_G, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, 0, st);
+    if (o.topo)  // the cells' triangles are kept for Weinberg codes (tier 0, or 3)
+        return batch ? launch_t<float, VG_T0_VPL, 64, true, VG_T0_G, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, tier, st)
+                     : launch_t<float, VG_T0_VPL, 64, false, VG_T0_G, true>(s, o, p, off, ticket, sm_count, w, cells, ncells, tier, st);
     return batch ? launch_t<float, VG_T0_VPL, 64, true, VG_T0_G>(s, o, p, off, ticket, sm_count, w, cells, ncells, tier, st)
                  : launch_t<float, VG_T0_VPL, 64, false, VG_T0_G>(s, o, p, off, ticket, sm_count, w, cells, ncells, tier, st);
 }
@@ -2055,6 +2055,10 @@ cudaError_t launch_cells3(const Store &s, const Out &o, const Params &p, const O
 cudaError_t launch_cells3_hot(const Store &s, const Out &o, const Params &p, const Offsets &off, unsigned *ticket,
                               int sm_count, int warps_per_cta, const int *cells, int ncells, cudaStream_t st) {
     const int w = warps_per_cta > 0 ? min(warps_per_cta, VG_MAXT / 32) : VG_MAXT / 32;
+    if (o.topo)  // Weinberg codes: the triangles kept (one system only)
+        return s.nsys > 1 ? cudaErrorInvalidValue
+                          : launch_t<float, VG_T0_VPL, 64, false, VG_T0_G, true, true>(s, o, p, off, ticket, sm_count, w,
+                                                                                       cells, ncells, 0, st);
     return s.nsys > 1
                ? launch_t<float, VG_T0_VPL, 64, true, VG_T0_G, false, true>(s, o, p, off, ticket, sm_count, w, cells,
                                                                            ncells, 0, st)
