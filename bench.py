@@ -122,7 +122,7 @@ MLP_PARAMS = os.path.join(PKG, "mlp_params_gb300.json")
 TUNE_CACHE = os.path.join(PKG, "tuned_gb300.json")
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -144,7 +144,7 @@ def parse():
                     help="3D FP32 prefetch: 1 = the hot kernel with deferral, 0 = the general kernel alone")
     ap.add_argument("--weinberg", action="store_true",
                     help="also time the cells with Weinberg codes (Sec. 4), eager calls")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def clip_of(name: str) -> float:
@@ -462,6 +462,19 @@ def accuracy(got, ref, cells, rtol):
             "bar": rtol, "within_bar": bool(rep["topology_ok"] and rep["values_ok"])}
 
 
+def job_rate(dist, t_local: float, cells_per_rank: int, steps: int, world: int, device) -> tuple[float, float]:
+    """Whole-job cells/s of N replicas: every rank's cells over the slowest
+    rank's time (a max-reduce, the only collective).  Returns (rate, time)."""
+    t = t_local
+    if dist is not None:
+        import torch
+        v = torch.tensor([t_local], dtype=torch.float64, device=device)
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        t = float(v.item())
+        dist.barrier()
+    return world * cells_per_rank * steps / t, t
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -560,13 +573,7 @@ def main():
     launches = V.vg_get_launches(ctx) - l0
     kern_ms, kern_n = V.vg_get_kernel_ms(ctx)
     sort_ms, sort_n = V.vg_get_sort_ms(ctx)
-    t_total = sum(step_ms) / 1000.0
-    if dist:
-        t = torch.tensor([t_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
-        dist.barrier()
-    value = world * n * args.steps / t_total
+    value, t_total = job_rate(dist, sum(step_ms) / 1000.0, n, args.steps, world, "cuda")
 
     if rank != 0:
         V.vg_destroy(ctx)
