@@ -97,6 +97,9 @@ CELL_KERNEL_NCU = {
     "uniform1m": {"dram_bytes": 204035328 + 298252288, "warp_inst_per_cell": 12404.2, "lanes_per_inst": 23.26,
                   "issue_active": 0.602, "kernel": "k_cells3<float,2,64,...,HOT> (hot kernel)",
                   "source": "profiles/k_cells3_hot_fp32_uniform1m_ncu.md"},
+    "hex10m": {"dram_bytes": 594627584 + 1095686144, "warp_inst_per_cell": 3478.1, "lanes_per_inst": 14.39,
+               "issue_active": 0.388, "kernel": "k_cells2<float,8,16> (2D tier 0)",
+               "source": "profiles/k_cells2_fp32_hex10m_ncu.md"},
 }
 MLP_ALPHA, MLP_KMIN, MLP_KMAX = 1.2, 24.0, 1024.0
 # peak warp-instruction issue rate: 152 SMs x 4 schedulers x 1 per cycle x 2.07 GHz
@@ -612,7 +615,7 @@ def main():
             "frac": achieved / FP32_PEAK_TFLOPS,
             "traffic": None,
             "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-            "kernel": ("k_cells3<float,2,64>" if dim == 3 else "k_cells2<float,8,32>") + " (cell kernel phase, all tiers)",
+            "kernel": ("k_cells3<float,2,64>" if dim == 3 else "k_cells2<float,8,16>") + " (cell kernel phase, all tiers)",
             "kernel_ms": kern_avg_ms,
             "flop_per_cell": flop / n,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}

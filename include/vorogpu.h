@@ -112,16 +112,19 @@ typedef struct {
     int weinberg;      /* 1 = also the Weinberg code of every 3D cell's edge
                           graph (Sec. 4), read with vg_get_weinberg(); either
                           form, vg_compute or a captured graph.  Default 0 */
-    int split;         /* 3D FP32 prefetch only.  1 (default): a kernel built
+    int split;         /* FP32 form.  3D prefetch, 1 (default): a kernel built
                           for the common path alone computes every cell it
                           can, and hands each cell that needs the walk after
                           its preloads, FP64 statistics, more than 64 planes
                           or more than 32 faces to the general kernel, which
                           computes that cell from the start (vg_get_deferred
-                          counts them).
-                          0: the general kernel computes every cell (better
-                          where many cells outgrow their preload, as in
-                          clustered sets).  Results are the same */
+                          counts them).  2D, 1: the first kernel holds 16
+                          vertices a cell and hands larger cells to one of 32
+                          (0: 32 from the start).
+                          3D, 0: the general kernel computes every cell.
+                          0 is better where many cells outgrow their preload
+                          or 16 vertices, as in clustered sets.  The cells
+                          are the same (values to rounding) */
 } vg_config;
 
 /* Fills `cfg` with the defaults listed above (FP32_RETEST, PREFETCH). */

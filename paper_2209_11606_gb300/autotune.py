@@ -209,7 +209,7 @@ def tune_batch(systems, torch, cache: Cache | None = None, sample_frac: float = 
             if order == "prefetch" and systems[0].dim != 3:
                 continue
             mlps = (0, 1) if order == "prefetch" and predictor is not None else (0,)
-            splits = (1, 0) if order == "prefetch" and systems[0].dim == 3 else (1,)
+            splits = (1, 0) if order == "prefetch" or systems[0].dim == 2 else (1,)
             for w in WARPS:
                 for ch in CHUNKS:
                     for um in mlps:

@@ -417,6 +417,7 @@ cudaError_t enqueue_cells(vg_ctx *c, const vg_config &cfg, cudaStream_t s, const
     pp.collect = cfg.collect_stats ? 1 : 0;
     pp.kblock = cfg.use_mlp ? c->d_kblock : nullptr;
     pp.rhoblk = c->d_rho;
+    pp.split = cfg.split ? 1 : 0;
     Offsets off;
     off.code = c->d_off_code; off.lb = c->d_off_lb;
     Out o;

@@ -864,7 +864,8 @@ cudaError_t launch2_t(const Store &s, const Out &o, const Params &p, const Offse
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    const int grid = tier > 0 ? sm_count : sm_count * per_sm;
+    // the FP64 tiers take few cells: one CTA an SM
+    const int grid = (tier > 0 && sizeof(T) == 8) ? sm_count : sm_count * per_sm;
     if ((e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
     ++g_launch_count;
     kfn<<<grid, threads, smem, st>>>(s, o, p, off, ticket, cells, ncells, tier);
@@ -877,13 +878,24 @@ cudaError_t launch_cells2(const Store &s, const Out &o, const Params &p, const O
                           unsigned *ticket, int sm_count, int warps_per_cta, const int *cells, int ncells, int tier,
                           cudaStream_t st) {
     (void)warps_per_cta;
-    // the rare large cells (tiers 1, 2) always take the batched form
+    // FP32 with vg_config.split = 1: tier 0 holds 16 vertices a cell (two
+    // per lane), fewer registers and slots per lane than 32, and hands the
+    // larger cells to an FP32 tier 1 of 32 (the block bound kept: the cells
+    // that reach far, as at a cluster's surface, are the ones with many
+    // vertices); split = 0: tier 0 holds 32, as the FP64 form.  The rare
+    // large cells (tiers 1, 2) always take the batched form.
+    const bool small0 = precision != VG_FP64 && p.split;
     if (tier == 2) return launch2_t<double, 32, 64, true>(s, o, p, off, ticket, sm_count, cells, ncells, tier, st);
-    if (tier == 1) return launch2_t<double, 16, 64, true>(s, o, p, off, ticket, sm_count, cells, ncells, tier, st);
+    if (tier == 1)
+        return small0 ? launch2_t<float, 8, 32, true>(s, o, p, off, ticket, sm_count, cells, ncells, tier, st)
+                      : launch2_t<double, 16, 64, true>(s, o, p, off, ticket, sm_count, cells, ncells, tier, st);
     const bool batch = s.nsys > 1;
     if (precision == VG_FP64)
         return batch ? launch2_t<double, 8, 32, true>(s, o, p, off, ticket, sm_count, cells, ncells, 0, st)
                      : launch2_t<double, 8, 32, false>(s, o, p, off, ticket, sm_count, cells, ncells, 0, st);
+    if (small0)
+        return batch ? launch2_t<float, 8, 16, true>(s, o, p, off, ticket, sm_count, cells, ncells, 0, st)
+                     : launch2_t<float, 8, 16, false>(s, o, p, off, ticket, sm_count, cells, ncells, 0, st);
     return batch ? launch2_t<float, 8, 32, true>(s, o, p, off, ticket, sm_count, cells, ncells, 0, st)
                  : launch2_t<float, 8, 32, false>(s, o, p, off, ticket, sm_count, cells, ncells, 0, st);
 }

@@ -103,6 +103,7 @@ struct Params {
     const float *kblock;   // per-block candidate target from the MLP, or null
     const float *rhoblk;   // per-block prefetch radius (prefetch_rho), or null
     double clip;           // clipped cells: cube side, 0 = none
+    int split;             // vg_config.split (host side: which kernels run)
 };
 
 // Hardware approximations (PTX rcp/sqrt/lg2/ex2 .approx, a few ulps) where
