@@ -45,10 +45,14 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         if (not force and os.path.exists(obj) and os.path.getmtime(obj) >= os.path.getmtime(src)
                 and os.path.getmtime(obj) >= newest_hdr):
             return obj, ""
-        cmd = [nvcc] + _flags(extra) + ["-c", src, "-o", obj]
+        # compiled under a name of this process's own, then moved into place:
+        # ranks that build at once never read a half-written object
+        tmp = obj + f".{os.getpid()}.tmp"
+        cmd = [nvcc] + _flags(extra) + ["-c", src, "-o", tmp]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")
+        os.replace(tmp, obj)
         return obj, r.stderr
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
