@@ -281,7 +281,7 @@ def batched_run(V, torch, stream, flush, mlp, steps: int = 5, seed: int = 5):
     systems = W.batched_systems(256, 1000, 200_000, seed=seed)
     t0 = time.perf_counter()
     cache = A.Cache(TUNE_CACHE)
-    key = "batched256-seed%d-nopt48" % seed
+    key = "batched256-seed%d-perclass" % seed
     tb = cache.get(key)
     if tb is None:
         tb = A.tune_batch(systems, torch, cache, predictor=mlp, mlp_args=(MLP_ALPHA, MLP_KMIN, MLP_KMAX))
@@ -292,10 +292,14 @@ def batched_run(V, torch, stream, flush, mlp, steps: int = 5, seed: int = 5):
     counts = [x.n for x in systems]
     pos = torch.from_numpy(np.concatenate([x.pos for x in systems])).cuda()
     ctx = V.vg_batch_create(3, descs, stream=stream)
+    hot = tb["launch"].get("hot_classes")
     try:
         cfg = A.config_from(tb["launch"])
         if cfg.use_mlp:
             V.vg_set_predictor(ctx, mlp, MLP_ALPHA, MLP_KMIN, MLP_KMAX)
+        if hot is not None:
+            for k, c in enumerate(tb["classes"]):
+                V.vg_set_system_split(ctx, k, int(c in hot))
         V.vg_graph_capture(ctx, counts, pos, None, cfg)
         for _ in range(3):
             V.vg_graph_launch(ctx)
@@ -318,6 +322,9 @@ def batched_run(V, torch, stream, flush, mlp, steps: int = 5, seed: int = 5):
                 pos_t = torch.from_numpy(np.concatenate([systems[k].pos for k in idx])).cuda()
                 if cfg.use_mlp:
                     V.vg_set_predictor(sub, mlp, MLP_ALPHA, MLP_KMIN, MLP_KMAX)
+                if hot is not None:
+                    for j, k in enumerate(idx):
+                        V.vg_set_system_split(sub, j, int(tb["classes"][k] in hot))
                 V.vg_graph_capture(sub, [counts[k] for k in idx], pos_t, None, cfg)
                 V.vg_graph_launch(sub)
                 V.vg_graph_sync(sub)
@@ -330,7 +337,8 @@ def batched_run(V, torch, stream, flush, mlp, steps: int = 5, seed: int = 5):
         return {"value": n * steps / (sum(ms) / 1000.0), "unit": "cells/s", "steps": steps,
                 "ms_per_step": sum(ms) / steps, "cells_per_step": n, "systems": len(systems),
                 "mix": mix, "n_opt_by_class": per_class, "by_distribution": by_tag,
-                "launch": {k: tb["launch"].get(k, 0) for k in ("order", "warps_per_cta", "chunk", "use_mlp", "split")},
+                "launch": {k: tb["launch"].get(k, 0) for k in ("order", "warps_per_cta", "chunk", "use_mlp", "split")}
+                | ({"hot_classes": hot} if hot is not None else {}),
                 "tuning_seconds": tune_s,
                 "form": "FP32 cuts + FP64 re-test, autotuned N_opt, launch and preload (fixed or learned), "
                         "one graph replay",

@@ -349,6 +349,18 @@ vg_status vg_get_sort_ms(vg_ctx *ctx, double *total_ms, int64_t *count);
 vg_status vg_get_deferred(vg_ctx *ctx, int64_t *count);
 
 /*
+ * Batched 3D containers, FP32 prefetch form with vg_config.split = 1: which
+ * kernel computes the cells of system k.  split = 1 (the default for every
+ * system): the kernel built for the common path, as for a single system;
+ * 0: the general kernel computes all of the system's cells (better for
+ * systems whose cells outgrow their preload, as clustered ones; the
+ * autotuner chooses per distribution class).  Kept until changed, also in
+ * a captured graph.  The cells are the same either way.  Synchronises the
+ * context's stream.  VG_ERR_ARG for k out of range or split not 0 or 1.
+ */
+vg_status vg_set_system_split(vg_ctx *ctx, int k, int split);
+
+/*
  * The sorted container: block_start has B+1 entries (B = product of the
  * block counts; for a batched container the sum over systems, system k's
  * blocks following those of systems < k) and order[k] is the input index of

@@ -172,9 +172,10 @@ def tune_batch(systems, torch, cache: Cache | None = None, sample_frac: float = 
     """Parameters for a batch of systems: N_opt per distribution class (tuned
     on the class's largest system with the default launch), then the launch
     parameters (order, warps per CTA, chunk, the hot/general kernel split of
-    the prefetch form, and with a `predictor` handle fixed or learned preload
-    targets, `mlp_args` = (alpha, kmin, kmax)) on a
-    sample of the whole batch with those grids.  Returns {"n_opt": [...],
+    the prefetch form, for the whole batch or per distribution class
+    (`launch["hot_classes"]`: the classes on the hot kernel), and with a
+    `predictor` handle fixed or learned preload targets, `mlp_args` =
+    (alpha, kmin, kmax)) on a sample of the whole batch with those grids.  Returns {"n_opt": [...],
     "launch": {...}, "classes": [...]}."""
     classes = [distribution_class(x.pos, x.lo, x.hi) for x in systems]
     n_opt_of = {}
@@ -217,6 +218,20 @@ def tune_batch(systems, torch, cache: Cache | None = None, sample_frac: float = 
                             ms = _time_subset(ctx, sample, _cfg(order, w, ch, um, sp), reps)
                             table.append({"order": order, "warps_per_cta": w, "chunk": ch, "use_mlp": um,
                                           "split": sp, "ms": ms})
+        # 3D prefetch: the kernel split per distribution class (some classes
+        # on the kernel built for the common path, the rest on the general
+        # one), at the best launch so far
+        best = min(table, key=lambda r: r["ms"])
+        cls_set = sorted(set(classes))
+        if best["order"] == "prefetch" and systems[0].dim == 3 and len(cls_set) > 1:
+            for mask in range(1, (1 << len(cls_set)) - 1):
+                hot = [c for b, c in enumerate(cls_set) if (mask >> b) & 1]
+                for k, c in enumerate(classes):
+                    V.vg_set_system_split(ctx, k, int(c in hot))
+                cfg = _cfg("prefetch", best["warps_per_cta"], best["chunk"], best["use_mlp"], 1)
+                ms = _time_subset(ctx, sample, cfg, reps)
+                table.append({"order": "prefetch", "warps_per_cta": best["warps_per_cta"], "chunk": best["chunk"],
+                              "use_mlp": best["use_mlp"], "split": 1, "hot_classes": hot, "ms": ms})
     finally:
         V.vg_destroy(ctx)
     launch = min(table, key=lambda r: r["ms"])

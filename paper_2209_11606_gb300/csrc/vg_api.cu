@@ -6,6 +6,7 @@
 // system after system, so one counting sort and one persistent cell launch
 // (cells taken from one atomic work queue) serve all of them.
 #include <math.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -519,6 +520,7 @@ vg_status vg_create(vg_ctx **out, int dim, const double *lo, const double *hi, c
     vg_status s = new_context(&c, dim, stream);
     if (s != VG_OK) return s;
     Sys sy{};
+    sy.hot = 1;
     for (int a = 0; a < dim; a++) {
         sy.g.lo[a] = lo[a];
         sy.g.hi[a] = hi[a];
@@ -560,6 +562,7 @@ vg_status vg_batch_create(vg_ctx **out, int dim, int nsys, const vg_system *syst
     for (int k = 0; k < nsys; k++) {
         const vg_system &in = systems[k];
         Sys sy{};
+        sy.hot = 1;
         for (int a = 0; a < dim; a++) {
             sy.g.lo[a] = in.lo[a];
             sy.g.hi[a] = in.hi[a];
@@ -949,6 +952,21 @@ vg_status vg_get_sort_ms(vg_ctx *c, double *total_ms, int64_t *count) {
     *total_ms = t;
     *count = c->nsev;
     c->nsev = 0;
+    return VG_OK;
+}
+
+vg_status vg_set_system_split(vg_ctx *c, int k, int split) {
+    if (!c || k < 0 || k >= (int)c->sys.size() || (split != 0 && split != 1)) return VG_ERR_ARG;
+    c->sys[k].hot = split;
+    // both device copies: the descriptor each insert starts from and the one
+    // the cell kernels read (a captured graph reads them at every replay)
+    const size_t at = sizeof(Sys) * (size_t)k + offsetof(Sys, hot);
+    for (Sys *d : {c->d_sys_init, c->d_sys}) {
+        if (!d) continue;
+        VG_CUDA(cudaMemcpyAsync(reinterpret_cast<char *>(d) + at, &c->sys[k].hot, sizeof(int),
+                                cudaMemcpyHostToDevice, c->stream));
+    }
+    VG_CUDA(cudaStreamSynchronize(c->stream));
     return VG_OK;
 }
 

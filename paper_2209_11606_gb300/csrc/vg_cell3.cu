@@ -627,6 +627,17 @@ __global__ void VG_BOUNDS
                     if (gl == 0) S.sys_id = sidx;
                     __syncwarp(gmask);
                 }
+                if constexpr (HOT) {
+                    // a system marked for the general kernel: all its cells go there
+                    if (!S.sysc.hot) {
+                        if (gl == 0) {
+                            const int slot = atomicAdd(o.retry0_count, 1);
+                            o.retry0[slot] = i;
+                        }
+                        __syncwarp(gmask);
+                        continue;
+                    }
+                }
             }
             const int kh = __ldg(&st.sblk[i]);
             const int khl = kh - (int)SY.blk_base;

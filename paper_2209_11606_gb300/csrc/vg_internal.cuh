@@ -47,7 +47,9 @@ struct Sys {
     long long p_base;     // first particle, input order (systems concatenated)
     long long n;          // particles
     double rmax;          // largest radius (0 for plain Voronoi)
-    int off_base, off_count, off_shell, pad;
+    int off_base, off_count, off_shell;
+    int hot;              // 3D FP32 prefetch, split = 1, batched: 0 sends every
+                          // cell of this system to the general kernel
 };
 
 // Sorted particle store written by the counting sort.

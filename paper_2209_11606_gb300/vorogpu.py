@@ -29,7 +29,7 @@ VG_CELL_OK, VG_CELL_EMPTY, VG_CELL_CAP, VG_CELL_DUP, VG_CELL_LIMIT = 0, 1, 2, 3,
 EXPORTS = ["vg_config_default", "vg_create", "vg_batch_create", "vg_insert", "vg_batch_insert",
            "vg_compute", "vg_compute_subset", "vg_get_counts", "vg_get_cells", "vg_get_faces", "vg_get_work",
            "vg_get_radius", "vg_get_weinberg", "vg_get_sorted", "vg_get_grid", "vg_get_system_grid", "vg_get_launches",
-           "vg_get_kernel_ms", "vg_get_sort_ms", "vg_get_deferred", "vg_graph_capture", "vg_graph_launch", "vg_graph_sync",
+           "vg_get_kernel_ms", "vg_get_sort_ms", "vg_get_deferred", "vg_set_system_split", "vg_graph_capture", "vg_graph_launch", "vg_graph_sync",
            "vg_sort_blocks_noalloc", "vg_last_error", "vg_destroy",
            "vg_mlp_create", "vg_mlp_destroy", "vg_mlp_last_error", "vg_mlp_set_params",
            "vg_mlp_get_params", "vg_mlp_features", "vg_mlp_labels", "vg_mlp_dataset",
@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH):
         "vg_get_kernel_ms": (I, [P, ctypes.POINTER(D), ctypes.POINTER(L)]),
         "vg_get_sort_ms": (I, [P, ctypes.POINTER(D), ctypes.POINTER(L)]),
         "vg_get_deferred": (I, [P, ctypes.POINTER(L)]),
+        "vg_set_system_split": (I, [P, I, I]),
         "vg_get_sorted": (I, [P, ctypes.POINTER(L), P, P, I]),
         "vg_get_grid": (I, [P, P]),
         "vg_get_system_grid": (I, [P, I, P]),
@@ -378,6 +379,10 @@ def vg_get_deferred(ctx):
     v = ctypes.c_int64()
     _check(ctx, load().vg_get_deferred(ctx, ctypes.byref(v)))
     return v.value
+
+
+def vg_set_system_split(ctx, k, split):
+    _check(ctx, load().vg_set_system_split(ctx, int(k), int(split)))
 
 
 def vg_get_launches(ctx):

@@ -67,3 +67,50 @@ def test_split_gives_the_oracles_cells(name):
     assert gen["deferred"] == 0
     share = hot["deferred"] / s.n
     assert lo_share <= share <= hi_share, (name, hot["deferred"], s.n)
+
+
+def test_per_system_split_in_a_batch():
+    # a batch of three systems with the middle one marked for the general
+    # kernel: all of its cells are handed over, every system's cells equal
+    # the oracle's, and the whole batch equals the all-hot one bit for bit
+    from paper_2209_11606_gb300 import vorogpu as V
+    from tests.test_gpu_batch import slice_system
+    systems = [W.uniform(6000, 3, 6000 ** (1 / 3), True, seed=64),
+               W.extreme_clustering(4000, 3, seed=65),
+               W.fcc(6, 1.0, 0.05, seed=66)]
+    descs = [V.vg_system(s.lo, s.hi, s.periodic, n_opt=4.6) for s in systems]
+    pos = np.ascontiguousarray(np.concatenate([s.pos for s in systems]))
+    counts = [s.n for s in systems]
+    outs = []
+    for marks in ((1, 1, 1), (1, 0, 1)):
+        ctx = V.vg_batch_create(3, descs)
+        try:
+            for k, m in enumerate(marks):
+                V.vg_set_system_split(ctx, k, m)
+            V.vg_batch_insert(ctx, counts, pos)
+            V.vg_compute(ctx, V._make_cfg("fp32", "prefetch", False, {"split": 1}))
+            out = V._fetch(ctx, pos.shape[0], 3, False)
+            out["deferred"] = V.vg_get_deferred(ctx)
+            out["grids"] = [V.vg_get_system_grid(ctx, k, 3) for k in range(3)]
+            outs.append(out)
+        finally:
+            V.vg_destroy(ctx)
+    assert outs[1]["deferred"] >= systems[1].n
+    base = 0
+    for k, s in enumerate(systems):
+        ref = oracle.compute(s.pos, s.lo, s.hi, s.periodic, nblocks=outs[1]["grids"][k])
+        rep = compare(slice_system(outs[1], base, s.n), ref, 1e-5)
+        assert rep["topology_ok"] and rep["values_ok"], (k, rep)
+        base += s.n
+    for key in ("nv", "ne", "nf", "status", "face_off", "nbr_id", "face_order"):
+        np.testing.assert_array_equal(outs[0][key], outs[1][key])
+    with pytest.raises(V.VgError):
+        _bad_split(V, descs)
+
+
+def _bad_split(V, descs):
+    ctx = V.vg_batch_create(3, descs)
+    try:
+        V.vg_set_system_split(ctx, 3, 1)  # no system 3
+    finally:
+        V.vg_destroy(ctx)
