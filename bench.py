@@ -83,6 +83,8 @@ METRIC_2D = "2D Voronoi cells/s, 1 GB300, chosen vs plain FP64 form; % of roofli
 # FP32 peak derived from unit counts and clock: 152 SMs x 128 FP32 lanes x
 # 2 FLOP (FMA) x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# GB300's nominal dense FP64 rate (its FP64 units are few; no measured peak)
+FP64_PEAK_TFLOPS = 1.25
 # algorithmic FLOP per unit of work: a vertex tested against a plane (3 FMA),
 # a candidate (offset, |q|^2, plane constant), a new vertex (Cramer's rule on
 # three planes), a fan tetrahedron of the statistics (determinant, centroid,
@@ -594,6 +596,15 @@ def main():
         return
 
     # ---- work counters -> algorithmic FLOPs of the cell kernels ----------------
+    def flop_of(w, ne, nf):
+        if dim == 3:
+            fan = 2 * ne.astype(np.int64) - 2 * nf.astype(np.int64)
+            return (FLOP_VTEST * w["v"].astype(np.int64).sum() + FLOP_CAND * w["t"].astype(np.int64).sum() +
+                    FLOP_NEWV * w["nv"].astype(np.int64).sum() + FLOP_FANTET * fan.sum())
+        # 2D: 4 per vertex test, 8 per candidate, 12 per new vertex, 6 per shoelace term
+        return (4 * w["v"].astype(np.int64).sum() + 8 * w["t"].astype(np.int64).sum() +
+                12 * w["nv"].astype(np.int64).sum() + 6 * ne.astype(np.int64).sum())
+
     def work(c):
         c.collect_stats = 1
         V.vg_insert(ctx, pos_d, rad_d)
@@ -609,14 +620,7 @@ def main():
     ne = np.zeros(n, np.int32)
     nf = np.zeros(n, np.int32)
     V.vg_get_cells(ctx, ne=ne, nf=nf)
-    if dim == 3:
-        fan = 2 * ne.astype(np.int64) - 2 * nf.astype(np.int64)
-        flop = (FLOP_VTEST * w["v"].astype(np.int64).sum() + FLOP_CAND * w["t"].astype(np.int64).sum() +
-                FLOP_NEWV * w["nv"].astype(np.int64).sum() + FLOP_FANTET * fan.sum())
-    else:
-        # 2D: 4 per vertex test, 8 per candidate, 12 per new vertex, 6 per shoelace term
-        flop = (4 * w["v"].astype(np.int64).sum() + 8 * w["t"].astype(np.int64).sum() +
-                12 * w["nv"].astype(np.int64).sum() + 6 * ne.astype(np.int64).sum())
+    flop = flop_of(w, ne, nf)
     kern_avg_ms = kern_ms / max(kern_n, 1)
     achieved = flop / (kern_avg_ms / 1000.0) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -670,22 +674,42 @@ def main():
                    "alpha": MLP_ALPHA, "trained": mlp_meta}
 
     # ---- the same step in other forms (graph replays) ---------------------------
-    def form_rate(order, use_mlp, precision=V.VG_FP32_RETEST, reps=5):
+    def form_rate(order, use_mlp, precision=V.VG_FP32_RETEST, reps=5, kernel_ms=False):
         c2 = V.vg_config_default()
         c2.precision, c2.order, c2.use_mlp = precision, order, use_mlp
         c2.clip = clip
+        c2.time_kernels = 1 if kernel_ms else 0
         V.vg_graph_capture(ctx, [n], pos_d, rad_d, c2)
         V.vg_graph_launch(ctx)
         V.vg_graph_sync(ctx)
+        V.vg_get_kernel_ms(ctx)  # reset
         ms = graph_steps(V, torch, ctx, stream, flush, reps)
-        return n * reps / (sum(ms) / 1000.0)
+        rate = n * reps / (sum(ms) / 1000.0)
+        if not kernel_ms:
+            return rate
+        km, kn = V.vg_get_kernel_ms(ctx)
+        return rate, km / max(kn, 1)
 
     forms = {}
     if not args.no_forms and (learned_on or chosen_order != "walk"):
         forms["fp32_walk"] = form_rate(V.VG_WALK, 0)
     if not args.no_forms and dim == 3 and (learned_on or chosen_order != "prefetch"):
         forms["fp32_prefetch_fixed_k72"] = form_rate(V.VG_PREFETCH, 0)
-    plain64 = None if args.no_plain else form_rate(V.VG_WALK, 0, V.VG_FP64, reps=1 if big else 3)
+    plain64, plain_roof = None, None
+    if not args.no_plain:
+        plain64, plain_ms = form_rate(V.VG_WALK, 0, V.VG_FP64, reps=1 if big else 3, kernel_ms=True)
+        if not big:
+            # the plain form against the FP64 rate: its own work counters
+            cp = V.vg_config_default()
+            cp.precision, cp.order, cp.clip = V.VG_FP64, V.VG_WALK, clip
+            wp, _ = work(cp)
+            nep, nfp = np.zeros(n, np.int32), np.zeros(n, np.int32)
+            V.vg_get_cells(ctx, ne=nep, nf=nfp)
+            fp = flop_of(wp, nep, nfp)
+            ach = fp / (plain_ms / 1000.0) / 1e12
+            plain_roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
+                          "frac": ach / FP64_PEAK_TFLOPS, "kernel_ms": plain_ms, "flop_per_cell": fp / n,
+                          "peak_source": "nominal FP64 rate of GB300 (no measured FP64 peak)"}
 
     # ---- end to end through the public API, host buffers -----------------------
     e2e = None
@@ -731,7 +755,8 @@ def main():
                     "(3 capacity tiers), face CSR",
             "roofline": roof,
             "plain_fp64": None if plain64 is None else
-            {"value": plain64, "unit": "cells/s", "form": "FP64 everywhere, block walk (Sec. 2.1.3), graph replay"},
+            {"value": plain64, "unit": "cells/s", "form": "FP64 everywhere, block walk (Sec. 2.1.3), graph replay",
+             "roofline": plain_roof},
             "chosen_vs_plain": None if plain64 is None else value / world / plain64,
             "forms": forms, "learned_preload": learned,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
