@@ -54,8 +54,11 @@ struct WbSmem {
     unsigned char frotn[WB_D];
     unsigned char frotp[WB_D];
     unsigned char flist[WB_D];
-    unsigned char lab[32][WB_V];     // per lane: labels of merged vertices
-    unsigned used[32][WB_D / 32];    // per lane: darts traversed
+    // per lane: labels of merged vertices and the darts traversed; the rows
+    // are padded to an odd number of words, so that the lanes of a warp,
+    // each in its own row, fall in different shared-memory banks
+    unsigned char lab[32][WB_V + 4];
+    unsigned used[32][WB_D / 32 + 1];
     unsigned short best[WB_D + 1];   // best code so far
 };
 
