@@ -23,9 +23,12 @@
 // after it.  The code lists the labels (order of first visit, from 1) of
 // the start and of every arrival: 2E + 1 entries.  The cell's code is the
 // lexicographic minimum over every start dart and both rotation directions.
-// The 32 lanes run 32 traversals in lockstep; at every step the lanes above
-// the warp's minimum label drop, and the survivors are compared with the
-// best code of earlier rounds as they go, so no lane stores a code.
+// Every (start, direction) first runs 8 steps, 32 at a time; the minimal
+// code begins with the minimal 8-label prefix, so only the starts that have
+// it are traced in full.  Those run 32 at a time in lockstep; at every step
+// the lanes above the warp's minimum label drop, and the survivors are
+// compared with the best code of earlier rounds as they go, so no lane
+// stores a code.
 // Outputs: darts traversed (2E; 0 = no code), an FNV-1a 64 hash of the
 // minimal code (labels as two little-endian bytes each) and the number of
 // (start, orientation) pairs that reach it.
@@ -37,6 +40,7 @@ namespace {
 constexpr int WB_V = 64;            // vertices of a tier-0 cell
 constexpr int WB_D = 3 * WB_V;      // darts
 constexpr int WB_WARPS = 4;
+constexpr int WB_PL = 8;            // labels in a start's prefix key
 constexpr unsigned WB_EMPTY = 0xffffffffu;
 
 struct WbSmem {
@@ -240,41 +244,100 @@ __global__ void __launch_bounds__(32 * WB_WARPS) k_weinberg(const unsigned *__re
         if (ok) {
             bool have = false, stuck = false;
             const int NT = 2 * Dm;
-            for (int r0 = 0; r0 < NT; r0 += 32) {
-                const int q = r0 + lane;
-                bool active = q < NT;
-                const int o = q >= Dm ? 1 : 0;  // rotation direction
-                int d = S.flist[active ? q % Dm : 0];
+            // one step of a traversal in direction o: mark dart d, label its
+            // head, choose the next dart (-1: none left)
+            auto step = [&](int d, int o, int &nl, int &L, int &nd) {
+                S.used[lane][d >> 5] |= 1u << (d & 31);
+                const int y = S.cl[S.dto[d]], rv = S.frev[d];
+                const unsigned char *rot = o ? S.frotp : S.frotn;
+                nd = -1;
+                if (!S.lab[lane][y]) {
+                    S.lab[lane][y] = (unsigned char)(++nl);
+                    L = nl;
+                    nd = rot[rv];
+                } else {
+                    L = S.lab[lane][y];
+                    if (!((S.used[lane][rv >> 5] >> (rv & 31)) & 1)) {
+                        nd = rv;
+                    } else {
+                        int e = rot[rv];
+                        for (int guard = 0; ((S.used[lane][e >> 5] >> (e & 31)) & 1) && e != rv && guard < Dm; guard++)
+                            e = rot[e];
+                        if (!((S.used[lane][e >> 5] >> (e & 31)) & 1)) nd = e;
+                    }
+                }
+            };
+            auto reset = [&](int d) {
                 for (int v = 0; v < WB_V; v += 4) *reinterpret_cast<unsigned *>(&S.lab[lane][v]) = 0u;
 #pragma unroll
                 for (int w = 0; w < WB_D / 32; w++) S.used[lane][w] = 0u;
-                int nl = 1;
                 S.lab[lane][S.cl[d / 3]] = 1;
+            };
+            // phase 1: the first WB_PL labels of every (start dart, direction),
+            // as a key (first label most significant).  The minimal code starts
+            // with the minimal key, so only the starts that have it are traced
+            // in full.  Keys and the start list use the plane-pair table's
+            // storage, free once the dart tables are built.
+            unsigned *khi = reinterpret_cast<unsigned *>(&S.pair[0][0]);
+            unsigned *klo = khi + 2 * WB_D;
+            unsigned short *slist = reinterpret_cast<unsigned short *>(klo + 2 * WB_D);
+            for (int r0 = 0; r0 < NT; r0 += 32) {
+                const int q = r0 + lane;
+                const bool act = q < NT;
+                const int o = q >= Dm ? 1 : 0;
+                int d = S.flist[act ? q % Dm : 0];
+                reset(d);
+                __syncwarp();
+                int nl = 1;
+                unsigned hi = 0, lo = 0;
+                bool live = act;
+#pragma unroll 1
+                for (int k = 0; k < WB_PL; k++) {
+                    int L = 0xff, nd = -1;
+                    if (live && k < Dm) {
+                        step(d, o, nl, L, nd);
+                        if (nd >= 0) d = nd; else live = false;
+                    }
+                    const unsigned b = (unsigned)min(L, 0xff);
+                    if (k < 4) hi |= b << (24 - 8 * k);
+                    else lo |= b << (24 - 8 * (k - 4));
+                }
+                if (act) { khi[q] = hi; klo[q] = lo; }
+                __syncwarp();
+            }
+            // the minimal key and the starts that have it
+            unsigned mh = 0xffffffffu, ml = 0xffffffffu;
+            for (int q = lane; q < NT; q += 32) {
+                const unsigned h = khi[q], l = klo[q];
+                if (h < mh || (h == mh && l < ml)) { mh = h; ml = l; }
+            }
+            const unsigned gmh = __reduce_min_sync(FULL, mh);
+            const unsigned gml = __reduce_min_sync(FULL, mh == gmh ? ml : 0xffffffffu);
+            int NS = 0;
+            for (int r0 = 0; r0 < NT; r0 += 32) {
+                const int q = r0 + lane;
+                const bool keep = q < NT && khi[q] == gmh && klo[q] == gml;
+                const unsigned m = __ballot_sync(FULL, keep);
+                if (keep) slist[NS + __popc(m & lt)] = (unsigned short)q;
+                NS += __popc(m);
+            }
+            __syncwarp();
+            // phase 2: those starts in full, 32 at a time in lockstep
+            for (int r0 = 0; r0 < NS; r0 += 32) {
+                const int j = r0 + lane;
+                bool active = j < NS;
+                const int q = slist[active ? j : 0];
+                const int o = q >= Dm ? 1 : 0;  // rotation direction
+                int d = S.flist[q % Dm];
+                reset(d);
+                int nl = 1;
                 int cmp = have ? 0 : -1;  // 0: equal to the best so far, -1: below it
                 if (!have && lane == 0) S.best[0] = 1;
                 __syncwarp();
                 for (int k = 0; k < Dm; k++) {
                     int L = 0xffff, nd = -1;
                     if (active) {
-                        S.used[lane][d >> 5] |= 1u << (d & 31);
-                        const int y = S.cl[S.dto[d]], rv = S.frev[d];
-                        const unsigned char *rot = o ? S.frotp : S.frotn;
-                        if (!S.lab[lane][y]) {
-                            S.lab[lane][y] = (unsigned char)(++nl);
-                            L = nl;
-                            nd = rot[rv];
-                        } else {
-                            L = S.lab[lane][y];
-                            if (!((S.used[lane][rv >> 5] >> (rv & 31)) & 1)) {
-                                nd = rv;
-                            } else {
-                                int e = rot[rv];
-                                for (int guard = 0; ((S.used[lane][e >> 5] >> (e & 31)) & 1) && e != rv && guard < Dm;
-                                     guard++)
-                                    e = rot[e];
-                                if (!((S.used[lane][e >> 5] >> (e & 31)) & 1)) nd = e;
-                            }
-                        }
+                        step(d, o, nl, L, nd);
                         if (k + 1 < Dm && nd < 0) stuck = true;
                     }
                     const unsigned m = __reduce_min_sync(FULL, (unsigned)L);
