@@ -68,11 +68,17 @@ typedef struct {
     double v[OR_MAXFV][3];
 } ofc;
 
+#define OR_MAXX 1024 /* crossing edges of one cut */
+
 typedef struct {
     int nf, cap_hit;
     ofc f[OR_MAXF];
     ofc tmp;
     double np_[OR_MAXNP][3];
+    /* per crossing edge of the current cut: its face, its place in the face
+     * and the plane of the other face that holds it */
+    int nxe, xe_face[OR_MAXX], xe_edge[OR_MAXX];
+    double xe_pl[OR_MAXX][4];
 } cell3;
 
 typedef struct {
@@ -80,9 +86,11 @@ typedef struct {
     double v[OR_MAXV2][2];
     long long lid[OR_MAXV2];  /* label of edge v[i] -> v[i+1] */
     int limg[OR_MAXV2][2];
+    double ln[OR_MAXV2][3];   /* its line n.x = c: n[0], n[1], c */
     double tv[OR_MAXV2][2];
     long long tlid[OR_MAXV2];
     int timg[OR_MAXV2][2];
+    double tln[OR_MAXV2][3];
 } cell2;
 
 typedef struct {
@@ -247,6 +255,32 @@ static void init3(cell3 *cl, const ctx_t *cx, const double *p, long long self) {
     }
 }
 
+static int same3(const double *a, const double *b) { return a[0] == b[0] && a[1] == b[1] && a[2] == b[2]; }
+
+/* Where the edge a-b, on the planes p1 and p2 (n, c each), crosses the cut
+ * plane q.r = c: the point on all three planes (Cramer's rule), so that its
+ * error is relative to the cell, not to the edge, which at first is as long
+ * as the box.  The two edge planes are taken in lexicographic order, so the
+ * two faces that share the edge compute the same point; nearly dependent
+ * planes fall back to interpolating along the edge. */
+static void cross3p(const double *p1, const double *p2, const double *q, double c, const double *a, const double *b,
+                    double da, double db, double *x) {
+    const double *u = p1, *w = p2;
+    for (int k = 0; k < 4; k++) {
+        if (p1[k] < p2[k]) break;
+        if (p1[k] > p2[k]) { u = p2; w = p1; break; }
+    }
+    const double wq[3] = {w[1] * q[2] - w[2] * q[1], w[2] * q[0] - w[0] * q[2], w[0] * q[1] - w[1] * q[0]};
+    const double qu[3] = {q[1] * u[2] - q[2] * u[1], q[2] * u[0] - q[0] * u[2], q[0] * u[1] - q[1] * u[0]};
+    const double uw[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+    const double det = u[0] * wq[0] + u[1] * wq[1] + u[2] * wq[2];
+    if (fabs(det) <= 1e-6 * sqrt(dot3(u, u) * dot3(w, w) * dot3(q, q))) {
+        isect(a, b, da, db, x, 3);
+        return;
+    }
+    for (int k = 0; k < 3; k++) x[k] = (u[3] * wq[k] + w[3] * qu[k] + c * uw[k]) / det;
+}
+
 /* Cut the cell by { r : q.r > c } (Eq. (3)).  Returns 0 if nothing was
  * removed, 1 if the cell changed, 2 if it became empty. */
 static int clip3(cell3 *cl, const double *q, double c, double tau, double eps,
@@ -256,6 +290,30 @@ static int clip3(cell3 *cl, const double *q, double c, double tau, double eps,
         for (int j = 0; j < cl->f[i].nv; j++)
             if (dot3(q, cl->f[i].v[j]) - c > tau) { any = 1; break; }
     if (!any) return 0;
+    /* the crossing edges and, before any face changes, the plane of the
+     * other face holding each (traversed the other way) */
+    cl->nxe = 0;
+    for (int i = 0; i < cl->nf; i++) {
+        const ofc *f = &cl->f[i];
+        for (int j = 0; j < f->nv; j++) {
+            const double *a = f->v[j], *b = f->v[(j + 1) % f->nv];
+            const double da = dot3(q, a) - c, db = dot3(q, b) - c;
+            if (!((da > tau && db < -tau) || (da < -tau && db > tau)) || cl->nxe >= OR_MAXX) continue;
+            int g = -1;
+            for (int i2 = 0; i2 < cl->nf && g < 0; i2++) {
+                if (i2 == i) continue;
+                const ofc *h = &cl->f[i2];
+                for (int j2 = 0; j2 < h->nv; j2++)
+                    if (same3(h->v[j2], b) && same3(h->v[(j2 + 1) % h->nv], a)) { g = i2; break; }
+            }
+            if (g < 0) continue;
+            const int t = cl->nxe++;
+            cl->xe_face[t] = i;
+            cl->xe_edge[t] = j;
+            cl->xe_pl[t][0] = cl->f[g].n[0]; cl->xe_pl[t][1] = cl->f[g].n[1];
+            cl->xe_pl[t][2] = cl->f[g].n[2]; cl->xe_pl[t][3] = cl->f[g].c;
+        }
+    }
     double eps2 = eps * eps;
     int npn = 0, nf = 0;
     for (int i = 0; i < cl->nf; i++) {
@@ -275,7 +333,14 @@ static int clip3(cell3 *cl, const double *q, double c, double tau, double eps,
             }
             if ((da > tau && db < -tau) || (da < -tau && db > tau)) {
                 double x[3];
-                isect(a, b, da, db, x, 3);
+                int t = 0;
+                while (t < cl->nxe && !(cl->xe_face[t] == i && cl->xe_edge[t] == j)) t++;
+                if (t < cl->nxe) {
+                    const double pf[4] = {f->n[0], f->n[1], f->n[2], f->c};
+                    cross3p(pf, cl->xe_pl[t], q, c, a, b, da, db, x);
+                } else {
+                    isect(a, b, da, db, x, 3);
+                }
                 if (k < OR_MAXFV) memcpy(o->v[k], x, sizeof(double) * 3);
                 k++;
                 if (npn < OR_MAXNP) memcpy(cl->np_[npn], x, sizeof(double) * 3);
@@ -343,11 +408,33 @@ static void init2(cell2 *cl, const ctx_t *cx, const double *p, long long self) {
         cl->limg[i][0] = cl->limg[i][1] = 0;
         if (!wall[a]) { cl->lid[i] = self; cl->limg[i][a] = s ? 1 : -1; }
         else cl->lid[i] = -(1 + 2 * a + s);
+        cl->ln[i][0] = a == 0 ? (s ? 1.0 : -1.0) : 0.0;
+        cl->ln[i][1] = a == 1 ? (s ? 1.0 : -1.0) : 0.0;
+        cl->ln[i][2] = s ? hi[a] : -lo[a];
     }
 }
 
+/* Where the edge a-b, on the line n.x = n[2], crosses the cut line
+ * q.x = c: the point on both lines (Cramer's rule), so that its error is
+ * relative to the cell, not to the edge, which at first is as long as the
+ * box; nearly parallel lines fall back to interpolating along the edge. */
+static void cross2(const double *n, const double *q, double c, const double *a, const double *b, double da,
+                   double db, double *x) {
+    const double det = n[0] * q[1] - n[1] * q[0];
+    const double nn = sqrt(n[0] * n[0] + n[1] * n[1]), qn = sqrt(q[0] * q[0] + q[1] * q[1]);
+    if (fabs(det) <= 1e-6 * nn * qn) {
+        isect(a, b, da, db, x, 2);
+        return;
+    }
+    x[0] = (n[2] * q[1] - c * n[1]) / det;
+    x[1] = (n[0] * c - q[0] * n[2]) / det;
+}
+
+static void setln(double *dst, const double *src) { dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2]; }
+
 static int clip2(cell2 *cl, const double *q, double c, double tau, double eps,
                  long long id, const int *img) {
+    const double qc[3] = {q[0], q[1], c};
     int any = 0;
     for (int j = 0; j < cl->nv; j++)
         if (q[0] * cl->v[j][0] + q[1] * cl->v[j][1] - c > tau) { any = 1; break; }
@@ -360,21 +447,26 @@ static int clip2(cell2 *cl, const double *q, double c, double tau, double eps,
         if (da <= tau) {
             /* a stays; the edge leaving it follows the cut line if b is out */
             cl->tv[k][0] = a[0]; cl->tv[k][1] = a[1];
-            if (db > tau) { cl->tlid[k] = id; cl->timg[k][0] = img[0]; cl->timg[k][1] = img[1]; }
-            else { cl->tlid[k] = cl->lid[j]; cl->timg[k][0] = cl->limg[j][0]; cl->timg[k][1] = cl->limg[j][1]; }
+            if (db > tau) { cl->tlid[k] = id; cl->timg[k][0] = img[0]; cl->timg[k][1] = img[1]; setln(cl->tln[k], qc); }
+            else {
+                cl->tlid[k] = cl->lid[j]; cl->timg[k][0] = cl->limg[j][0]; cl->timg[k][1] = cl->limg[j][1];
+                setln(cl->tln[k], cl->ln[j]);
+            }
             k++;
             if (da < -tau && db > tau) {
                 /* leaving: the crossing point, then along the cut line */
-                isect(a, b, da, db, cl->tv[k], 2);
-                cl->tlid[k] = id; cl->timg[k][0] = img[0]; cl->timg[k][1] = img[1];
+                cross2(cl->ln[j], q, c, a, b, da, db, cl->tv[k]);
+                cl->tlid[k] = id; cl->timg[k][0] = img[0]; cl->timg[k][1] = img[1]; setln(cl->tln[k], qc);
                 /* the edge a->x keeps the old label, x->... follows the cut */
                 cl->tlid[k - 1] = cl->lid[j]; cl->timg[k - 1][0] = cl->limg[j][0]; cl->timg[k - 1][1] = cl->limg[j][1];
+                setln(cl->tln[k - 1], cl->ln[j]);
                 k++;
             }
         } else if (db < -tau) {
             /* entering: the crossing point, then along the old edge */
-            isect(a, b, da, db, cl->tv[k], 2);
+            cross2(cl->ln[j], q, c, a, b, da, db, cl->tv[k]);
             cl->tlid[k] = cl->lid[j]; cl->timg[k][0] = cl->limg[j][0]; cl->timg[k][1] = cl->limg[j][1];
+            setln(cl->tln[k], cl->ln[j]);
             k++;
         }
     }
@@ -384,10 +476,12 @@ static int clip2(cell2 *cl, const double *q, double c, double tau, double eps,
     for (int i = 0; i < k; i++) {
         if (m > 0 && dist2(cl->tv[i], cl->v[m - 1], 2) <= eps2) {
             cl->lid[m - 1] = cl->tlid[i]; cl->limg[m - 1][0] = cl->timg[i][0]; cl->limg[m - 1][1] = cl->timg[i][1];
+            setln(cl->ln[m - 1], cl->tln[i]);
             continue;
         }
         cl->v[m][0] = cl->tv[i][0]; cl->v[m][1] = cl->tv[i][1];
         cl->lid[m] = cl->tlid[i]; cl->limg[m][0] = cl->timg[i][0]; cl->limg[m][1] = cl->timg[i][1];
+        setln(cl->ln[m], cl->tln[i]);
         m++;
     }
     while (m > 1 && dist2(cl->v[m - 1], cl->v[0], 2) <= eps2) {

@@ -179,12 +179,9 @@ def test_extreme_clustering_3d(precision, order, rtol):
     check(s, (34, 34, 34), precision, order, rtol)
 
 
-# FP64 bar: the oracle places each new vertex by interpolating along the
-# edge it cuts, and the first edges are as long as the box, so a vertex is
-# off by up to about 2^-53 of the box side, 1e-12 of a cell 1e-4 across; its
-# worst cells here are 3.8e-12 from their exact rational areas (the kernel
-# intersects the two lines, whose error does not grow with the edge)
-@pytest.mark.parametrize("precision,order,rtol", [("fp64", "walk", 1e-10), ("fp32", "walk", 1e-5)])
+# both sides place each 2D vertex where its two lines cross, so the FP64
+# form holds the 1e-12 bar on cells far smaller than the box
+@pytest.mark.parametrize("precision,order,rtol", [("fp64", "walk", 1e-12), ("fp32", "walk", 1e-5)])
 def test_extreme_clustering_2d(precision, order, rtol):
     # Sec. 3.1 'extreme clustering' in 2D: cells near the centre are 1e-4 of
     # a block side and smaller, where block-relative FP32 positions carry
@@ -202,12 +199,14 @@ def test_localized_2d_fine_grid(precision, order, rtol):
     check(s, (200, 200), precision, order, rtol)
 
 
-# FP64 bar for cells far smaller than the mean spacing s: the on-plane
-# tolerance is tau_rel * s, absolute, so a vertex that one side keeps on a
-# plane and the other cuts moves a volume by up to about tau_rel * s / R
-# relative, 3e-8 for these cells (R about 3e-4 s)
-CORNER_FORMS = [(3, "fp64", "walk", 1e-7), (3, "fp32", "walk", 1e-5), (3, "fp32", "prefetch", 1e-5),
-                (2, "fp64", "walk", 1e-7), (2, "fp32", "walk", 1e-5)]
+# FP64 bars: both sides place each vertex on its planes (lines in 2D), so
+# neither error grows with the box, and the 2D cells hold 1e-12.  In 3D the
+# background cells beside the cluster carry its tiny faces, whose vertices
+# lie where planes of cluster particles 1e-4 of a block apart meet, nearly
+# parallel: a condition number of some 1e4-1e5 on both sides puts those
+# cells' volumes 4e-11 apart (the cluster's own cells agree to 1e-12)
+CORNER_FORMS = [(3, "fp64", "walk", 1e-10), (3, "fp32", "walk", 1e-5), (3, "fp32", "prefetch", 1e-5),
+                (2, "fp64", "walk", 1e-12), (2, "fp32", "walk", 1e-5)]
 
 
 @pytest.mark.parametrize("dim,precision,order,rtol", CORNER_FORMS)

@@ -78,11 +78,10 @@ def test_oracle_exact_on_corner_cluster_cells_2d():
         area, nbrs = _exact_cell_2d(s.pos, i, s.lo, s.hi, cand[np.argsort(d[cand])])
         got = set(r["nbr_id"][r["face_off"][k]:r["face_off"][k + 1]].tolist())
         assert got == nbrs, (i, got, nbrs)
-        # the oracle interpolates each new vertex along the edge it cuts,
-        # and the first edges are as long as the box: a vertex is off by up
-        # to about 2^-53 of the box side, some 1e-10 of these cells (about
-        # 2e-6 across)
-        assert abs(r["vol"][k] - area) <= 1e-9 * area, (i, r["vol"][k], area)
+        # the oracle places each new vertex where its two lines cross, so
+        # its error is relative to the cell (interpolating along the edge,
+        # at first as long as the box, was off by some 1e-10 here)
+        assert abs(r["vol"][k] - area) <= 1e-14 * area, (i, r["vol"][k], area)
     # inside the cluster the cells are 1e-4 of a block (20 blocks per side);
     # one at its edge reaches out into the background
     assert np.median(r["rmax"]) < 1e-4 / 20 and r["rmax"].max() < 1e-2 / 20
