@@ -223,3 +223,20 @@ def test_oracle_exact_on_corner_cluster_cells_3d():
         got = set(r["nbr_id"][r["face_off"][k]:r["face_off"][k + 1]].tolist())
         assert got == nbrs, (i, got, nbrs)
         assert abs(r["vol"][k] - vol) <= 1e-13 * vol, (i, r["vol"][k], vol)
+
+
+def test_oracle_exact_on_uniform_cells_3d():
+    # ordinary cells of a walled uniform set, one of them against walls
+    s = W.uniform(3000, 3, 1.0, False, seed=44)
+    corner = int(np.argmin(np.linalg.norm(s.pos, axis=1)))
+    cells = np.sort(np.array([corner, 1000, 2000]))
+    r = oracle.compute(s.pos, s.lo, s.hi, s.periodic, method="grid", nblocks=(8, 8, 8), cells=cells)
+    for k, i in enumerate(cells):
+        R = r["rmax"][k]
+        d = np.linalg.norm(s.pos - s.pos[i], axis=1)
+        cand = np.nonzero(d < 2.05 * R)[0]
+        assert len(cand) < 80, len(cand)
+        vol, nbrs = _exact_cell_3d(s.pos, i, s.lo, s.hi, cand)
+        got = {x for x in r["nbr_id"][r["face_off"][k]:r["face_off"][k + 1]].tolist() if x >= 0}
+        assert got == nbrs, (i, got, nbrs)
+        assert abs(r["vol"][k] - vol) <= 1e-13 * vol, (i, r["vol"][k], vol)
