@@ -567,12 +567,13 @@ __global__ void k_prefetch_rho(const Sys *__restrict__ sys, int nsys, const int 
 // ---- the kernel ------------------------------------------------------------------
 
 // HOT: the common path only (FP32, prefetch, tier 0).  A cell that needs
-// anything else -- the walk after its preload, FP64 vertices for its
-// statistics (degenerate, ill-conditioned or thin cells) -- is handed on
-// whole, through the deferred list, to the general kernel (tier 3), which
-// computes it from the start.  The hot kernel's code then holds neither the
-// walk nor the FP64 statistics, which keeps it small in the instruction
-// cache.
+// anything else -- the walk after both preloads, FP64 vertices for its
+// statistics (degenerate, ill-conditioned or thin cells), more than 64
+// planes or 32 faces, or a batched system marked for the general kernel --
+// is handed on whole, through the deferred list, to the general kernel
+// (tier 3), which computes it from the start.  The hot kernel's code then
+// holds neither the walk nor the FP64 statistics nor those rare branches,
+// which keeps the path it runs compact in the instruction cache.
 // (the second preload's label is used by the hot instantiation only)
 #pragma nv_diag_suppress 177
 template <typename T, int VPL, int MAXP, bool BATCH, int G, bool TOPO = false, bool HOT = false>
