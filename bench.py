@@ -11,7 +11,7 @@ the CSR compaction of the faces.  L2 is flushed between steps (a 256 MB write
 outside the timed events).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload uniform1m|slabs102m|radical2m|hex10m]
+                    [--workload NAME] [--split 0|1] [--grid NX NY [NZ]] [--weinberg]
 
 With N > 1 (torchrun, one rank per GPU) every rank processes its own system
 (weak scaling, no collective on the data path); value is the cells of all
@@ -19,7 +19,11 @@ ranks over the slowest rank's time.
 
 --workload selects another configuration (no e2e and no batched line there):
 slabs102m, the 102.4M-point periodic cube of alternating perturbed-FCC and
-uniform slabs; radical2m, 2M radical (power) cells; hex10m, 10M 2D cells.
+uniform slabs; radical2m, 2M radical (power) cells; hex10m, 10M 2D cells;
+the paper's cases of Sec. 3.1 in the walled unit cube or square
+(homog3d, local3d, local3d_clip, extreme3d, homog2d, local2d, extreme2d);
+vorotop102m, 102.4M uniform points in the periodic unit cube (with
+--weinberg, VoroTop's case: cells with Weinberg codes).
 
 --impl reference times the FP64 CPU oracle (block-grid walk with the radius
 bound, OpenMP over cells) on this host's cores, on a bounded sample of the
