@@ -11,7 +11,7 @@ the CSR compaction of the faces.  L2 is flushed between steps (a 256 MB write
 outside the timed events).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload NAME] [--split 0|1] [--grid NX NY [NZ]] [--weinberg]
+                    [--workload NAME] [--split 0|1] [--grid N] [--weinberg]
 
 With N > 1 (torchrun, one rank per GPU) every rank processes its own system
 (weak scaling, no collective on the data path); value is the cells of all
@@ -150,9 +150,10 @@ def parse(argv=None):
     ap.add_argument("--grid", type=int, default=0,
                     help="blocks per axis instead of the workload's grid (e.g. a tuned grid)")
     ap.add_argument("--split", type=int, default=1, choices=[0, 1],
-                    help="3D FP32 prefetch: 1 = the hot kernel with deferral, 0 = the general kernel alone")
+                    help="FP32 form: 1 = the kernel built for the common path, handing the rest on "
+                         "(3D: to the general kernel; 2D: from 16 to 32 vertices a cell), 0 = the general kernel alone")
     ap.add_argument("--weinberg", action="store_true",
-                    help="also time the cells with Weinberg codes (Sec. 4), eager calls")
+                    help="also time the cells with Weinberg codes (Sec. 4), graph replays")
     return ap.parse_args(argv)
 
 
