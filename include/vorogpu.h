@@ -127,7 +127,10 @@ typedef struct {
                           are the same (values to rounding) */
 } vg_config;
 
-/* Fills `cfg` with the defaults listed above (FP32_RETEST, PREFETCH). */
+/* Fills `cfg` (caller-owned) with the defaults listed above (FP32_RETEST,
+ * PREFETCH); the arithmetic forms, orders and options are this library's
+ * (the paper computes in FP64 with the block walk of Sec. 2.1.3).  No error
+ * (a NULL cfg is ignored). */
 void vg_config_default(vg_config *cfg);
 
 /*
@@ -175,7 +178,8 @@ vg_status vg_batch_create(vg_ctx **out, int dim, int nsys, const vg_system *syst
  * `radii` (or NULL) likewise.  Cell i and neighbour ids use this
  * concatenated numbering, so system k's cells are the input indices
  * [sum(counts[<k]), sum(counts[<=k])).  Validation and errors as
- * vg_insert(); the per-system n_opt rule fixes the grids here.
+ * vg_insert() (the paper's clear() and add_parallel(), Sec. 2.2.5, for every
+ * system); the per-system n_opt rule (Sec. 2.1.4) fixes the grids here.
  */
 vg_status vg_batch_insert(vg_ctx *ctx, const int64_t *counts, const void *pos,
                           const void *radii, int dtype, int on_device);
@@ -202,12 +206,26 @@ enum {
 vg_status vg_insert(vg_ctx *ctx, int64_t n, const void *pos, const void *radii, int dtype,
                     int on_device);
 
-/* Computes all cells with the given configuration (NULL: defaults). */
+/*
+ * Computes every cell of the inserted particles with the given configuration
+ * (`cfg` read during the call; NULL: defaults): the container box relative
+ * to the particle (Eqs. 1-2) cut by the half-space of Eq. 3 for each
+ * neighbour, visited near to far until the radius bound of Sec. 2.1.3
+ * ends the search, then the statistics of Sec. 2.1.2.  Results stay in the
+ * context until the next compute or insert (read with the vg_get_* calls).
+ * Errors: VG_ERR_STATE before an insert, VG_ERR_ARG for an invalid
+ * configuration (see vg_config), VG_ERR_OOM when a device buffer cannot
+ * grow, VG_ERR_CAP when the face buffer still overflows after growing three
+ * times, VG_ERR_CUDA on another CUDA failure.  A cell that exceeds every
+ * capacity tier is reported VG_CELL_CAP in its status, not as an error.
+ */
 vg_status vg_compute(vg_ctx *ctx, const vg_config *cfg);
 
 /*
  * Computes only the cells of the m input indices in `cells` (host or device
- * int32 per on_device), e.g. a sample for timing a configuration.  The
+ * int32 per on_device, caller-owned), e.g. a sample for timing a
+ * configuration (the method of vg_compute(); the paper's cells are
+ * independent, Sec. 2.2, so a subset is computed the same way).  The
  * per-cell arrays of the listed cells then equal those of vg_compute();
  * those of other cells are unspecified, and vg_get_faces / vg_get_counts
  * return VG_ERR_STATE until the next full compute.  VG_ERR_ARG for an index
@@ -238,26 +256,31 @@ vg_status vg_compute_subset(vg_ctx *ctx, const vg_config *cfg, const int32_t *ce
 vg_status vg_graph_capture(vg_ctx *ctx, const int64_t *counts, const void *pos,
                            const void *radii, int dtype, const vg_config *cfg);
 
-/* Replays the captured graph on the context's stream; asynchronous.
- * VG_ERR_STATE when no graph is held. */
+/* Replays the captured graph (the step of vg_graph_capture(): Sec. 2.1.1
+ * sort, Sec. 2.1.3 cells, Sec. 2.1.2 statistics) on the context's stream;
+ * asynchronous, input errors are read by vg_graph_sync().  VG_ERR_STATE
+ * when no graph is held, VG_ERR_CUDA when the launch fails. */
 vg_status vg_graph_launch(vg_ctx *ctx);
 
 /*
  * Waits for the last replay and reads its flags: VG_ERR_OUT_OF_BOX or
- * VG_ERR_NONFINITE as vg_insert() reports them; if the replay's input made
+ * VG_ERR_NONFINITE as vg_insert() (Sec. 2.2.5) reports them; if the replay's input made
  * more faces than the face buffer holds, the step is redone eagerly with a
  * larger buffer and the graph re-captured (VG_OK, results complete).  The
  * vg_get_* calls do this themselves after a replay.
  */
 vg_status vg_graph_sync(vg_ctx *ctx);
 
-/* Number of cells and total number of faces (edges in 2D) of the last
- * vg_compute(); synchronises the stream. */
+/* Number of cells and total number of faces (edges in 2D; the face list of
+ * Sec. 2.1.2) of the last vg_compute(), written to the caller's host
+ * variables (either may be NULL); synchronises the stream.  VG_ERR_STATE
+ * before a compute or after vg_compute_subset(). */
 vg_status vg_get_counts(vg_ctx *ctx, int64_t *n_cells, int64_t *n_faces);
 
 /*
- * Per-cell outputs, n entries each, in input order (any pointer may be
- * NULL to skip it):
+ * Per-cell statistics of Sec. 2.1.2, n entries each, in input order, into
+ * caller-owned buffers (any pointer may be NULL to skip it); VG_ERR_STATE
+ * before a compute:
  *   vol       volume (3D) or area (2D), FP64
  *   area      total face area (3D) or perimeter (2D), FP64
  *   centroid  n x dim, relative to the particle, FP64
@@ -269,7 +292,9 @@ vg_status vg_get_cells(vg_ctx *ctx, double *vol, double *area, double *centroid,
                        int on_device);
 
 /*
- * Faces as CSR: face_off has n+1 entries; cell i's faces are
+ * The neighbour list and face orders of Sec. 2.1.2, as a CSR in
+ * caller-owned buffers sized by vg_get_counts() (VG_ERR_STATE before a full
+ * compute): face_off has n+1 entries; cell i's faces are
  * [face_off[i], face_off[i+1]) in canonical order, ascending (neighbour id,
  * image shift).  nbr_id is the neighbour's input index, or -1..-6 for the
  * walls x-, x+, y-, y+, z-, z+ of a walled axis; nbr_img is the periodic
@@ -280,8 +305,10 @@ vg_status vg_get_faces(vg_ctx *ctx, int64_t *face_off, int32_t *nbr_id, int8_t *
                        uint8_t *face_order, int on_device);
 
 /*
- * Per-cell work counters of the last vg_compute() with collect_stats = 1,
- * n entries each (any may be NULL): candidates offered to the cut routine,
+ * Per-cell work counters of the last vg_compute() with collect_stats = 1
+ * (the work of Eq. 3's cuts and of the search of Sec. 2.1.3), n entries
+ * each into caller-owned buffers (any may be NULL; VG_ERR_STATE before a
+ * compute): candidates offered to the cut routine,
  * vertex-plane tests, cuts that removed something, vertices those cuts
  * created, FP64 re-tests, how the prefetch form met a shortfall of its
  * preload (0 none, 1 the walk, 2 a second, wider preload), and how many
@@ -323,9 +350,11 @@ vg_status vg_get_radius(vg_ctx *ctx, float *rmax, int on_device);
 vg_status vg_get_weinberg(vg_ctx *ctx, int32_t *len, uint64_t *hash, int32_t *sym, int on_device);
 
 /*
- * Device time of the cell-kernel phase of every vg_compute() made with
+ * Device time of the cell-kernel phase (the cuts and statistics of Sec.
+ * 2.1.2-2.1.3) of every vg_compute() or graph replay made with
  * time_kernels = 1 since the previous call of this function: the sum in
- * milliseconds and the number of computes.  Synchronises the stream.
+ * milliseconds and the number of computes, into the caller's host
+ * variables.  Synchronises the stream.  VG_ERR_ARG for NULL outputs.
  */
 vg_status vg_get_kernel_ms(vg_ctx *ctx, double *total_ms, int64_t *count);
 
@@ -339,7 +368,8 @@ vg_status vg_get_kernel_ms(vg_ctx *ctx, double *total_ms, int64_t *count);
 vg_status vg_get_sort_ms(vg_ctx *ctx, double *total_ms, int64_t *count);
 
 /*
- * Diagnostics of the 3D FP32 prefetch form with vg_config.split = 1: the
+ * Diagnostics of the cell phase (Sec. 2.1.3) in the 3D FP32 prefetch form
+ * with vg_config.split = 1, into the caller's host variable: the
  * number of cells that the last vg_compute() or graph replay handed from
  * the kernel built for the common path to the general kernel (the walk
  * after both preloads, FP64 statistics, plane slots used up, more than 32
@@ -349,8 +379,9 @@ vg_status vg_get_sort_ms(vg_ctx *ctx, double *total_ms, int64_t *count);
 vg_status vg_get_deferred(vg_ctx *ctx, int64_t *count);
 
 /*
- * Batched 3D containers, FP32 prefetch form with vg_config.split = 1: which
- * kernel computes the cells of system k.  split = 1 (the default for every
+ * Batched 3D containers (the work queue of Sec. 2.2.4 across systems), FP32
+ * prefetch form with vg_config.split = 1: which kernel computes the cells of
+ * system k.  split = 1 (the default for every
  * system): the kernel built for the common path, as for a single system;
  * 0: the general kernel computes all of the system's cells (better for
  * systems whose cells outgrow their preload, as clustered ones; the
@@ -361,23 +392,29 @@ vg_status vg_get_deferred(vg_ctx *ctx, int64_t *count);
 vg_status vg_set_system_split(vg_ctx *ctx, int k, int split);
 
 /*
- * The sorted container: block_start has B+1 entries (B = product of the
- * block counts; for a batched container the sum over systems, system k's
- * blocks following those of systems < k) and order[k] is the input index of
- * the k-th particle in block order.  For checking the counting sort; device or host output.
+ * The sorted container of Sec. 2.1.1 (the blocks' particle lists):
+ * block_start has B+1 entries (B = product of the block counts; for a
+ * batched container the sum over systems, system k's blocks following those
+ * of systems < k) and order[k] is the input index of the k-th particle in
+ * block order; *n_blocks receives B.  For checking the counting sort;
+ * caller-owned device or host outputs.  VG_ERR_STATE before an insert.
  */
 vg_status vg_get_sorted(vg_ctx *ctx, int64_t *n_blocks, int32_t *block_start, int32_t *order,
                         int on_device);
 
 /* Number of CUDA kernels this context has launched since vg_create()
- * (diagnostics: lets a caller count the GPU work behind a call). */
+ * (diagnostics of this library, no counterpart in the paper: lets a caller
+ * count the GPU work behind a call).  VG_ERR_ARG for a NULL output. */
 vg_status vg_get_launches(vg_ctx *ctx, int64_t *count);
 
-/* The block counts in use (after vg_insert() when the n_opt rule applies);
- * for a batched container, those of system 0. */
+/* The block counts in use (the grid of Sec. 2.1.1, sized by the Sec. 2.1.4
+ * rule after vg_insert() when n_opt applies), dim ints into the caller's
+ * host array; for a batched container, those of system 0.  VG_ERR_ARG for
+ * a NULL output. */
 vg_status vg_get_grid(vg_ctx *ctx, int *nblocks);
 
-/* The block counts of system k of a (batched) container. */
+/* The block counts (Sec. 2.1.1) of system k of a (batched) container, as
+ * vg_get_grid().  VG_ERR_ARG for k out of range. */
 vg_status vg_get_system_grid(vg_ctx *ctx, int k, int *nblocks);
 
 /* ---- learned candidate count ---------------------------------------------
@@ -411,48 +448,62 @@ vg_status vg_get_system_grid(vg_ctx *ctx, int k, int *nblocks);
  */
 typedef struct vg_mlp vg_mlp;
 
-/* A predictor with all parameters 0; its work goes on `stream`. */
+/* A predictor (the learned count above) with all parameters 0, owned by
+ * the caller until vg_mlp_destroy(); its work goes on `stream`.  VG_ERR_ARG
+ * for a NULL `out`, VG_ERR_OOM when its buffers cannot be allocated,
+ * VG_ERR_CUDA on another CUDA failure. */
 vg_status vg_mlp_create(vg_mlp **out, void *stream);
 void vg_mlp_destroy(vg_mlp *mlp);
 const char *vg_mlp_last_error(vg_mlp *mlp);
 
-/* Sets the FP32 master parameters (1985 host floats), refreshes the FP16
- * copy and clears the Adam state. */
+/* Sets the FP32 master parameters of the network above (1985 host floats,
+ * read during the call), refreshes the FP16 copy and clears the Adam state.
+ * VG_ERR_ARG for NULL. */
 vg_status vg_mlp_set_params(vg_mlp *mlp, const float *params);
-/* Copies the FP32 master parameters to 1985 host floats. */
+/* Copies the FP32 master parameters of the network above to 1985
+ * caller-owned host floats.  VG_ERR_ARG for NULL. */
 vg_status vg_mlp_get_params(vg_mlp *mlp, float *params);
 
-/* Features of every block of an inserted container (all systems, global
- * block order): total blocks x 27 floats, row-major. */
+/* Features (above) of every block of an inserted container (all systems,
+ * global block order): total blocks x 27 floats, row-major, caller-owned.
+ * VG_ERR_STATE before an insert, VG_ERR_ARG for a NULL output. */
 vg_status vg_mlp_features(vg_ctx *ctx, float *X, int on_device);
 
-/* k* of every cell of the last vg_compute() (n int32, input order). */
+/* k* (above: candidates within twice the cell's radius, the bound of
+ * Sec. 2.1.3) of every cell of the last vg_compute() (n int32, input order,
+ * caller-owned).  VG_ERR_STATE before a compute. */
 vg_status vg_mlp_labels(vg_ctx *ctx, int32_t *kstar, int on_device);
 
 /*
- * Training rows from the last vg_compute(): one per block holding a
- * particle, in block order: features into X (DEVICE, room for total blocks
- * x 27 floats) and targets into t (DEVICE, room for total blocks floats);
- * *m receives the number of rows.
+ * Training rows (features and targets above) from the last vg_compute():
+ * one per block holding a particle, in block order: features into X
+ * (DEVICE, caller-owned, room for total blocks x 27 floats) and targets into
+ * t (DEVICE, room for total blocks floats); *m receives the number of rows.
+ * VG_ERR_ARG for NULL outputs, VG_ERR_STATE before a compute.
  */
 vg_status vg_mlp_dataset(vg_ctx *ctx, float *X, float *t, int64_t *m);
 
-/* Loss and gradient over M device rows (X: M x 27, t: M) at the current
- * FP16 weights, without an update; grad is 1985 host floats (may be NULL). */
+/* Loss and gradient (above) over M device rows (X: M x 27, t: M,
+ * caller-owned) at the current FP16 weights, without an update; grad is
+ * 1985 host floats (may be NULL).  VG_ERR_ARG for M < 1 or NULL rows. */
 vg_status vg_mlp_loss_grad(vg_mlp *mlp, const float *X, const float *t, int64_t M, float u,
                            double *loss, float *grad);
 
-/* `steps` full-batch Adam steps over M device rows with learning rate lr
- * and under-prediction weight u; losses (host, `steps` floats, may be NULL)
- * receives the loss before each step. */
+/* `steps` full-batch Adam steps (above) over M device rows with learning
+ * rate lr and under-prediction weight u; losses (host, `steps` floats, may
+ * be NULL) receives the loss before each step.  VG_ERR_ARG for M < 1,
+ * steps < 0, lr <= 0 or NULL rows. */
 vg_status vg_mlp_train(vg_mlp *mlp, const float *X, const float *t, int64_t M, float u, float lr,
                        int steps, float *losses);
 
-/* Network output y for M device rows of features (y: M device floats). */
+/* Network output y (above) for M device rows of features (y: M device
+ * floats, caller-owned).  VG_ERR_ARG for M < 0 or, with M > 0, NULL
+ * buffers. */
 vg_status vg_mlp_infer(vg_mlp *mlp, const float *X, int64_t M, float *y);
 
 /*
- * Per-block preload targets for the inserted container: clamp(alpha exp(y),
+ * Per-block preload targets (the learned count above) for the inserted
+ * container: clamp(alpha exp(y),
  * kmin, kmax) for every block, used by vg_compute() with use_mlp = 1 until
  * the next insert (each block preloads the geometric mean of the targets
  * of its 27 blocks, at least 8).  VG_ERR_STATE before an insert.
@@ -463,9 +514,11 @@ vg_status vg_mlp_predict(vg_ctx *ctx, vg_mlp *mlp, float alpha, float kmin, floa
  * Attaches a predictor to a container (NULL detaches): every later sort
  * (vg_insert, vg_batch_insert, graph replays) is followed by the prediction
  * of vg_mlp_predict(), so use_mlp = 1 needs no separate call and a captured
- * graph runs sort -> predict -> cells -> faces.  The container does not own
- * the predictor, which must outlive its use; attach again after training it
- * further.
+ * graph runs sort -> predict -> cells -> faces (the preload target of the
+ * prefetch form; the search of Sec. 2.1.3 still decides).  The container
+ * does not own the predictor, which must outlive its use; attach again
+ * after training it further.  VG_ERR_ARG for a NULL context or, with a
+ * predictor, alpha <= 0, kmin <= 0 or kmax < kmin.
  */
 vg_status vg_set_predictor(vg_ctx *ctx, vg_mlp *mlp, float alpha, float kmin, float kmax);
 
